@@ -1,0 +1,421 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+None of these compares the oracle with itself re-typed: the expected values
+come from hand-worked examples (tests/golden), numerical quadrature of the
+paper's integrals, textbook closed forms, the adjoint identity, a dense
+eigensolver, and brute-force enumeration of the L1 problem's supports.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1310_2078_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+DIRAC, PAR, WIDE = oracle.DIRAC, oracle.GAUSS_PARAXIAL, oracle.GAUSS_WIDE
+
+
+def _quad_1d(f, x0, sigma, h_div=200, half=9.0):
+    x = x0 + np.arange(-half * sigma, half * sigma + sigma / h_div / 2, sigma / h_div)
+    return np.sum(f(x)) * (sigma / h_div)
+
+
+def gaussian_paraxial_quadrature(l0, m0, sigma, u, v, w):
+    """Eq. samlm3 integral with gain and 1/n frozen at the pixel centre.
+
+    The integrand factorises into an l- and an m-integral; each is done by the
+    trapezoid rule on a fine grid (spectrally accurate for a Gaussian)."""
+    n0 = math.sqrt(1 - l0 * l0 - m0 * m0)
+
+    def fl(x):
+        return np.exp(-math.pi * (x - l0) ** 2 / sigma ** 2 + 1j * math.pi * w * x ** 2
+                      - 2j * math.pi * u * x) / sigma
+
+    def fm(x):
+        return np.exp(-math.pi * (x - m0) ** 2 / sigma ** 2 + 1j * math.pi * w * x ** 2
+                      - 2j * math.pi * v * x) / sigma
+
+    return _quad_1d(fl, l0, sigma) * _quad_1d(fm, m0, sigma) / n0
+
+
+def exact_gaussian_quadrature(l0, m0, sigma, u, v, w, h_div=60):
+    """Eq. samlm integral of one unit Gaussian pixel with the exact n(l, m)
+    everywhere (no Taylor step); 2-D trapezoid rule."""
+    ax = np.arange(-7 * sigma, 7 * sigma + sigma / h_div / 2, sigma / h_div)
+    L, M = np.meshgrid(l0 + ax, m0 + ax, indexing="ij")
+    n = np.sqrt(1 - L ** 2 - M ** 2)
+    f = np.exp(-math.pi * ((L - l0) ** 2 + (M - m0) ** 2) / sigma ** 2) / sigma ** 2
+    g = f / n * np.exp(-2j * math.pi * (u * L + v * M + w * (n - 1)))
+    # 1/n and the gain are taken at the centre by the closed form; undo the
+    # variation of 1/n so that only the phase approximation is compared
+    n0 = math.sqrt(1 - l0 * l0 - m0 * m0)
+    return np.sum(g * n / n0) * (sigma / h_div) ** 2
+
+
+# ---------------------------------------------------------------- Dirac entry
+
+def test_dirac_hand_worked_values():
+    rows = np.loadtxt(os.path.join(GOLDEN, "dirac_entries.txt"))
+    for l, m, u, v, w, re, im in rows:
+        a = oracle.entry(DIRAC, l, m, 0.0, u, v, w)
+        assert abs(a - complex(re, im)) < 1e-13, (l, m, u, v, w, a)
+
+
+def test_phase_centre_source_gives_constant_visibilities():
+    """A point source at the phase centre: V_k = flux for every baseline (n=1)."""
+    d = synth.random_problem(1, 50, 7, uv_max=2000, w_max=500)
+    lm = d["lm"].copy()
+    lm[3] = 0.0
+    P = oracle.Problem(d["uvw"], lm)
+    x = np.zeros(7)
+    x[3] = 2.5
+    V = oracle.forward(P, x)
+    assert np.max(np.abs(V - 2.5)) < 1e-13
+
+
+def test_n_minus_one_is_cancellation_free():
+    """n - 1 recovered from the w-phase matches its series to 1e-12 even at
+    r^2 = 1e-8, where sqrt(1 - r^2) - 1 loses ~8 digits."""
+    for r2 in (1e-8, 1e-6, 1e-3):
+        l = math.sqrt(r2)
+        exact = -r2 / 2 - r2 ** 2 / 8 - r2 ** 3 / 16 - 5 * r2 ** 4 / 128 - 7 * r2 ** 5 / 256
+        w = 0.25 / abs(exact)                    # phase w (n - 1) = -0.25 turn
+        a = oracle.entry(DIRAC, l, 0.0, 0.0, 0.0, 0.0, w)
+        n = math.sqrt(1 - r2)
+        # a = (1/n) exp(-2 pi i w (n-1)):  arg(a) = -2 pi w (n - 1)
+        nm1 = -math.atan2(a.imag, a.real) / (2 * math.pi * w)
+        assert abs(nm1 - exact) <= 1e-12 * abs(exact)
+        assert abs(abs(a) - 1 / n) < 1e-15
+
+
+# ----------------------------------------------------------- Gaussian entries
+
+GAUSS_CASES = [
+    # sigma, l, m, u, v, w
+    (0.01, 0.03, -0.02, 150.0, -80.0, 60.0),
+    (0.004, -0.1, 0.05, 400.0, 250.0, -300.0),
+    (0.02, 0.0, 0.0, 30.0, 10.0, 500.0),
+    (0.001, 0.2, 0.3, -900.0, 700.0, 200.0),
+]
+
+
+@pytest.mark.parametrize("case", GAUSS_CASES)
+def test_gaussian_paraxial_matches_quadrature(case):
+    """Eq. samlm4 (without the printed 1/sigma^2) equals the Eq. samlm3 integral."""
+    s, l, m, u, v, w = case
+    q = gaussian_paraxial_quadrature(l, m, s, u, v, w)
+    a = oracle.entry(PAR, l, m, s, u, v, w)
+    assert abs(a - q) <= 1e-10 * max(abs(q), 1e-300) + 1e-14
+
+
+def test_gaussian_w0_is_fourier_transform_of_gaussian():
+    """w -> 0: the textbook FT of a unit Gaussian, exp(-pi s^2 |u|^2) e^{-2 pi i u.x0}."""
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        s = rng.uniform(1e-4, 0.02)
+        l, m = rng.uniform(-0.3, 0.3, 2)
+        u, v = rng.uniform(-300, 300, 2)
+        n = math.sqrt(1 - l * l - m * m)
+        ft = math.exp(-math.pi * s * s * (u * u + v * v)) * np.exp(-2j * math.pi * (u * l + v * m)) / n
+        a = oracle.entry(PAR, l, m, s, u, v, 0.0)
+        assert abs(a - ft) < 1e-13
+
+
+@pytest.mark.parametrize("case", GAUSS_CASES)
+def test_gaussian_wide_matches_frozen_phase_quadrature(case):
+    """Eq. samlm5 = the integral whose non-quadratic phase is frozen at the
+    pixel centre, i.e. the paraxial integral times exp(-2 pi i w (n0-1+r0^2/2))."""
+    s, l, m, u, v, w = case
+    r2 = l * l + m * m
+    n0 = math.sqrt(1 - r2)
+    frozen = np.exp(-2j * math.pi * w * (n0 - 1 + r2 / 2))
+    q = gaussian_paraxial_quadrature(l, m, s, u, v, w) * frozen
+    a = oracle.entry(WIDE, l, m, s, u, v, w)
+    assert abs(a - q) <= 1e-10 * max(abs(q), 1e-300) + 1e-14
+
+
+def test_gaussian_wide_sigma_to_zero_is_dirac():
+    """sigma -> 0 of Eq. samlm5 is Eq. deltam exactly (this fixes the sign of
+    the r^2/2 term; the printed sign would leave a phase exp(2 pi i w r^2))."""
+    rng = np.random.default_rng(7)
+    for _ in range(50):
+        l, m = rng.uniform(-0.6, 0.6, 2)
+        u, v, w = rng.uniform(-1500, 1500, 3)
+        a = oracle.entry(WIDE, l, m, 1e-9, u, v, w)
+        d = oracle.entry(DIRAC, l, m, 0.0, u, v, w)
+        assert abs(a - d) < 1e-9 * abs(d)
+
+
+def test_gaussian_paraxial_sigma_to_zero_is_paraxial_dirac():
+    """sigma -> 0 of Eq. samlm4 is the paraxial point source: at small (l, m)
+    it approaches Eq. deltam with an error that falls like w r^4."""
+    for r in (0.02, 0.01, 0.005):
+        l, m, u, v, w = r * 0.6, r * 0.8, 120.0, -40.0, 300.0
+        a = oracle.entry(PAR, l, m, 1e-9, u, v, w)
+        d = oracle.entry(DIRAC, l, m, 0.0, u, v, w)
+        # phase of exp(-2 pi i w (n-1+r^2/2)) ~ 2 pi w r^4 / 8
+        assert abs(a - d) / abs(d) < 2 * math.pi * w * r ** 4 / 8 * 1.1 + 1e-12
+
+
+def test_gaussian_wide_converges_to_exact_integral():
+    """Against Eq. samlm with the exact n(l, m) inside the integral, the
+    wide-field pixel error shrinks as the pixel shrinks (its only
+    approximation is the Taylor step inside one pixel)."""
+    l, m, u, v, w = 0.35, 0.2, 150.0, -80.0, 60.0
+    errs = []
+    for s in (0.008, 0.004, 0.002):
+        ex = exact_gaussian_quadrature(l, m, s, u, v, w)
+        a = oracle.entry(WIDE, l, m, s, u, v, w)
+        errs.append(abs(a - ex) / abs(ex))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 0.3 * errs[0]
+    assert errs[2] < 1e-2
+
+
+# ------------------------------------------------------------------ gains
+
+def test_phase_ramp_gain_equals_uv_shift():
+    """G[j][a] = exp(2 pi i (alpha_a l + beta_a m)) makes g_jk a phase ramp:
+    for Dirac pixels the gained entry equals the ungained one at
+    (u - (alpha_a - alpha_b), v - (beta_a - beta_b), w)."""
+    rng = np.random.default_rng(11)
+    d = synth.random_problem(3, 40, 12, n_ant=6)
+    al, be = rng.uniform(-2, 2, 6), rng.uniform(-2, 2, 6)
+    lm = d["lm"]
+    G = np.exp(2j * np.pi * (lm[:, 0:1] * al[None] + lm[:, 1:2] * be[None]))
+    P = oracle.Problem(d["uvw"], lm, ant_pair=d["ant_pair"], gains=G)
+    for k in range(40):
+        a, b = d["ant_pair"][k]
+        u, v, w = d["uvw"][k]
+        for j in range(12):
+            want = oracle.entry(DIRAC, lm[j, 0], lm[j, 1], 0.0,
+                                u - (al[a] - al[b]), v - (be[a] - be[b]), w)
+            assert abs(oracle.entry_kj(P, k, j) - want) < 1e-12
+
+
+def test_real_gains_scale_by_product_and_swap_conjugates():
+    d = synth.random_problem(4, 30, 9, kinds=(DIRAC, PAR, WIDE), gains=True, n_ant=5)
+    P = oracle.Problem(d["uvw"], d["lm"], d["sigma"], d["kind"], ant_pair=d["ant_pair"],
+                       gains=d["gains"])
+    P0 = oracle.Problem(d["uvw"], d["lm"], d["sigma"], d["kind"])
+    ap_sw = d["ant_pair"][:, ::-1].copy()
+    Psw = oracle.Problem(d["uvw"], d["lm"], d["sigma"], d["kind"], ant_pair=ap_sw,
+                         gains=d["gains"])
+    G = d["gains"]
+    for k in range(30):
+        a, b = d["ant_pair"][k]
+        for j in range(9):
+            g = G[j, a] * np.conj(G[j, b])
+            e = oracle.entry_kj(P, k, j)
+            e0 = oracle.entry_kj(P0, k, j)
+            assert abs(abs(e) - abs(G[j, a]) * abs(G[j, b]) * abs(e0)) < 1e-12
+            # swapping the antennas conjugates the gain product
+            esw = oracle.entry_kj(Psw, k, j)
+            assert abs(esw * g - e * np.conj(g)) < 1e-12
+
+
+# ------------------------------------------------------ forward / adjoint
+
+def _dense(P):
+    return np.array([[oracle.entry_kj(P, k, j) for j in range(P.n_pix)] for k in range(P.n_vis)])
+
+
+def _problem(seed, nv, npx, **kw):
+    d = synth.random_problem(seed, nv, npx, **kw)
+    return oracle.Problem(d["uvw"], d["lm"], d["sigma"], d["kind"], d["weights"],
+                          d["ant_pair"], d["gains"]), d
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(kinds=(DIRAC, PAR, WIDE)),
+                                dict(kinds=(DIRAC, WIDE), gains=True, weights=True)])
+def test_forward_and_adjoint_match_dense_matrix(kw):
+    P, d = _problem(21, 37, 23, **kw)
+    A = _dense(P)
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=23)
+    x[rng.random(23) < 0.3] = 0.0
+    assert np.allclose(oracle.forward(P, x), A @ x, rtol=0, atol=1e-12 * np.abs(A).sum())
+    r = rng.normal(size=37) + 1j * rng.normal(size=37)
+    assert np.allclose(oracle.adjoint(P, r), (A.conj().T @ r).real, rtol=0,
+                       atol=1e-12 * np.abs(A).sum() * np.abs(r).max())
+    rows = [5, 0, 36]
+    assert np.allclose(oracle.forward(P, x, rows=rows), (A @ x)[rows], rtol=0, atol=1e-11)
+    cols = [22, 3]
+    assert np.allclose(oracle.adjoint(P, r, cols=cols), (A.conj().T @ r).real[cols],
+                       rtol=0, atol=1e-11)
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(kinds=(DIRAC, PAR, WIDE), gains=True)])
+def test_adjoint_identity(kw):
+    """<A x, y>_R = <x, Re A^H y> to 1e-12 relative, all kinds, with gains."""
+    P, d = _problem(31, 300, 200, uv_max=1500, w_max=400, **kw)
+    rng = np.random.default_rng(1)
+    for _ in range(3):
+        x = rng.normal(size=200)
+        y = rng.normal(size=300) + 1j * rng.normal(size=300)
+        lhs = np.real(np.vdot(y, oracle.forward(P, x)))
+        rhs = np.dot(x, oracle.adjoint(P, y))
+        scale = np.abs(x).sum() * np.abs(y).sum()
+        assert abs(lhs - rhs) <= 1e-12 * scale
+
+
+# ------------------------------------------------------------------- L
+
+def test_power_iteration_single_pixel_is_exact():
+    P, d = _problem(41, 60, 1, weights=True, gains=True, kinds=(WIDE,))
+    A = _dense(P)[:, 0]
+    L, it = oracle.power(P, max_iter=5, tol=1e-14)
+    assert abs(L - np.sum(d["weights"] * np.abs(A) ** 2)) < 1e-12 * L
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(kinds=(DIRAC, PAR), weights=True, gains=True)])
+def test_power_iteration_matches_dense_eigensolver(kw):
+    P, d = _problem(43, 80, 40, **kw)
+    A = _dense(P)
+    W = d["weights"] if d["weights"] is not None else np.ones(80)
+    B = (A.conj().T @ (W[:, None] * A)).real
+    lam = np.linalg.eigvalsh(B)[-1]
+    L, it = oracle.power(P, max_iter=20000, tol=1e-15)
+    assert abs(L - lam) < 1e-7 * lam
+    # and the default stopping rule gives a lower bound close to it
+    L6, _ = oracle.power(P, max_iter=50, tol=1e-6)
+    assert L6 <= lam * (1 + 1e-12) and L6 > 0.9 * lam
+
+
+# ----------------------------------------------------------------- FISTA
+
+def _normal_eqs(A, W, V):
+    B = (A.conj().T @ (W[:, None] * A)).real
+    c = (A.conj().T @ (W * V)).real
+    return B, c
+
+
+def brute_force_l1(A, W, V, lam):
+    """argmin_{x>=0} 1/2 sum W|Ax - V|^2 + lam sum x by enumerating supports."""
+    B, c = _normal_eqs(A, W, V)
+    n = B.shape[0]
+    best, best_F = None, np.inf
+    for mask in range(1 << n):
+        S = [j for j in range(n) if mask >> j & 1]
+        x = np.zeros(n)
+        if S:
+            xs = np.linalg.solve(B[np.ix_(S, S)], c[S] - lam)
+            if np.any(xs <= 0):
+                continue
+            x[S] = xs
+        grad = B @ x - c
+        off = [j for j in range(n) if j not in S]
+        if off and np.min(grad[off]) < -lam - 1e-9:
+            continue
+        r = A @ x - V
+        F = 0.5 * np.sum(W * np.abs(r) ** 2) + lam * x.sum()
+        if F < best_F:
+            best, best_F = x, F
+    return best, best_F
+
+
+def test_fista_single_pixel_closed_form():
+    """N_p = 1 with L = ||a||_W^2: one step reaches max(0, (Re a^H W V - lam)/||a||^2)."""
+    P, d = _problem(51, 25, 1, weights=True)
+    a = _dense(P)[:, 0]
+    W = d["weights"]
+    rng = np.random.default_rng(2)
+    V = 3.0 * a + 0.1 * (rng.normal(size=25) + 1j * rng.normal(size=25))
+    L = np.sum(W * np.abs(a) ** 2)
+    for lam in (0.0, 1.0, 20.0, 1e4):
+        want = max(0.0, (np.real(np.vdot(a, W * V)) - lam) / L)
+        img, st = oracle.fista(P, V, lam, L, max_iter=1)
+        assert abs(img[0] - want) < 1e-12 * max(1.0, want)
+        img5, _ = oracle.fista(P, V, lam, L, max_iter=5)
+        assert abs(img5[0] - want) < 1e-12 * max(1.0, want)
+
+
+def test_fista_zero_above_lambda_max():
+    """lam >= max_j Re(A^H W V)_j: the solution is exactly zero."""
+    P, d = _problem(53, 60, 30, weights=True)
+    A = _dense(P)
+    rng = np.random.default_rng(3)
+    V = A @ (np.abs(rng.normal(size=30)) * (rng.random(30) < 0.2))
+    dirty = (A.conj().T @ (d["weights"] * V)).real
+    L, _ = oracle.power(P)
+    img, st = oracle.fista(P, V, dirty.max() * 1.0001, L, max_iter=50)
+    assert np.all(img == 0.0) and st["nnz"] == 0
+
+
+@pytest.mark.parametrize("seed", [61, 62, 63])
+def test_fista_matches_brute_force_and_rate_bound(seed):
+    """Small strictly convex problems: FISTA reaches the enumerated minimiser,
+    and F(I_k) - F* <= 2 L ||I_0 - I*||^2 / (k+1)^2 (Beck & Teboulle 2009,
+    Thm 4.4) holds along the way."""
+    P, d = _problem(seed, 30, 6, kinds=(DIRAC, PAR), weights=True, uv_max=40, w_max=10,
+                    extent=0.2, sigma_max=0.02)
+    A = _dense(P)
+    W = d["weights"]
+    rng = np.random.default_rng(seed)
+    xt = np.abs(rng.normal(size=6)) * (rng.random(6) < 0.5)
+    V = A @ xt + 0.05 * (rng.normal(size=30) + 1j * rng.normal(size=30))
+    lam = 0.5
+    xs, Fs = brute_force_l1(A, W, V, lam)
+    B, _ = _normal_eqs(A, W, V)
+    L = np.linalg.eigvalsh(B)[-1]
+    for k in (1, 2, 5, 10, 30, 100):
+        img, st = oracle.fista(P, V, lam, L, max_iter=k)
+        assert st["E"] - Fs <= 2 * L * np.sum(xs ** 2) / (k + 1) ** 2 + 1e-9
+    img, st = oracle.fista(P, V, lam, L, max_iter=20000)
+    assert np.max(np.abs(img - xs)) < 1e-7 * max(1.0, xs.max())
+    assert abs(st["E"] - Fs) < 1e-10 * Fs
+
+
+def test_fista_kkt_at_convergence():
+    """I_j > 0 => Re(A^H W(AI - V))_j = -lam;  I_j = 0 => >= -lam."""
+    P, d = _problem(71, 120, 40, kinds=(DIRAC, WIDE), gains=True, uv_max=60, w_max=20,
+                    extent=0.2, sigma_max=0.02)
+    A = _dense(P)
+    rng = np.random.default_rng(4)
+    xt = np.zeros(40)
+    xt[rng.choice(40, 5, replace=False)] = rng.uniform(1, 3, 5)
+    V = A @ xt
+    lam = 0.3
+    L, _ = oracle.power(P, max_iter=2000, tol=1e-14)
+    img, st = oracle.fista(P, V, lam, L * 1.000001, max_iter=20000)
+    g = (A.conj().T @ (A @ img - V)).real
+    on = img > 0
+    assert on.sum() >= 1
+    assert np.max(np.abs(g[on] + lam)) < 1e-6 * lam
+    assert np.min(g[~on]) > -lam * (1 + 1e-6)
+
+
+def test_noise_free_isolated_sources_are_recovered():
+    """Noise-free, isolated point sources on pixel centres, small lam: the
+    recovered fluxes sit within the L1 bias (~lam/||a_j||^2) of the truth."""
+    w = synth.config1(scale=0.5)           # 16x16 grid, 2,208 visibilities
+    P = oracle.Problem(w.uvw, w.lm)
+    V = oracle.forward(P, w.x_true)
+    L, _ = oracle.power(P)
+    lam = 1.0
+    img, st = oracle.fista(P, V, lam, L, max_iter=1500)
+    on = w.x_true > 0
+    colnorm2 = np.array([np.sum(np.abs(oracle.forward(P, np.eye(1, w.n_pix, j)[0])) ** 2)
+                         for j in np.flatnonzero(on)])
+    bias = lam / colnorm2
+    err = np.abs(img[on] - w.x_true[on])
+    assert np.all(err < 5 * bias + 1e-3 * w.x_true[on].max())
+    assert img[~on].sum() < 1e-2 * w.x_true.sum()
+    assert st["l1"] < w.x_true.sum()
+
+
+def test_stopping_rule_relative_change_of_E():
+    P, d = _problem(81, 80, 30, uv_max=60, w_max=10)
+    A = _dense(P)
+    rng = np.random.default_rng(5)
+    V = A @ (np.abs(rng.normal(size=30)) * (rng.random(30) < 0.3))
+    L, _ = oracle.power(P)
+    img, st = oracle.fista(P, V, 0.2, L, max_iter=5000, tol=1e-6)
+    assert st["converged"] == 1 and st["iters"] < 5000
+    # one more step changes E by no more than the tolerance's order
+    img2, st2 = oracle.fista(P, V, 0.2, L, max_iter=st["iters"] - 1)
+    assert abs(st["E"] - st2["E"]) <= 1e-6 * st2["E"] * (1 + 1e-9)
+    assert st["E_paper"] == pytest.approx(st["resid2"] + 0.2 * st["l1"])
