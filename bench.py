@@ -1,0 +1,362 @@
+"""Benchmark of the SL1M hot path on GB300.
+
+Workload (default): the wide-field w-term configuration -- 256x256 = 65,536
+Dirac pixels over l,m in +/-0.5, 64 antennas (R = 2 km, 50 m height scatter),
+20 snapshots -> 40,320 visibilities, 200 point sources + noise, mixed
+precision.  One step = one complete solve through the C ABI: L by power
+iteration (<= 50 steps, tol 1e-6), then 200 FISTA steps with
+lambda = 0.02 * max Re(A^H V).  Metric: pixel-visibility pairs evaluated per
+second by the forward and adjoint kernels (pairs/s), whole job.
+
+value : inputs resident in HBM when the timed region starts; each step timed
+        with CUDA events on the library's stream, L2 flushed between steps.
+e2e   : the same solve through the C ABI from HOST buffers: setting the
+        visibilities and pixels (layout + H2D) and reading the image back are
+        inside the timed region.
+--impl reference : the FP64 CPU oracle on the host cores, bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MUFU_PER_SM_CLK = 16          # sin/cos/ex2 per clock per SM (CUDA guide throughput table)
+SFU_OPS_PER_PAIR = {"dirac": 2, "gauss": 3}
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--iters", type=int, default=200)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ops-only", action="store_true",
+                    help="profiling helper: run forward+adjoint pairs only (for ncu)")
+    return ap.parse_args()
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return ws, rank, local
+
+
+def workload(cfg: int, rank: int = 0):
+    from paper_1310_2078_gb300 import synth
+    w = synth.CONFIGS[cfg]()
+    if rank:
+        # weak scaling: every rank solves its own independent problem of the same shape
+        rng = synth.rng_for(synth.BASE_SEED + 100 * rank + cfg)
+        w.noise = synth.complex_noise(rng, w.n_vis, float(np.std(w.noise.real)) or 0.01)
+    return w
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                pw.append(float(r[3]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": float(np.median(load)), "sm_max_mhz": max(mx),
+                "power_w_max": max(pw) if pw else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def ncu_traffic():
+    """dram bytes per launch of the dominant kernel from the committed ncu
+    summary (null when absent or stale)."""
+    p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
+def cpu_baseline(w, budget_s: float = 12.0):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample of
+    the same workload: forward rows and adjoint columns; pairs/s."""
+    import oracle
+    O = oracle.Problem(w.uvw, w.lm, w.sigma, w.kind, w.weights, w.ant_pair, w.gains)
+    rng = np.random.default_rng(0)
+    x = np.abs(rng.normal(size=w.n_pix))
+    r = rng.normal(size=w.n_vis) + 1j * rng.normal(size=w.n_vis)
+    # calibrate: 8 rows
+    t0 = time.perf_counter()
+    oracle.forward(O, x, rows=np.arange(8))
+    per_row = (time.perf_counter() - t0) / 8
+    n_rows = max(8, int(0.5 * budget_s / per_row))
+    n_cols = max(8, int(0.5 * budget_s / (per_row * w.n_vis / w.n_pix)))
+    rows = rng.choice(w.n_vis, min(n_rows, w.n_vis), replace=False)
+    cols = rng.choice(w.n_pix, min(n_cols, w.n_pix), replace=False)
+    t0 = time.perf_counter()
+    oracle.forward(O, x, rows=rows)
+    oracle.adjoint(O, r, cols=cols)
+    dt = time.perf_counter() - t0
+    pairs = len(rows) * w.n_pix + len(cols) * w.n_vis
+    return {"value": pairs / dt, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(rows)} forward rows x {w.n_pix} px + {len(cols)} adjoint "
+                      f"columns x {w.n_vis} vis of {w.name}, FP64, single thread, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores (bounded samples)."""
+    ws, rank, _ = dist_init()
+    if rank != 0:
+        return
+    import oracle
+    w = workload(args.config)
+    O = oracle.Problem(w.uvw, w.lm, w.sigma, w.kind, w.weights, w.ant_pair, w.gains)
+    rng = np.random.default_rng(0)
+    x = np.abs(rng.normal(size=w.n_pix))
+    r = rng.normal(size=w.n_vis) + 1j * rng.normal(size=w.n_vis)
+    t0 = time.perf_counter()
+    oracle.forward(O, x, rows=np.arange(4))
+    per_row = (time.perf_counter() - t0) / 4
+    n_rows = max(4, int(2.0 / per_row))            # ~2 s forward + ~2 s adjoint per step
+    n_cols = max(4, int(2.0 / (per_row * w.n_vis / w.n_pix)))
+    times, pairs = [], 0
+    for s in range(args.warmup + args.steps):
+        rows = rng.choice(w.n_vis, min(n_rows, w.n_vis), replace=False)
+        cols = rng.choice(w.n_pix, min(n_cols, w.n_pix), replace=False)
+        t0 = time.perf_counter()
+        oracle.forward(O, x, rows=rows)
+        oracle.adjoint(O, r, cols=cols)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            pairs += len(rows) * w.n_pix + len(cols) * w.n_vis
+    T = sum(times)
+    val = pairs / T
+    sample = (f"per step {min(n_rows, w.n_vis)} forward rows + {min(n_cols, w.n_pix)} adjoint "
+              f"columns of {w.name} (FP64 oracle, single thread)")
+    out = {"impl": "reference", "metric": "pixel-visibility pairs/s (fwd+adj)", "value": val,
+           "unit": "pairs/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * T / len(times), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name, "n_pix": w.n_pix, "n_vis": w.n_vis},
+           "cpu_baseline": {"value": val, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": val, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    ws, rank, local = dist_init()
+    from paper_1310_2078_gb300 import sl1m
+    sl1m.load()
+    dev = local
+    torch.cuda.set_device(dev)
+    prec = sl1m.MIXED if args.precision == "mixed" else sl1m.FP64
+    w = workload(args.config, rank)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = sl1m.Context(dev, stream=stream)
+    # synthetic visibilities: V = A x_true + noise, formed by the library's own forward
+    P = ctx.problem()
+    P.set_visibilities(w.uvw, None, w.weights, w.ant_pair)
+    P.set_pixels(w.lm, w.sigma, w.kind)
+    if w.gains is not None:
+        P.set_gains(w.gains)
+    V = P.forward(w.x_true, sl1m.FP64 if w.n_vis * w.n_pix < 5e9 else sl1m.MIXED) + w.noise
+    P.set_vis_data(V)
+    lam = w.lambda_frac * P.adjoint(V * (1 if w.weights is None else w.weights), prec).max()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
+
+    def one_step():
+        return P.solve(lam, L=0.0, max_iter=args.iters, precision=prec)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    ctx.profile_reset()
+    ctx.counters_reset()
+    ctx.profile_enable(True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev = []
+    stats = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)                     # L2 flush between steps (outside the events)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        img, st = one_step()
+        with torch.cuda.stream(stream):
+            e1.record(stream)
+        ev.append((e0, e1))
+        stats.append(st)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ctx.profile_enable(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    T = sum(step_ms) / 1e3
+    counters = ctx.counters()
+    prof = {k: ctx.profile_read(k) for k in sl1m.KERNEL_IDS}
+    op_pairs = sum(prof[k]["pairs"] for k in ("fwd_fp64", "adj_fp64", "fwd_mixed", "adj_mixed"))
+    if ws > 1:
+        t = torch.tensor([T, op_pairs], dtype=torch.float64, device=f"cuda:{dev}")
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax[0:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t[1:2], op=torch.distributed.ReduceOp.SUM)
+        T_job, pairs_job = float(tmax[0]), float(t[1])
+    else:
+        T_job, pairs_job = T, op_pairs
+    value = pairs_job / T_job
+    solves_per_s = ws * args.steps / T_job
+
+    # roofline of the dominant kernel
+    keys = ("fwd_mixed", "adj_mixed") if prec == sl1m.MIXED else ("fwd_fp64", "adj_fp64")
+    dom = max(keys, key=lambda k: prof[k]["ms"])
+    pd = prof[dom]
+    achieved = pd["pairs"] / (pd["ms"] / 1e3) / 1e9 if pd["ms"] > 0 else 0.0
+    kind = "gauss" if (w.kind is not None and np.any(w.kind != 0)) else "dirac"
+    peak = N_SM * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / SFU_OPS_PER_PAIR[kind] / 1e9
+    traffic = ncu_traffic()
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "Gpairs/s", "frac": achieved / peak,
+                "peak_basis": (f"SFU issue: {N_SM} SM x {MUFU_PER_SM_CLK} MUFU/clk x "
+                               f"{SM_MAX_MHZ:.0f} MHz / {SFU_OPS_PER_PAIR[kind]} MUFU per pair"),
+                "launches": pd["launches"], "avg_launch_ms": pd["ms"] / max(1, pd["launches"]),
+                "traffic": (traffic or {}).get("dram_bytes_per_launch")}
+    fin_ms = prof["fwd_finish"]["ms"] + prof["adj_finish"]["ms"]
+    fin_bytes = prof["fwd_finish"]["bytes"] + prof["adj_finish"]["bytes"]
+    vec = {"kernels": "fwd_finish+adj_finish (residual, threshold, momentum)",
+           "achieved_GBps": fin_bytes / (fin_ms / 1e3) / 1e9 if fin_ms else None,
+           "share_of_step": fin_ms / (T * 1e3)}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(ctx, w, V, lam, prec, args, sl1m, stream)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(w)
+    if rank == 0:
+        out = {"metric": "pixel-visibility pairs/s (fwd+adj)", "value": value, "unit": "pairs/s",
+               "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": 1e3 * T_job / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None,
+               "dtype": "f32+f64" if prec == sl1m.MIXED else "f64", "data": "synthetic",
+               "config": {"workload": w.name, "n_pix": w.n_pix, "n_vis": w.n_vis,
+                          "step": f"one solve: power iteration (<=50) + {args.iters} FISTA steps",
+                          "precision": args.precision, "lambda": lam,
+                          "l2": "flushed between steps (268 MB write)",
+                          "parallelism": f"replicas{ws}" if ws > 1 else "1 GPU"},
+               "solves_per_s": solves_per_s,
+               "iters": [s["iters"] for s in stats], "power_iters": stats[-1]["power_iters"],
+               "final": {"E": stats[-1]["E"], "resid2": stats[-1]["resid2"],
+                         "nnz": stats[-1]["nnz"], "L": stats[-1]["L"]},
+               "roofline": roofline, "vector_updates": vec,
+               "clocks": clk, "gpu_launches": counters["launches"],
+               "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(out))
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_e2e(ctx, w, V, lam, prec, args, sl1m, stream):
+    """The same solve from host buffers through the C ABI: set inputs (host
+    layout + H2D), solve, read the image back (D2H) -- all timed."""
+    import torch
+    steps = max(1, min(args.steps, 3))
+    ctx.counters_reset()
+    t0 = time.perf_counter()
+    pairs = 0.0
+    for _ in range(steps):
+        Q = ctx.problem()
+        Q.set_visibilities(w.uvw, V, w.weights, w.ant_pair)
+        Q.set_pixels(w.lm, w.sigma, w.kind)
+        if w.gains is not None:
+            Q.set_gains(w.gains)
+        img, st = Q.solve(lam, L=0.0, max_iter=args.iters, precision=prec)
+        pairs += (2 * st["power_iters"] + 2 * st["iters"] + 1) * float(w.n_vis) * w.n_pix
+        Q.close()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    c = ctx.counters()
+    return {"value": pairs / dt, "unit": "pairs/s", "steps": steps,
+            "h2d_bytes_per_step": c["h2d_bytes"] // steps, "d2h_bytes_per_step": c["d2h_bytes"] // steps,
+            "ms_per_step": 1e3 * dt / steps}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * sl1m.h -- C ABI of libsl1m, the GB300 (sm_103a) hot path of SL1M:
+ * positivity-constrained L1 deconvolution of ungridded radio visibilities
+ * (S. J. Hardy 2013, "Direct deconvolution of radio synthesis images using
+ * L1 minimisation", A&A; arxiv 1310.2078).
+ *
+ * Conventions (all entry points):
+ *   - Index convention: pixel j (n_pix of them), visibility k (n_vis).  The
+ *     operator A is n_vis x n_pix, A_kj = the paper's M_jk (Eq. sme).
+ *   - Units: u, v, w in wavelengths (Sect. 2: b = lambda (u e_u + v e_v +
+ *     w e_w)); l, m direction cosines with l^2 + m^2 < 1; sigma in direction
+ *     cosines; fluxes in Jy.  Complex arrays are interleaved (re, im) doubles.
+ *   - Ownership: the caller owns every array it passes.  Host-pointer calls
+ *     copy inputs in and results out before returning.  The *_dev calls take
+ *     device pointers (CUDA global memory on the context's device), borrow
+ *     them for the duration of the call and are asynchronous on the
+ *     context's stream unless stated otherwise.
+ *   - Every call returns an SL1M_* status.  On failure nothing that the call
+ *     was to produce is valid; sl1m_last_error() gives a one-line reason.
+ *   - Thread safety: a context and its problems must be used from one host
+ *     thread at a time.
+ *   - Precision: SL1M_FP64 evaluates every step in FP64 ("plain" path);
+ *     SL1M_MIXED evaluates sincos/exp and the complex multiply-accumulates in
+ *     FP32 after an exact FP32 reduction of the phase to fractional turns;
+ *     sums over tiles, norms, step sizes and the projection stay in FP64.
+ */
+#ifndef SL1M_H
+#define SL1M_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SL1M_OK 0
+#define SL1M_ERR_ARG 1        /* null pointer, bad size, l^2+m^2 >= 1, sigma < 0,
+                                 non-finite input, antenna index out of range */
+#define SL1M_ERR_OOM 2        /* device or host allocation failed              */
+#define SL1M_ERR_CUDA 3       /* a CUDA runtime call failed                    */
+#define SL1M_ERR_NONFINITE 4  /* a non-finite value appeared during a solve    */
+#define SL1M_ERR_TIMEOUT 5    /* a bounded wait expired                        */
+#define SL1M_ERR_BUSY 6       /* admission refused (memory budget)             */
+#define SL1M_ERR_STATE 7      /* problem incomplete (no pixels/visibilities),
+                                 or gains set without antenna pairs            */
+
+#define SL1M_FP64 0
+#define SL1M_MIXED 1
+
+/* Pixel kinds.  Dirac: Eq. deltam.  Paraxial Gaussian: Eq. samlm4.
+ * Wide-field Gaussian: Eq. samlm5.  (For the Gaussian kinds the factor
+ * 1/sigma^2 printed in front of Eq. samlm4/5 is not applied: the pixel of
+ * Eq. gaus has unit integral, so x_j is the pixel's total flux; and the
+ * wide-field residual phase is w (n - 1 + (l^2+m^2)/2), the form whose
+ * Taylor expansion is Eq. taylorexp.) */
+#define SL1M_DIRAC 0
+#define SL1M_GAUSS_PARAXIAL 1
+#define SL1M_GAUSS_WIDE 2
+
+typedef struct sl1m_ctx sl1m_ctx;
+typedef struct sl1m_problem sl1m_problem;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int sl1m_version(void);
+
+/* Static description of a status code. */
+const char* sl1m_status_string(int status);
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a
+ * cudaStream_t to run on, or NULL for a stream the context creates and owns.
+ * The context owns every device allocation made through it. */
+int sl1m_create(sl1m_ctx** out, int device, void* cuda_stream);
+
+/* Destroy a context and every problem created in it. */
+int sl1m_destroy(sl1m_ctx* ctx);
+
+/* Last error message of the context ("" if none).  Valid until the next call. */
+const char* sl1m_last_error(const sl1m_ctx* ctx);
+
+/* Create / destroy an (empty) deconvolution problem. */
+int sl1m_problem_create(sl1m_ctx* ctx, sl1m_problem** out);
+int sl1m_problem_destroy(sl1m_problem* prob);
+
+/* Visibilities, Sect. 2 (Eq. samuvw): uvw [n_vis][3] in wavelengths,
+ * vis [n_vis][2] the measured V_k (may be NULL: zeros), weights [n_vis] W_k
+ * >= 0 or NULL (= 1; W multiplies the squared residual, W = 1 is the paper's
+ * case), ant_pair [n_vis][2] antenna indices (a_k, b_k) or NULL (required
+ * only with gains).  Replaces any earlier visibilities.  Copies the data. */
+int sl1m_set_visibilities(sl1m_problem* prob, int64_t n_vis, const double* uvw,
+                          const double* vis, const double* weights, const int32_t* ant_pair);
+
+/* Replace only the measured visibilities V (same uvw, same order). */
+int sl1m_set_vis_data(sl1m_problem* prob, const double* vis);
+
+/* Pixels, Sect. 2.1 (pixel list (l_k, m_k), arbitrary positions):
+ * lm [n_pix][2], sigma [n_pix] (NULL = 0) and kind [n_pix] (NULL = all
+ * Dirac).  Gaussian kinds need sigma > 0.  Copies the data. */
+int sl1m_set_pixels(sl1m_problem* prob, int64_t n_pix, const double* lm,
+                    const double* sigma, const int32_t* kind);
+
+/* Direction-dependent gains (Sect. 2: A(l,m; Z_j, chi_j), "arbitrary gains
+ * between each pixel and each antenna element"): G [n_pix][n_ant][2],
+ * per pixel and antenna; the entry for visibility k is multiplied by
+ * g_jk = G[j][a_k] * conj(G[j][b_k]).  G == NULL or n_ant == 0 removes the
+ * gains.  The mixed-precision forward holds a pixel tile's gains for all
+ * antennas in shared memory and supports n_ant <= 400. */
+int sl1m_set_gains(sl1m_problem* prob, int32_t n_ant, const double* G);
+
+/* Forward operator, Eq. sme: vis_out_k = sum_j A_kj x_j.
+ * x [n_pix] (host), vis_out [n_vis][2] (host).  Synchronous. */
+int sl1m_forward(sl1m_problem* prob, const double* x, double* vis_out, int precision);
+
+/* Adjoint (back-projection of Sect. 3): img_out_j = sum_k Re(conj(A_kj) r_k).
+ * r [n_vis][2] (host), img_out [n_pix] (host).  Synchronous. */
+int sl1m_adjoint(sl1m_problem* prob, const double* r, double* img_out, int precision);
+
+/* Device-pointer variants of the two calls above, asynchronous on the
+ * context's stream (the caller synchronises before reading the output). */
+int sl1m_forward_dev(sl1m_problem* prob, const double* x_dev, double* vis_out_dev, int precision);
+int sl1m_adjoint_dev(sl1m_problem* prob, const double* r_dev, double* img_out_dev, int precision);
+
+/* Step constant of FISTA (Sect. 3, algorithm box: L = largest eigenvalue of
+ * M*M; the paper uses "an algorithm to calculate the largest eigenvalue",
+ * Sect. 3.1).  Power iteration on B = Re(A^H W A) from x = 1/sqrt(n_pix):
+ * z = B x, mu = ||z||, x = z/mu, stopping when |mu_i - mu_{i-1}| <= tol*mu_i
+ * or after max_iter steps; L = the last mu.  Synchronous. */
+int sl1m_max_eig(sl1m_problem* prob, int max_iter, double tol, int precision,
+                 double* L_out, int* iters_out);
+
+/* Solver options.  lambda: regulariser of Eq. cme.  L: step constant, or 0 to
+ * compute it with sl1m_max_eig(power_max_iter, power_tol).  rel_tol: stop
+ * when |E_k - E_{k-1}| <= rel_tol * E_{k-1} (Sect. 3; 0 = run max_iter
+ * steps), where E = 1/2 sum W |A I - V|^2 + lambda sum I is the objective the
+ * algorithm box minimises.  x0: starting image [n_pix] (host) or NULL (zero,
+ * the box's Step 0). */
+typedef struct {
+    double lambda;
+    double L;
+    double rel_tol;
+    int32_t max_iter;
+    int32_t precision;
+    int32_t power_max_iter;   /* 0 = 50   */
+    double power_tol;         /* 0 = 1e-6 */
+    const double* x0;
+} sl1m_solve_opts;
+
+typedef struct {
+    int32_t iters;        /* FISTA steps taken                                   */
+    int32_t converged;    /* 1 when rel_tol was met                              */
+    double E;             /* 1/2 sum W|A I - V|^2 + lambda sum I                 */
+    double E_paper;       /* sum W|A I - V|^2 + lambda sum I   (Eq. cme)          */
+    double resid2;        /* sum W |A I - V|^2                                   */
+    double l1;            /* sum I                                               */
+    int64_t nnz;          /* number of I_j > 0                                   */
+    double L;             /* step constant used                                  */
+    int32_t power_iters;  /* power-iteration steps (0 if L was given)            */
+    double seconds;       /* wall time of the call                               */
+} sl1m_solve_stats;
+
+/* FISTA with the positive soft threshold (Sect. 3 algorithm box, Eq. threshp):
+ *   I_k = T^{lambda/L}(y_k - Re A^H W (A y_k - V)/L),
+ *   t_{k+1} = (1 + sqrt(1 + 4 t_k^2))/2,
+ *   y_{k+1} = I_k + ((t_k - 1)/t_{k+1}) (I_k - I_{k-1}).
+ * img_out [n_pix] (host) receives the last I_k; stats may be NULL.
+ * Synchronous.  SL1M_ERR_NONFINITE if a non-finite value appeared. */
+int sl1m_solve(sl1m_problem* prob, const sl1m_solve_opts* opts, double* img_out,
+               sl1m_solve_stats* stats);
+
+/* Kernel timing with CUDA events on the context's stream (for benchmarks).
+ * Kernel ids: 0 forward FP64, 1 adjoint FP64, 2 forward mixed, 3 adjoint
+ * mixed, 4 forward finish, 5 adjoint finish (solver vector updates), 6 other.
+ * sl1m_profile_read synchronises the stream and returns, for one kernel id,
+ * the summed event time (ms), the number of launches, the pixel-visibility
+ * pairs those launches evaluated and the bytes the finish kernels moved. */
+int sl1m_profile_enable(sl1m_ctx* ctx, int on);
+int sl1m_profile_reset(sl1m_ctx* ctx);
+int sl1m_profile_read(sl1m_ctx* ctx, int kernel_id, double* ms, int64_t* launches,
+                      double* pairs, double* bytes);
+
+/* Counters since context creation or the last sl1m_counters_reset: kernel
+ * launches the library issued, bytes it copied host->device (inputs and their
+ * device layout, starting images) and device->host (results). */
+int sl1m_counters(sl1m_ctx* ctx, int64_t* launches, int64_t* h2d_bytes, int64_t* d2h_bytes);
+int sl1m_counters_reset(sl1m_ctx* ctx);
+
+/* Host-only inspection of the work split (no GPU needed).  Work on a batch
+ * of problems is cut into units (owned block of 512 elements x streamed
+ * granule of 64), owned_blocks[p] * streamed_granules[p] per problem, and
+ * spread over n_ctas = min(max_ctas, units) persistent CTAs: CTA c takes units
+ * [c U / C, (c+1) U / C).  For every block (problems in order) the call
+ * returns the first contributing CTA, their count and the first partial-sum
+ * slot; arrays are sized by the total number of blocks. */
+int sl1m_plan_preview(int32_t n_probs, const int32_t* owned_blocks, const int32_t* streamed_granules,
+                      int32_t max_ctas, int32_t* n_ctas, int64_t* n_units, int32_t* n_slots,
+                      int32_t* blk_first_cta, int32_t* blk_n_ctas, int32_t* blk_first_slot);
+
+/* Host-only: the granule order the library uses for n points xy [n][2]:
+ * order [n_pad] receives point indices, -1 for padding, so that each run of
+ * 64 is a compact box (k-d median split along the wider axis at multiples of
+ * 64).  n_pad = ceil(n / 64) * 64.  order may be NULL to query n_pad. */
+int sl1m_granule_order(int64_t n, const double* xy, int32_t* order, int64_t* n_pad);
+
+/* Device bytes the problem holds (inputs, layout and solver workspace). */
+int sl1m_problem_bytes(const sl1m_problem* prob, int64_t* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SL1M_H */

@@ -1,0 +1,144 @@
+// sl1m_dev.h -- device-side data layout shared by the kernels and the host
+// code of libsl1m.  Internal: not part of the public C ABI (include/sl1m.h).
+//
+// Layout in HBM (per problem, after sorting; see sl1m_host.cpp):
+//   * Both sides (visibilities and pixels) are permuted into "granules" of
+//     G = 64 elements by a k-d median split, so that every granule is a
+//     compact box in (u,v,w) resp. (l,m).  Pixels are first grouped into
+//     classes of equal (kind, sigma); each class is padded to a multiple of G
+//     with inert padding (amplitude 0 / weight 0), so kind and sigma are
+//     uniform per pixel granule.
+//   * Per element: FP64 coordinates (x,y,z,aux) for the FP64 path, and for
+//     the mixed path the FP32 hi/lo split of the absolute coordinates and of
+//     the offset from the granule centre.
+//   * A CTA "owns" a block of BLK_GRAN granules of one side (one granule per
+//     warp, 2 elements per lane) and streams granules of the other side
+//     through shared memory.  Work is split over a persistent grid by
+//     "units" = (owned block, streamed granule), stream-K style; partial sums
+//     land in per-(block, contributing CTA) slots that the finish kernels add
+//     up in a fixed order (deterministic, no atomics).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sl1m {
+
+// 32-byte aligned quadruple of doubles (one 256-bit access).
+struct __align__(32) d4 {
+    double x, y, z, w;
+};
+__host__ __device__ inline d4 make_d4(double x, double y, double z, double w)
+{
+    d4 r;
+    r.x = x; r.y = y; r.z = z; r.w = w;
+    return r;
+}
+
+constexpr int G = 64;                 // granule size
+constexpr int BLK_GRAN = 8;           // owned granules per CTA (one per warp)
+constexpr int BLK = G * BLK_GRAN;     // owned elements per CTA block
+constexpr int NTHREADS = 256;         // 8 warps
+constexpr int MAX_PROBS = 1024;       // problems per batched launch
+
+enum Kind : int { DIRAC = 0, PARAXIAL = 1, WIDE = 2 };
+
+// One side (visibilities or pixels) of a problem, sorted and padded.
+struct Side {
+    int n;              // real elements
+    int n_pad;          // n_gran * G
+    int n_gran;
+    int n_blk;          // ceil(n_gran / BLK_GRAN)
+    const float4* hi;     // absolute coordinates, FP32 hi part  {x,y,z,0}
+    const float4* lo;     // absolute coordinates, FP32 lo part
+    const float4* off;    // offset from granule centre, rounded {dx,dy,dz,aux32}
+    const float4* offlo;  // offset residual: offset = off + offlo (to ~2^-48)
+    const float4* cen_hi; // granule centre, hi   [n_gran]
+    const float4* cen_lo; // granule centre, lo   [n_gran]
+    const float4* ext;    // granule extent: max |offset| per coordinate [n_gran]
+    const d4* d;     // FP64 {x, y, z, aux}
+    const int* orig;      // sorted index -> caller's index, -1 for padding
+};
+// vis: x,y,z = u,v,w (wavelengths); aux = weight W_k (0 for padding)
+// pix: x,y,z = l, m, n-1 (n-1 = -(l^2+m^2)/(1+n)); aux = 1/n (0 for padding)
+
+struct DevProblem {
+    Side vis;
+    Side pix;
+    const int2* ant;          // [vis.n_pad] antenna pair (a, b)
+    const double2* V;         // [vis.n_pad] measured visibilities (sorted)
+    const float4* pgauss;     // [pix.n_pad] {l, m, (l^2+m^2)/2, nu = n-1+(l^2+m^2)/2}
+    const d4* pgauss64;  // same in FP64
+    const float* gsig;        // [pix.n_gran] sigma per pixel granule
+    const int* gkind;         // [pix.n_gran] kind per pixel granule
+    const float2* gains32;    // [pix.n_pad][n_ant] or null
+    const double2* gains64;   // [pix.n_pad][n_ant] or null
+    int n_ant;
+    int active;               // 0: skip this problem in batched launches
+    // per-launch operands (sorted layouts)
+    const double* x;          // forward input  [pix.n_pad]
+    const double* xpp[2];     // solve mode: forward input is xpp[*xsel]
+    const int* xsel;          // null: use x
+    const double* xscale;     // optional device scalar multiplying x (power iteration)
+    const double2* r;         // adjoint input  [vis.n_pad]
+    const int* done;          // optional device flag: 1 = problem finished, skip its units
+    double2* fwd_out;         // operator mode: forward result [vis.n_pad]
+    double* adj_out;          // operator mode: adjoint result [pix.n_pad]
+};
+
+__host__ __device__ inline const double* fwd_input(const DevProblem& P)
+{
+    return P.xsel ? P.xpp[*P.xsel] : P.x;
+}
+
+// Stream-K plan of one launch over a set of problems.
+struct Plan {
+    int n_probs;
+    int C;                        // CTAs of the persistent grid
+    long long U;                  // total units
+    const long long* prob_u0;     // [n_probs+1] first unit of each problem
+    const int* prob_b0;           // [n_probs+1] first global block of each problem
+    const int* blk_poff;          // [n_blocks] first partial slot of the block
+    const int* blk_clo;           // [n_blocks] first CTA contributing to it
+    const int* blk_ncon;          // [n_blocks] contributing CTAs
+    int n_blocks;
+    int n_slots;
+};
+
+// Solver state of one problem (device resident, FP64 scalars).
+struct SolveState {
+    double lambda, L, tol;
+    double t;            // t_k of the momentum sequence (t_1 = 1)
+    double beta;         // (t_k - 1) / t_{k+1} of the step in flight
+    double E_prev;       // E(I_{k-1})
+    double E, resid2, l1;
+    long long nnz;
+    int k;               // FISTA steps completed
+    int max_iter;
+    int done;            // 1: finished (converged or max_iter)
+    int converged;
+    int nonfinite;       // 1: a non-finite value was met
+    // power iteration
+    double mu, mu_prev, inv_mu;
+    int pit, pmax;
+    double ptol;
+    int pdone;
+    int parity;          // k & 1 at the start of the step in flight
+};
+
+// Per-problem solver workspace (device pointers).
+struct SolveBufs {
+    double* I[2];        // I_k ping-pong [pix.n_pad]
+    double* y;           // y_k [pix.n_pad]
+    double* xv;          // power-iteration vector [pix.n_pad]
+    double2* AI[2];      // A I_k ping-pong [vis.n_pad]
+    double2* r;          // W (A y - V) [vis.n_pad]
+    double* blk_r2;      // [vis.n_blk] per-block sum W|A I - V|^2
+    double* blk_l1;      // [pix.n_blk] per-block sum I
+    double* blk_z2;      // [pix.n_blk] per-block sum z^2 (power)
+    int* blk_nnz;        // [pix.n_blk]
+    int* blk_badv;       // [vis.n_blk] non-finite flags
+    int* blk_badp;       // [pix.n_blk] non-finite flags
+    SolveState* st;
+};
+
+}  // namespace sl1m

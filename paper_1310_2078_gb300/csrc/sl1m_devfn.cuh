@@ -1,0 +1,82 @@
+// sl1m_devfn.cuh -- device helpers shared by the operator kernels (internal).
+#pragma once
+#include "sl1m_dev.h"
+
+namespace sl1m {
+
+#define TWO_PI_F 6.283185307179586f
+#define LOG2E_F 1.4426950408889634f
+
+// A tile (owned granule x streamed granule) whose offsets can make the FP32
+// product term D = (X - Xc).(Y - Yc) exceed D_MAX turns is evaluated with
+// the exact split instead (its FP32 rounding error grows like 2^-24 |D|).
+constexpr float D_MAX = 6.0f;
+
+// frac(a*b) in turns for a = ah + al, b = bh + bl: p + e == ah*bh exactly
+// (TwoProduct with one fma), p - rint(p) is exact, the cross terms are small.
+__device__ __forceinline__ float tp_frac(float ah, float al, float bh, float bl)
+{
+    const float p = __fmul_rn(ah, bh);
+    const float e = __fmaf_rn(ah, bh, -p);
+    const float f = __fsub_rn(p, rintf(p));
+    const float lo = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, e));
+    return __fadd_rn(f, lo);
+}
+
+// frac(a . b) over x, y, z in turns, result in [-0.5, 0.5].
+__device__ __forceinline__ float frac_dot3(const float4 ah, const float4 al,
+                                           const float4 bh, const float4 bl)
+{
+    float s = __fadd_rn(tp_frac(ah.x, al.x, bh.x, bl.x), tp_frac(ah.y, al.y, bh.y, bl.y));
+    s = __fadd_rn(s, tp_frac(ah.z, al.z, bh.z, bl.z));
+    return __fsub_rn(s, rintf(s));
+}
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float dot3(const float4 a, const float4 b)
+{
+    return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z));
+}
+
+// Largest p with prob_u0[p] <= u (problems with no units are skipped).
+__device__ __forceinline__ int find_prob(const Plan& pl, long long u)
+{
+    int lo = 0, hi = pl.n_probs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pl.prob_u0[mid] <= u) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int slot_of(const Plan& pl, int gblk)
+{
+    return pl.blk_poff[gblk] + ((int)blockIdx.x - pl.blk_clo[gblk]);
+}
+
+// Constants of one (visibility, Gaussian scale) pair, Eq. samlm4 in split form.
+struct GaussConst {
+    float beta, id, gam, coef;   // beta = w s^2, id = 1/(1+beta^2), gam = beta^2 id,
+                                 // coef = -pi s^2 id log2(e)
+    float cphase;                // id beta s^2 (u^2+v^2)/2, turns
+};
+
+__device__ __forceinline__ GaussConst gauss_const(float u, float v, float w, float sigma)
+{
+    GaussConst g;
+    const float s2 = sigma * sigma;
+    g.beta = w * s2;
+    g.id = 1.0f / fmaf(g.beta, g.beta, 1.0f);
+    g.gam = g.beta * g.beta * g.id;
+    g.coef = -3.14159265358979f * s2 * g.id * LOG2E_F;
+    g.cphase = 0.5f * g.id * g.beta * s2 * fmaf(u, u, v * v);
+    return g;
+}
+
+}  // namespace sl1m

@@ -1,0 +1,35 @@
+// sl1m_kernels.h -- launch wrappers of the libsl1m kernels (internal).
+#pragma once
+#include "sl1m_dev.h"
+
+namespace sl1m {
+
+enum FinishMode : int { FIN_OP = 0, FIN_POWER = 1, FIN_SOLVE = 2, FIN_INIT = 3 };
+
+// operator kernels (sl1m_ops.cu); precision 0 = FP64, 1 = mixed
+cudaError_t launch_forward(int precision, bool gains, int n_ant, const DevProblem* probs,
+                           const Plan& pl, double2* partial, cudaStream_t st);
+cudaError_t launch_adjoint(int precision, bool gains, const DevProblem* probs, const Plan& pl,
+                           double* partial, cudaStream_t st);
+// which: 0 fwd fp64, 1 adj fp64, 2 fwd mixed, 3 adj mixed
+int occupancy(int which, bool gains, int n_ant);
+int fwd_smem_bytes(int n_ant, bool gains);
+
+// solver kernels (sl1m_solver.cu)
+cudaError_t launch_gather_real(const double* src, double* dst, const int* orig, int n_pad,
+                               double scale, cudaStream_t st);
+cudaError_t launch_gather_cplx(const double2* src, double2* dst, const int* orig, int n_pad,
+                               cudaStream_t st);
+cudaError_t launch_scatter_real(const double* src, double* dst, const int* orig, int n_pad,
+                                cudaStream_t st);
+cudaError_t launch_scatter_cplx(const double2* src, double2* dst, const int* orig, int n_pad,
+                                cudaStream_t st);
+cudaError_t launch_fill_valid(double* dst, const int* orig, int n_pad, double val, cudaStream_t st);
+cudaError_t launch_fwd_finish(const DevProblem* probs, const SolveBufs* bufs, const Plan& pl,
+                              const double2* partial, int mode, cudaStream_t st);
+cudaError_t launch_adj_finish(const DevProblem* probs, const SolveBufs* bufs, const Plan& pl,
+                              const double* partial, int mode, cudaStream_t st);
+cudaError_t launch_scalars(const SolveBufs* bufs, const DevProblem* probs, int n_probs, int mode,
+                           cudaStream_t st);
+
+}  // namespace sl1m

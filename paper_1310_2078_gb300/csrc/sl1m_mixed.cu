@@ -1,0 +1,524 @@
+// sl1m_mixed.cu -- mixed-precision forward operator and adjoint of SL1M
+// (Hardy 2013, Sect. 2 and 3.1) as sm_103a kernels.
+//
+//   forward  Vhat_k = sum_j A_kj x_j                    (Eq. sme)
+//   adjoint  g_j    = sum_k Re(conj(A_kj) r_k)          (gradient, Sect. 3)
+//   A_kj = g_jk P_j exp(-2 pi i (u_k l_j + v_k m_j + w_k (n_j - 1)))
+//   Dirac pixels P = 1/n (Eq. deltam); Gaussian pixels (Eq. samlm4/samlm5) in
+//   the real split form
+//     A = (g/n) e^{Re(qc)} id (1 + i beta) exp(-2 pi i (phi_D - corr)),
+//     beta = w s^2, id = 1/(1+beta^2), gam = beta^2 id,
+//     Re(qc) = -pi s^2 id ((u - w l)^2 + (v - w m)^2),
+//     corr = [paraxial: w nu] + gam (u l + v m - w r^2/2) - id beta s^2 (u^2+v^2)/2,
+//     nu = n - 1 + r^2/2
+//   (no 1/sigma^2 prefactor; wide-field residual phase w (n - 1 + r^2/2)).
+//
+// Phase: with X the owned element, Y the streamed one and Xc, Yc their
+// granule centres,  X.Y = X.Yc + Xc.(Y - Yc) + (X - Xc).(Y - Yc) = C + B + D
+// exactly.  C (per owned element and streamed granule) and B (per owned
+// granule and streamed element) are reduced to fractional turns by an FP32
+// TwoProduct; D is one FP32 fma chain when the tile's offset extents bound
+// |D| <= D_MAX turns, else it is reduced exactly too.  sincos / exp2 run on
+// the SFU in FP32; each granule's FP32 sum is added into FP64 accumulators.
+//
+// Work split: a CTA owns BLK_GRAN granules of one side (one per warp, 2
+// elements per lane) and streams granules of the other side through shared
+// memory; units = (owned block, streamed granule) are spread over a
+// persistent grid stream-K style (Plan); partials are summed by the finish
+// kernels in a fixed order.
+#include "sl1m_dev.h"
+#include "sl1m_devfn.cuh"
+#include "sl1m_kernels.h"
+
+namespace sl1m {
+
+// ----------------------------------------------------------- forward tiles
+
+template <bool GAINS, bool EXACT>
+__device__ __forceinline__ void fwd_dirac_tile(const float4* __restrict__ s_off,
+                                               const float4* __restrict__ s_lo,
+                                               const float* __restrict__ sB,
+                                               const float2* __restrict__ s_gain, int n_ant,
+                                               const float4 (&dx)[2], const float4 (&dxl)[2],
+                                               const int2 (&ant)[2], float (&sr)[2], float (&si)[2])
+{
+#pragma unroll 4
+    for (int j = 0; j < G; ++j) {
+        const float4 o = s_off[j];             // {dl, dm, dn, a = x/n}
+        const float b = sB[j];
+        const float4 ol = EXACT ? s_lo[j] : o;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            float ph;
+            if (EXACT) ph = b + frac_dot3(dx[r], dxl[r], o, ol);
+            else ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, b)));
+            ph = ph - rintf(ph);
+            float sn, cs;
+            __sincosf(ph * TWO_PI_F, &sn, &cs);
+            if (GAINS) {
+                const float2 ga = s_gain[j * n_ant + ant[r].x];
+                const float2 gb = s_gain[j * n_ant + ant[r].y];
+                const float gr = fmaf(ga.x, gb.x, ga.y * gb.y);    // G_a conj(G_b)
+                const float gi = fmaf(ga.y, gb.x, -ga.x * gb.y);
+                sr[r] = fmaf(o.w, fmaf(gr, cs, gi * sn), sr[r]);    // a g (cs - i sn)
+                si[r] = fmaf(o.w, fmaf(gi, cs, -gr * sn), si[r]);
+            } else {
+                sr[r] = fmaf(o.w, cs, sr[r]);
+                si[r] = fmaf(-o.w, sn, si[r]);
+            }
+        }
+    }
+}
+
+template <bool GAINS, bool EXACT>
+__device__ __forceinline__ void fwd_gauss_tile(const float4* __restrict__ s_off,
+                                               const float4* __restrict__ s_lo,
+                                               const float4* __restrict__ s_pg,
+                                               const float* __restrict__ sB,
+                                               const float2* __restrict__ s_gain, int n_ant, bool par,
+                                               const float4 (&xh)[2], const float4 (&dx)[2],
+                                               const float4 (&dxl)[2], const GaussConst (&gc)[2],
+                                               const int2 (&ant)[2], float (&sr)[2], float (&si)[2])
+{
+#pragma unroll 2
+    for (int j = 0; j < G; ++j) {
+        const float4 o = s_off[j];
+        const float4 pg = s_pg[j];             // {l, m, r^2/2, nu}
+        const float b = sB[j];
+        const float4 ol = EXACT ? s_lo[j] : o;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const float uf = xh[r].x, vf = xh[r].y, wf = xh[r].z;
+            float ph;
+            if (EXACT) ph = b + frac_dot3(dx[r], dxl[r], o, ol);
+            else ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, b)));
+            const float t = fmaf(uf, pg.x, fmaf(vf, pg.y, -wf * pg.z));
+            ph = fmaf(-gc[r].gam, t, ph);
+            if (par) ph = fmaf(-wf, pg.w, ph);
+            ph = ph - rintf(ph);
+            float sn, cs;
+            __sincosf(ph * TWO_PI_F, &sn, &cs);
+            const float e1 = fmaf(-wf, pg.x, uf), e2 = fmaf(-wf, pg.y, vf);
+            const float amp = o.w * ex2_approx(gc[r].coef * fmaf(e1, e1, e2 * e2));
+            if (GAINS) {
+                const float2 ga = s_gain[j * n_ant + ant[r].x];
+                const float2 gb = s_gain[j * n_ant + ant[r].y];
+                const float gr = fmaf(ga.x, gb.x, ga.y * gb.y);
+                const float gi = fmaf(ga.y, gb.x, -ga.x * gb.y);
+                sr[r] = fmaf(amp, fmaf(gr, cs, gi * sn), sr[r]);
+                si[r] = fmaf(amp, fmaf(gi, cs, -gr * sn), si[r]);
+            } else {
+                sr[r] = fmaf(amp, cs, sr[r]);
+                si[r] = fmaf(-amp, sn, si[r]);
+            }
+        }
+    }
+}
+
+// Owned: visibilities (warp = one vis granule, lane = 2 visibilities).
+// Streamed: pixel granules through shared memory.
+template <bool GAINS>
+__global__ void __launch_bounds__(NTHREADS)
+fwd_mixed_kernel(const DevProblem* __restrict__ probs, Plan pl, double2* __restrict__ partial)
+{
+    __shared__ float4 s_off[G];            // {dl, dm, dn, a = x/n}
+    __shared__ float4 s_lo[G];             // offset residuals
+    __shared__ float4 s_pg[G];             // {l, m, r^2/2, nu}
+    __shared__ float s_B[BLK_GRAN][G];
+    __shared__ float4 s_cen[3];            // centre hi, lo, extent
+    extern __shared__ float2 s_gain[];     // GAINS: [G][n_ant]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long c = blockIdx.x;
+    long long u = (pl.U * c) / pl.C;
+    const long long u_end = (pl.U * (c + 1)) / pl.C;
+
+    while (u < u_end) {
+        const int p = find_prob(pl, u);
+        const DevProblem& P = probs[p];
+        const long long loc = u - pl.prob_u0[p];
+        if (P.done && *P.done) {                  // finished solve: skip its units
+            u = min(u_end, pl.prob_u0[p + 1]);
+            continue;
+        }
+        const int upb = P.pix.n_gran;
+        const int blk = (int)(loc / upb);
+        const int g0 = (int)(loc % upb);
+        const int g1 = (int)min((long long)upb, (long long)g0 + (u_end - u));
+        const int vg = blk * BLK_GRAN + warp;
+        const bool vg_ok = vg < P.vis.n_gran;
+        const int n_ant = P.n_ant;
+
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 xh[2] = {z4, z4}, xl[2] = {z4, z4}, dx[2] = {z4, z4}, dxl[2] = {z4, z4};
+        int2 ant[2] = {make_int2(0, 0), make_int2(0, 0)};
+        float4 ch = z4, cl = z4, ext = z4;
+        if (vg_ok) {
+            ch = P.vis.cen_hi[vg];
+            cl = P.vis.cen_lo[vg];
+            ext = P.vis.ext[vg];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int e = vg * G + lane + 32 * r;
+                xh[r] = P.vis.hi[e];
+                xl[r] = P.vis.lo[e];
+                dx[r] = P.vis.off[e];
+                dxl[r] = P.vis.offlo[e];
+                if (GAINS) ant[r] = P.ant[e];
+            }
+        }
+        const double xs = P.xscale ? *P.xscale : 1.0;
+        const double* X = fwd_input(P);
+        double tr[2] = {0.0, 0.0}, ti[2] = {0.0, 0.0};
+
+        for (int g = g0; g < g1; ++g) {
+            __syncthreads();                       // previous tile consumed
+            const int kind = P.gkind[g];
+            if (threadIdx.x < G) {
+                const int e = g * G + threadIdx.x;
+                float4 o = P.pix.off[e];
+                o.w = (float)(X[e] * xs * P.pix.d[e].w);     // x / n (0 on padding)
+                s_off[threadIdx.x] = o;
+                s_lo[threadIdx.x] = P.pix.offlo[e];
+                if (kind != DIRAC) s_pg[threadIdx.x] = P.pgauss[e];
+            } else if (threadIdx.x == G) {
+                s_cen[0] = P.pix.cen_hi[g];
+                s_cen[1] = P.pix.cen_lo[g];
+                s_cen[2] = P.pix.ext[g];
+            }
+            if (GAINS) {
+                const float2* src = P.gains32 + (size_t)g * G * n_ant;
+                for (int i = threadIdx.x; i < G * n_ant; i += NTHREADS) s_gain[i] = src[i];
+            }
+            __syncthreads();
+            // B_j = frac(Xc . (Y_j - Yc)) for this warp's granule centre
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = lane + 32 * h;
+                s_B[warp][j] = frac_dot3(ch, cl, s_off[j], s_lo[j]);
+            }
+            __syncwarp();
+            const float4 yc_h = s_cen[0], yc_l = s_cen[1];
+            const bool exact = dot3(ext, s_cen[2]) > D_MAX;       // warp-uniform
+            float C[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) C[r] = frac_dot3(xh[r], xl[r], yc_h, yc_l);
+            float sr[2] = {0.f, 0.f}, si[2] = {0.f, 0.f};
+            if (kind == DIRAC) {
+                if (exact)
+                    fwd_dirac_tile<GAINS, true>(s_off, s_lo, s_B[warp], s_gain, n_ant, dx, dxl, ant, sr, si);
+                else
+                    fwd_dirac_tile<GAINS, false>(s_off, s_lo, s_B[warp], s_gain, n_ant, dx, dxl, ant, sr, si);
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    float sn, cs;
+                    __sincosf(C[r] * TWO_PI_F, &sn, &cs);          // rotate by exp(-2 pi i C)
+                    tr[r] += (double)fmaf(cs, sr[r], sn * si[r]);
+                    ti[r] += (double)fmaf(cs, si[r], -sn * sr[r]);
+                }
+            } else {
+                const float sigma = P.gsig[g];
+                const bool par = (kind == PARAXIAL);
+                GaussConst gc[2];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    gc[r] = gauss_const(xh[r].x, xh[r].y, xh[r].z, sigma);
+                    const float cc = C[r] + gc[r].cphase;
+                    C[r] = cc - rintf(cc);
+                }
+                if (exact)
+                    fwd_gauss_tile<GAINS, true>(s_off, s_lo, s_pg, s_B[warp], s_gain, n_ant, par, xh, dx,
+                                                dxl, gc, ant, sr, si);
+                else
+                    fwd_gauss_tile<GAINS, false>(s_off, s_lo, s_pg, s_B[warp], s_gain, n_ant, par, xh, dx,
+                                                 dxl, gc, ant, sr, si);
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    // S id (1 + i beta), then rotate by exp(-2 pi i C)
+                    const float ar = gc[r].id * fmaf(-gc[r].beta, si[r], sr[r]);
+                    const float ai = gc[r].id * fmaf(gc[r].beta, sr[r], si[r]);
+                    float sn, cs;
+                    __sincosf(C[r] * TWO_PI_F, &sn, &cs);
+                    tr[r] += (double)fmaf(cs, ar, sn * ai);
+                    ti[r] += (double)fmaf(cs, ai, -sn * ar);
+                }
+            }
+        }
+        if (vg_ok) {
+            const int gb = pl.prob_b0[p] + blk;
+            double2* dst = partial + (size_t)slot_of(pl, gb) * BLK + warp * G + lane;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) dst[32 * r] = make_double2(tr[r], ti[r]);
+        }
+        u += g1 - g0;
+    }
+}
+
+// ----------------------------------------------------------- adjoint tiles
+
+template <bool GAINS, bool EXACT>
+__device__ __forceinline__ void adj_dirac_tile(const float4* __restrict__ s_off,
+                                               const float4* __restrict__ s_lo,
+                                               const float2* __restrict__ s_r,
+                                               const int2* __restrict__ s_ant,
+                                               const float* __restrict__ sB,
+                                               const float2* __restrict__ gains, int n_ant,
+                                               const int (&eidx)[2], const float (&C)[2],
+                                               const float4 (&dx)[2], const float4 (&dxl)[2],
+                                               float (&acc)[2])
+{
+#pragma unroll 4
+    for (int k = 0; k < G; ++k) {
+        const float4 o = s_off[k];             // {du, dv, dw, W}
+        const float b = sB[k];
+        const float2 rr = s_r[k];
+        const float4 ol = EXACT ? s_lo[k] : o;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            float ph;
+            if (EXACT) ph = (C[r] + b) + frac_dot3(dx[r], dxl[r], o, ol);
+            else ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, C[r] + b)));
+            ph = ph - rintf(ph);
+            float sn, cs;
+            __sincosf(ph * TWO_PI_F, &sn, &cs);           // exp(+2 pi i ph) = cs + i sn
+            if (GAINS) {
+                const int2 ab = s_ant[k];
+                const float2 ga = gains[(size_t)eidx[r] * n_ant + ab.x];
+                const float2 gb = gains[(size_t)eidx[r] * n_ant + ab.y];
+                const float gr = fmaf(ga.x, gb.x, ga.y * gb.y);
+                const float gi = fmaf(ga.y, gb.x, -ga.x * gb.y);
+                const float zr = fmaf(cs, rr.x, -sn * rr.y);
+                const float zi = fmaf(cs, rr.y, sn * rr.x);
+                acc[r] = fmaf(gr, zr, fmaf(gi, zi, acc[r]));  // Re(conj(g) z)
+            } else {
+                acc[r] = fmaf(cs, rr.x, fmaf(-sn, rr.y, acc[r]));
+            }
+        }
+    }
+}
+
+template <bool GAINS, bool EXACT>
+__device__ __forceinline__ void adj_gauss_tile(const float4* __restrict__ s_off,
+                                               const float4* __restrict__ s_lo,
+                                               const float4* __restrict__ s_abs,
+                                               const int2* __restrict__ s_ant,
+                                               const float* __restrict__ sB,
+                                               const float4* __restrict__ s_gw,
+                                               const float2* __restrict__ gains, int n_ant, bool par,
+                                               const int (&eidx)[2], const float (&C)[2],
+                                               const float4 (&dx)[2], const float4 (&dxl)[2],
+                                               const float4 (&pgd)[2], float (&acc)[2])
+{
+#pragma unroll 2
+    for (int k = 0; k < G; ++k) {
+        const float4 o = s_off[k];
+        const float4 va = s_abs[k];            // {u, v, w, -}
+        const float4 gw = s_gw[k];             // {gam, coef, r're, r'im}
+        const float b = sB[k];
+        const float4 ol = EXACT ? s_lo[k] : o;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            float ph;
+            if (EXACT) ph = (C[r] + b) + frac_dot3(dx[r], dxl[r], o, ol);
+            else ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, C[r] + b)));
+            const float t = fmaf(va.x, pgd[r].x, fmaf(va.y, pgd[r].y, -va.z * pgd[r].z));
+            ph = fmaf(-gw.x, t, ph);
+            if (par) ph = fmaf(-va.z, pgd[r].w, ph);
+            ph = ph - rintf(ph);
+            float sn, cs;
+            __sincosf(ph * TWO_PI_F, &sn, &cs);
+            const float e1 = fmaf(-va.z, pgd[r].x, va.x), e2 = fmaf(-va.z, pgd[r].y, va.y);
+            const float amp = ex2_approx(gw.y * fmaf(e1, e1, e2 * e2));
+            const float zr = fmaf(cs, gw.z, -sn * gw.w);
+            if (GAINS) {
+                const int2 ab = s_ant[k];
+                const float2 ga = gains[(size_t)eidx[r] * n_ant + ab.x];
+                const float2 gb = gains[(size_t)eidx[r] * n_ant + ab.y];
+                const float gr = fmaf(ga.x, gb.x, ga.y * gb.y);
+                const float gi = fmaf(ga.y, gb.x, -ga.x * gb.y);
+                const float zi = fmaf(cs, gw.w, sn * gw.z);
+                acc[r] = fmaf(amp, fmaf(gr, zr, gi * zi), acc[r]);
+            } else {
+                acc[r] = fmaf(amp, zr, acc[r]);
+            }
+        }
+    }
+}
+
+// Owned: pixels (warp = one pixel granule, lane = 2 pixels).
+// Streamed: visibility granules through shared memory.
+template <bool GAINS>
+__global__ void __launch_bounds__(NTHREADS)
+adj_mixed_kernel(const DevProblem* __restrict__ probs, Plan pl, double* __restrict__ partial)
+{
+    __shared__ float4 s_off[G];            // {du, dv, dw, W}
+    __shared__ float4 s_lo[G];
+    __shared__ float4 s_abs[G];            // {u, v, w, 0} (Gaussian owners)
+    __shared__ float2 s_r[G];
+    __shared__ int2 s_ant[G];
+    __shared__ float s_B[BLK_GRAN][G];
+    __shared__ float4 s_gw[BLK_GRAN][G];   // Gaussian owners: {gam, coef, r're, r'im}
+    __shared__ float4 s_cen[3];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long c = blockIdx.x;
+    long long u = (pl.U * c) / pl.C;
+    const long long u_end = (pl.U * (c + 1)) / pl.C;
+
+    while (u < u_end) {
+        const int p = find_prob(pl, u);
+        const DevProblem& P = probs[p];
+        const long long loc = u - pl.prob_u0[p];
+        if (P.done && *P.done) {
+            u = min(u_end, pl.prob_u0[p + 1]);
+            continue;
+        }
+        const int upb = P.vis.n_gran;
+        const int blk = (int)(loc / upb);
+        const int g0 = (int)(loc % upb);
+        const int g1 = (int)min((long long)upb, (long long)g0 + (u_end - u));
+        const int pgi = blk * BLK_GRAN + warp;
+        const bool pg_ok = pgi < P.pix.n_gran;
+        const int n_ant = P.n_ant;
+
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 xh[2] = {z4, z4}, xl[2] = {z4, z4}, dx[2] = {z4, z4}, dxl[2] = {z4, z4};
+        float4 pgd[2] = {z4, z4};
+        double invn[2] = {0.0, 0.0};
+        int eidx[2] = {0, 0};
+        float4 ch = z4, cl = z4, ext = z4;
+        int kind = DIRAC;
+        float sigma = 0.f;
+        if (pg_ok) {
+            ch = P.pix.cen_hi[pgi];
+            cl = P.pix.cen_lo[pgi];
+            ext = P.pix.ext[pgi];
+            kind = P.gkind[pgi];
+            sigma = P.gsig[pgi];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int e = pgi * G + lane + 32 * r;
+                eidx[r] = e;
+                xh[r] = P.pix.hi[e];
+                xl[r] = P.pix.lo[e];
+                dx[r] = P.pix.off[e];
+                dxl[r] = P.pix.offlo[e];
+                invn[r] = P.pix.d[e].w;
+                if (kind != DIRAC) pgd[r] = P.pgauss[e];
+            }
+        }
+        const bool gauss = (kind != DIRAC);
+        const bool par = (kind == PARAXIAL);
+        double tot[2] = {0.0, 0.0};
+
+        for (int g = g0; g < g1; ++g) {
+            __syncthreads();
+            if (threadIdx.x < G) {
+                const int e = g * G + threadIdx.x;
+                s_off[threadIdx.x] = P.vis.off[e];
+                s_lo[threadIdx.x] = P.vis.offlo[e];
+                s_abs[threadIdx.x] = P.vis.hi[e];
+                const double2 rr = P.r[e];
+                s_r[threadIdx.x] = make_float2((float)rr.x, (float)rr.y);
+                if (GAINS) s_ant[threadIdx.x] = P.ant[e];
+            } else if (threadIdx.x == G) {
+                s_cen[0] = P.vis.cen_hi[g];
+                s_cen[1] = P.vis.cen_lo[g];
+                s_cen[2] = P.vis.ext[g];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = lane + 32 * h;
+                float b = frac_dot3(ch, cl, s_off[k], s_lo[k]);
+                if (gauss) {
+                    const float4 va = s_abs[k];
+                    const GaussConst gc = gauss_const(va.x, va.y, va.z, sigma);
+                    b += gc.cphase;
+                    b -= rintf(b);
+                    const float2 rr = s_r[k];
+                    // r' = id (1 - i beta) r
+                    s_gw[warp][k] = make_float4(gc.gam, gc.coef, gc.id * fmaf(gc.beta, rr.y, rr.x),
+                                                gc.id * fmaf(-gc.beta, rr.x, rr.y));
+                }
+                s_B[warp][k] = b;
+            }
+            __syncwarp();
+            const float4 yc_h = s_cen[0], yc_l = s_cen[1];
+            const bool exact = dot3(ext, s_cen[2]) > D_MAX;
+            float C[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) C[r] = frac_dot3(xh[r], xl[r], yc_h, yc_l);
+            float acc[2] = {0.f, 0.f};
+            if (!gauss) {
+                if (exact)
+                    adj_dirac_tile<GAINS, true>(s_off, s_lo, s_r, s_ant, s_B[warp], P.gains32, n_ant, eidx, C,
+                                                dx, dxl, acc);
+                else
+                    adj_dirac_tile<GAINS, false>(s_off, s_lo, s_r, s_ant, s_B[warp], P.gains32, n_ant, eidx, C,
+                                                 dx, dxl, acc);
+            } else {
+                if (exact)
+                    adj_gauss_tile<GAINS, true>(s_off, s_lo, s_abs, s_ant, s_B[warp], s_gw[warp], P.gains32,
+                                                n_ant, par, eidx, C, dx, dxl, pgd, acc);
+                else
+                    adj_gauss_tile<GAINS, false>(s_off, s_lo, s_abs, s_ant, s_B[warp], s_gw[warp], P.gains32,
+                                                 n_ant, par, eidx, C, dx, dxl, pgd, acc);
+            }
+#pragma unroll
+            for (int r = 0; r < 2; ++r) tot[r] += (double)acc[r];
+        }
+        if (pg_ok) {
+            const int gb = pl.prob_b0[p] + blk;
+            double* dst = partial + (size_t)slot_of(pl, gb) * BLK + warp * G + lane;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) dst[32 * r] = tot[r] * invn[r];
+        }
+        u += g1 - g0;
+    }
+}
+
+// ------------------------------------------------------------- launchers
+
+int fwd_smem_bytes(int n_ant, bool gains) { return gains ? G * n_ant * (int)sizeof(float2) : 0; }
+
+cudaError_t launch_forward_mixed(bool gains, int n_ant, const DevProblem* probs, const Plan& pl,
+                                 double2* partial, cudaStream_t st)
+{
+    if (gains) {
+        const int sm = fwd_smem_bytes(n_ant, true);
+        cudaFuncSetAttribute(fwd_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        fwd_mixed_kernel<true><<<pl.C, NTHREADS, sm, st>>>(probs, pl, partial);
+    } else {
+        fwd_mixed_kernel<false><<<pl.C, NTHREADS, 0, st>>>(probs, pl, partial);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_mixed(bool gains, const DevProblem* probs, const Plan& pl, double* partial,
+                                 cudaStream_t st)
+{
+    if (gains) adj_mixed_kernel<true><<<pl.C, NTHREADS, 0, st>>>(probs, pl, partial);
+    else adj_mixed_kernel<false><<<pl.C, NTHREADS, 0, st>>>(probs, pl, partial);
+    return cudaGetLastError();
+}
+
+int occupancy_mixed(int op, bool gains, int n_ant)
+{
+    int n = 0;
+    if (op == 0) {
+        if (gains) {
+            const int sm = fwd_smem_bytes(n_ant, true);
+            cudaFuncSetAttribute(fwd_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fwd_mixed_kernel<true>, NTHREADS, sm);
+        } else {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fwd_mixed_kernel<false>, NTHREADS, 0);
+        }
+    } else {
+        if (gains) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adj_mixed_kernel<true>, NTHREADS, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adj_mixed_kernel<false>, NTHREADS, 0);
+    }
+    return n < 1 ? 1 : n;
+}
+
+}  // namespace sl1m

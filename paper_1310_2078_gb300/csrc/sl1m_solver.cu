@@ -1,0 +1,408 @@
+// sl1m_solver.cu -- the vector side of SL1M's FISTA (Hardy 2013, Sect. 3):
+// finishing the stream-K partial sums of the operator kernels, the residual
+// r = W (A y - V) and its norm, the positive soft threshold (Eq. threshp) and
+// the momentum step of the algorithm box, the power iteration for L, and the
+// per-problem FP64 scalars.  All reductions use a fixed order (deterministic,
+// no atomics).  These kernels are bound by HBM bandwidth.
+#include <math.h>
+
+#include "sl1m_dev.h"
+#include "sl1m_kernels.h"
+
+namespace sl1m {
+
+// ---------------------------------------------------------- permutations
+
+__global__ void gather_real_kernel(const double* __restrict__ src, double* __restrict__ dst,
+                                   const int* __restrict__ orig, int n_pad, double scale)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += gridDim.x * blockDim.x) {
+        const int o = orig[i];
+        dst[i] = o >= 0 ? src[o] * scale : 0.0;
+    }
+}
+
+__global__ void gather_cplx_kernel(const double2* __restrict__ src, double2* __restrict__ dst,
+                                   const int* __restrict__ orig, int n_pad)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += gridDim.x * blockDim.x) {
+        const int o = orig[i];
+        dst[i] = o >= 0 ? src[o] : make_double2(0.0, 0.0);
+    }
+}
+
+__global__ void scatter_real_kernel(const double* __restrict__ src, double* __restrict__ dst,
+                                    const int* __restrict__ orig, int n_pad)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += gridDim.x * blockDim.x) {
+        const int o = orig[i];
+        if (o >= 0) dst[o] = src[i];
+    }
+}
+
+__global__ void scatter_cplx_kernel(const double2* __restrict__ src, double2* __restrict__ dst,
+                                    const int* __restrict__ orig, int n_pad)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += gridDim.x * blockDim.x) {
+        const int o = orig[i];
+        if (o >= 0) dst[o] = src[i];
+    }
+}
+
+__global__ void fill_valid_kernel(double* __restrict__ dst, const int* __restrict__ orig, int n_pad,
+                                  double val)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += gridDim.x * blockDim.x)
+        dst[i] = orig[i] >= 0 ? val : 0.0;
+}
+
+static int grid_for(int n) { return n <= 0 ? 1 : (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096; }
+
+cudaError_t launch_gather_real(const double* src, double* dst, const int* orig, int n_pad,
+                               double scale, cudaStream_t st)
+{
+    gather_real_kernel<<<grid_for(n_pad), 256, 0, st>>>(src, dst, orig, n_pad, scale);
+    return cudaGetLastError();
+}
+cudaError_t launch_gather_cplx(const double2* src, double2* dst, const int* orig, int n_pad,
+                               cudaStream_t st)
+{
+    gather_cplx_kernel<<<grid_for(n_pad), 256, 0, st>>>(src, dst, orig, n_pad);
+    return cudaGetLastError();
+}
+cudaError_t launch_scatter_real(const double* src, double* dst, const int* orig, int n_pad,
+                                cudaStream_t st)
+{
+    scatter_real_kernel<<<grid_for(n_pad), 256, 0, st>>>(src, dst, orig, n_pad);
+    return cudaGetLastError();
+}
+cudaError_t launch_scatter_cplx(const double2* src, double2* dst, const int* orig, int n_pad,
+                                cudaStream_t st)
+{
+    scatter_cplx_kernel<<<grid_for(n_pad), 256, 0, st>>>(src, dst, orig, n_pad);
+    return cudaGetLastError();
+}
+cudaError_t launch_fill_valid(double* dst, const int* orig, int n_pad, double val, cudaStream_t st)
+{
+    fill_valid_kernel<<<grid_for(n_pad), 256, 0, st>>>(dst, orig, n_pad, val);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- helpers
+
+// t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2 and beta_k = (t_k - 1) / t_{k+1}
+// (the momentum step of the FISTA box).
+__device__ __forceinline__ void fista_beta(double t, double& t_next, double& beta)
+{
+    t_next = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    beta = (t - 1.0) / t_next;
+}
+
+__device__ __forceinline__ int find_blk_prob(const Plan& pl, int gb)
+{
+    int lo = 0, hi = pl.n_probs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pl.prob_b0[mid] <= gb) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Fixed-order block sum of one double per thread (256 threads).
+__device__ double block_sum(double v, double* sh)
+{
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ int block_sum_int(int v, int* sh)
+{
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    const int r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------- forward finish
+// One CTA per global owned block (BLK visibilities): sums the block's partial
+// slots in CTA order, then
+//   FIN_OP    : fwd_out = A x
+//   FIN_POWER : r = W (A x)                      (input of the next adjoint)
+//   FIN_INIT  : AI_0 = A I_0, r = W (A I_0 - V), block sum W|A I_0 - V|^2
+//   FIN_SOLVE : AI_k = A I_k, block sum W|A I_k - V|^2,
+//               A y_{k+1} = AI_k + beta_k (AI_k - AI_{k-1})  (linearity),
+//               r = W (A y_{k+1} - V)
+__global__ void __launch_bounds__(256)
+fwd_finish_kernel(const DevProblem* __restrict__ probs, const SolveBufs* __restrict__ bufs, Plan pl,
+                  const double2* __restrict__ partial, int mode)
+{
+    __shared__ double sh[256];
+    __shared__ int shi[256];
+    const int gb = blockIdx.x;
+    const int p = find_blk_prob(pl, gb);
+    const DevProblem& P = probs[p];
+    if (mode != FIN_INIT && P.done && *P.done) return;
+    const int blk = gb - pl.prob_b0[p];
+    const int poff = pl.blk_poff[gb], ncon = pl.blk_ncon[gb];
+    double beta = 0.0;
+    int par = 0;
+    if (mode == FIN_SOLVE) {
+        const SolveState& S = *bufs[p].st;
+        double tn;
+        fista_beta(S.t, tn, beta);
+        par = (S.k + 1) & 1;
+    }
+    double bn = 0.0;
+    int bad = 0;
+    for (int h = 0; h < 2; ++h) {
+        const int i = threadIdx.x + 256 * h;
+        const int e = blk * BLK + i;
+        if (e >= P.vis.n_pad) continue;
+        double2 s = make_double2(0.0, 0.0);
+        for (int c = 0; c < ncon; ++c) {
+            const double2 q = partial[(size_t)(poff + c) * BLK + i];
+            s.x += q.x;
+            s.y += q.y;
+        }
+        if (!isfinite(s.x) || !isfinite(s.y)) bad = 1;
+        if (mode == FIN_OP) {
+            P.fwd_out[e] = s;
+            continue;
+        }
+        const SolveBufs& B = bufs[p];
+        const double W = P.vis.d[e].w;
+        if (mode == FIN_POWER) {
+            B.r[e] = make_double2(W * s.x, W * s.y);
+            continue;
+        }
+        const double2 V = P.V[e];
+        const double dr = s.x - V.x, di = s.y - V.y;
+        bn += W * (dr * dr + di * di);
+        if (mode == FIN_INIT) {
+            B.AI[0][e] = s;
+            B.r[e] = make_double2(W * dr, W * di);
+        } else {
+            const double2 old = B.AI[par ^ 1][e];
+            B.AI[par][e] = s;
+            const double ayr = s.x + beta * (s.x - old.x);
+            const double ayi = s.y + beta * (s.y - old.y);
+            B.r[e] = make_double2(W * (ayr - V.x), W * (ayi - V.y));
+        }
+    }
+    if (mode == FIN_OP || mode == FIN_POWER) {
+        if (mode == FIN_POWER) {
+            const int nb = block_sum_int(bad, shi);
+            if (threadIdx.x == 0) bufs[p].blk_badv[blk] = nb;
+        }
+        return;
+    }
+    const double tot = block_sum(bn, sh);
+    const int nb = block_sum_int(bad, shi);
+    if (threadIdx.x == 0) {
+        bufs[p].blk_r2[blk] = tot;
+        bufs[p].blk_badv[blk] = nb;
+    }
+}
+
+// ---------------------------------------------------------- adjoint finish
+//   FIN_OP    : adj_out = Re A^H r
+//   FIN_POWER : z = Re A^H W A x into xv, block sum z^2
+//   FIN_SOLVE : I_k = T^{lambda/L}(y_k - g/L)                 (Eq. threshp)
+//               y_{k+1} = I_k + beta_k (I_k - I_{k-1})        (FISTA box)
+//               block sums of I_k and of nnz
+__global__ void __launch_bounds__(256)
+adj_finish_kernel(const DevProblem* __restrict__ probs, const SolveBufs* __restrict__ bufs, Plan pl,
+                  const double* __restrict__ partial, int mode)
+{
+    __shared__ double sh[256];
+    __shared__ int shi[256];
+    const int gb = blockIdx.x;
+    const int p = find_blk_prob(pl, gb);
+    const DevProblem& P = probs[p];
+    if (P.done && *P.done) return;
+    const int blk = gb - pl.prob_b0[p];
+    const int poff = pl.blk_poff[gb], ncon = pl.blk_ncon[gb];
+    double inv_L = 0.0, thr = 0.0, beta = 0.0;
+    int par = 0;
+    if (mode == FIN_SOLVE) {
+        const SolveState& S = *bufs[p].st;
+        double tn;
+        fista_beta(S.t, tn, beta);
+        inv_L = 1.0 / S.L;
+        thr = S.lambda / S.L;
+        par = (S.k + 1) & 1;
+        if (gb == pl.prob_b0[p] && threadIdx.x == 0) bufs[p].st->parity = par;
+    }
+    double acc = 0.0;
+    int cnt = 0, bad = 0;
+    for (int h = 0; h < 2; ++h) {
+        const int i = threadIdx.x + 256 * h;
+        const int e = blk * BLK + i;
+        if (e >= P.pix.n_pad) continue;
+        double s = 0.0;
+        for (int c = 0; c < ncon; ++c) s += partial[(size_t)(poff + c) * BLK + i];
+        if (!isfinite(s)) bad = 1;
+        if (mode == FIN_OP) {
+            P.adj_out[e] = s;
+            continue;
+        }
+        const SolveBufs& B = bufs[p];
+        if (mode == FIN_POWER) {
+            B.xv[e] = s;
+            acc += s * s;
+            continue;
+        }
+        // FIN_SOLVE
+        const double v = B.y[e] - s * inv_L;
+        double In = v > thr ? v - thr : 0.0;
+        if (P.pix.orig[e] < 0) In = 0.0;
+        const double Io = B.I[par ^ 1][e];
+        B.I[par][e] = In;
+        B.y[e] = In + beta * (In - Io);
+        acc += In;
+        cnt += In > 0.0;
+    }
+    if (mode == FIN_OP) return;
+    const double tot = block_sum(acc, sh);
+    const int nb = block_sum_int(bad, shi);
+    int nz = 0;
+    if (mode == FIN_SOLVE) nz = block_sum_int(cnt, shi);
+    if (threadIdx.x == 0) {
+        const SolveBufs& B = bufs[p];
+        if (mode == FIN_POWER) B.blk_z2[blk] = tot;
+        else {
+            B.blk_l1[blk] = tot;
+            B.blk_nnz[blk] = nz;
+        }
+        B.blk_badp[blk] = nb;
+    }
+}
+
+// ------------------------------------------------------------------ scalars
+// One warp per problem; fixed-order (lane-strided, then xor-tree) sums.
+__device__ double warp_sum_fixed(const double* a, int n)
+{
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) s += a[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+__device__ long long warp_sum_fixed_i(const int* a, int n)
+{
+    long long s = 0;
+    for (int i = threadIdx.x; i < n; i += 32) s += a[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+__global__ void scalars_kernel(const SolveBufs* __restrict__ bufs, const DevProblem* __restrict__ probs,
+                               int mode)
+{
+    const int p = blockIdx.x;
+    const SolveBufs& B = bufs[p];
+    const DevProblem& P = probs[p];
+    SolveState& S = *B.st;
+    const int nvb = P.vis.n_blk, npb = P.pix.n_blk;
+    if (mode == FIN_POWER) {
+        if (S.pdone) return;
+        const double z2 = warp_sum_fixed(B.blk_z2, npb);
+        const long long bad = warp_sum_fixed_i(B.blk_badv, nvb) + warp_sum_fixed_i(B.blk_badp, npb);
+        if (threadIdx.x == 0) {
+            const double mu = sqrt(z2);
+            S.pit += 1;
+            if (bad || !isfinite(mu)) {
+                S.nonfinite = 1;
+                S.pdone = 1;
+            } else {
+                if ((S.pit > 1 && fabs(mu - S.mu_prev) <= S.ptol * mu) || S.pit >= S.pmax || mu == 0.0)
+                    S.pdone = 1;
+            }
+            S.mu = mu;
+            S.mu_prev = mu;
+            S.inv_mu = mu > 0.0 ? 1.0 / mu : 0.0;
+        }
+        return;
+    }
+    if (mode == FIN_INIT) {
+        const double r2 = warp_sum_fixed(B.blk_r2, nvb);
+        const long long bad = warp_sum_fixed_i(B.blk_badv, nvb);
+        if (threadIdx.x == 0) {
+            S.resid2 = r2;
+            S.E_prev = 0.5 * r2 + S.lambda * S.l1;
+            S.E = S.E_prev;
+            S.k = 0;
+            S.t = 1.0;
+            S.converged = 0;
+            S.nonfinite = bad ? 1 : 0;
+            S.done = (S.max_iter <= 0 || bad) ? 1 : 0;
+        }
+        return;
+    }
+    // FIN_SOLVE
+    if (S.done) return;
+    const double r2 = warp_sum_fixed(B.blk_r2, nvb);
+    const double l1 = warp_sum_fixed(B.blk_l1, npb);
+    const long long nnz = warp_sum_fixed_i(B.blk_nnz, npb);
+    const long long bad = warp_sum_fixed_i(B.blk_badv, nvb) + warp_sum_fixed_i(B.blk_badp, npb);
+    if (threadIdx.x == 0) {
+        double tn, beta;
+        fista_beta(S.t, tn, beta);
+        const double E = 0.5 * r2 + S.lambda * l1;
+        S.k += 1;
+        S.t = tn;
+        S.beta = beta;
+        S.resid2 = r2;
+        S.l1 = l1;
+        S.nnz = nnz;
+        S.E = E;
+        if (bad || !isfinite(E)) {
+            S.nonfinite = 1;
+            S.done = 1;
+        }
+        if (S.tol > 0.0 && fabs(E - S.E_prev) <= S.tol * S.E_prev) {
+            S.converged = 1;
+            S.done = 1;
+        }
+        if (S.k >= S.max_iter) S.done = 1;
+        S.E_prev = E;
+    }
+}
+
+cudaError_t launch_fwd_finish(const DevProblem* probs, const SolveBufs* bufs, const Plan& pl,
+                              const double2* partial, int mode, cudaStream_t st)
+{
+    if (pl.n_blocks == 0) return cudaSuccess;
+    fwd_finish_kernel<<<pl.n_blocks, 256, 0, st>>>(probs, bufs, pl, partial, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_finish(const DevProblem* probs, const SolveBufs* bufs, const Plan& pl,
+                              const double* partial, int mode, cudaStream_t st)
+{
+    if (pl.n_blocks == 0) return cudaSuccess;
+    adj_finish_kernel<<<pl.n_blocks, 256, 0, st>>>(probs, bufs, pl, partial, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scalars(const SolveBufs* bufs, const DevProblem* probs, int n_probs, int mode,
+                           cudaStream_t st)
+{
+    if (n_probs <= 0) return cudaSuccess;
+    scalars_kernel<<<n_probs, 32, 0, st>>>(bufs, probs, mode);
+    return cudaGetLastError();
+}
+
+}  // namespace sl1m

@@ -1,0 +1,93 @@
+"""Host logic of libsl1m that needs no GPU: the stream-K work split and the
+k-d granule order (through the library's host-only entry points)."""
+import numpy as np
+import pytest
+
+from paper_1310_2078_gb300 import synth
+
+G = 64
+
+
+@pytest.fixture(scope="module")
+def sl1m():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1310_2078_gb300 import sl1m as s
+    return s
+
+
+CASES = [([1], [1], 608), ([5], [16], 608), ([79], [1024], 456), ([794], [16384], 456),
+         ([3, 0, 7, 2], [10, 5, 0, 33], 17), ([1, 1, 1], [1, 1, 1], 1000), ([12], [7], 5)]
+
+
+@pytest.mark.parametrize("nb,ns,cmax", CASES)
+def test_stream_k_plan_covers_every_unit_once(sl1m, nb, ns, cmax):
+    pv = sl1m.plan_preview(nb, ns, cmax)
+    U = sum(a * b for a, b in zip(nb, ns))
+    C = max(1, min(cmax, U))
+    assert pv["n_units"] == U and pv["n_ctas"] == C
+    # independent recomputation: CTA c takes [cU/C, (c+1)U/C)
+    lo = [(U * c) // C for c in range(C)]
+    hi = [(U * (c + 1)) // C for c in range(C)]
+    gb, slot = 0, 0
+    u0 = 0
+    for a, b in zip(nb, ns):
+        for blk in range(a):
+            s, e = u0 + blk * b, u0 + (blk + 1) * b
+            ctas = [c for c in range(C) if lo[c] < e and hi[c] > s] if b else []
+            assert pv["first_slot"][gb] == slot
+            if ctas:
+                assert pv["first_cta"][gb] == ctas[0]
+                assert pv["n_ctas_blk"][gb] == len(ctas) == ctas[-1] - ctas[0] + 1
+            else:
+                assert pv["n_ctas_blk"][gb] == 0
+            slot += len(ctas)
+            gb += 1
+        u0 += a * b
+    assert pv["n_slots"] == slot
+    # every unit is in exactly one CTA range
+    assert lo[0] == 0 and hi[-1] == U and all(hi[c] == lo[c + 1] for c in range(C - 1))
+
+
+def test_plan_rejects_bad_arguments(sl1m):
+    with pytest.raises(sl1m.SL1MError):
+        sl1m.plan_preview([1], [-1], 4)
+    with pytest.raises(sl1m.SL1MError):
+        sl1m.plan_preview([1], [1], 0)
+
+
+@pytest.mark.parametrize("n", [1, 63, 64, 65, 1000, 4097])
+def test_granule_order_is_a_padded_permutation(sl1m, n):
+    xy = np.random.default_rng(n).uniform(-1, 1, (n, 2))
+    order = sl1m.granule_order(xy)
+    assert len(order) == -(-n // G) * G
+    real = order[order >= 0]
+    assert sorted(real.tolist()) == list(range(n))
+    pad = np.flatnonzero(order < 0)
+    assert pad.size == len(order) - n
+    assert pad.size == 0 or pad[0] == n       # padding only in the last granule
+
+
+def test_granules_of_a_regular_grid_are_8x8_blocks(sl1m):
+    lm = synth.regular_grid(64, 0.5)
+    order = sl1m.granule_order(lm)
+    delta = 1.0 / 64
+    for g in range(len(order) // G):
+        pts = lm[order[g * G:(g + 1) * G]]
+        ext = np.ptp(pts, axis=0)
+        assert np.allclose(ext, 7 * delta)
+
+
+def test_granules_are_compact_for_uv_tracks(sl1m):
+    w = synth.config2(n_side=32)
+    order = sl1m.granule_order(w.uvw[:, :2])
+    ext = []
+    for g in range(len(order) // G):
+        idx = order[g * G:(g + 1) * G]
+        idx = idx[idx >= 0]
+        ext.append(np.ptp(w.uvw[idx, :2], axis=0).max())
+    rnd = np.random.default_rng(0).permutation(w.n_vis)
+    ext_rnd = [np.ptp(w.uvw[rnd[g * G:(g + 1) * G], :2], axis=0).max()
+               for g in range(w.n_vis // G)]
+    # k-d granules are more than an order of magnitude tighter than random ones
+    assert np.median(ext) < 0.1 * np.median(ext_rnd)
