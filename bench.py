@@ -45,12 +45,20 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--small", action="store_true",
+                    help="config 2 at 128x128 pixels (a small case for ncu captures)")
+    ap.add_argument("--n-side", type=int, default=0, help="override: pixel grid side")
+    ap.add_argument("--n-ant", type=int, default=0, help="override: antennas")
+    ap.add_argument("--n-times", type=int, default=0, help="override: snapshots")
     ap.add_argument("--iters", type=int, default=200)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--ops-only", action="store_true",
-                    help="profiling helper: run forward+adjoint pairs only (for ncu)")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving workload: Poisson stream of independent solves through the server")
+    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--fp64-sample", type=int, default=3)
     return ap.parse_args()
 
 
@@ -66,9 +74,14 @@ def dist_init():
     return ws, rank, local
 
 
-def workload(cfg: int, rank: int = 0):
+def workload(cfg: int, rank: int = 0, small: bool = False, args=None):
     from paper_1310_2078_gb300 import synth
-    w = synth.CONFIGS[cfg]()
+    kw = {}
+    if args is not None and cfg in (2, 4):
+        for k in ("n_side", "n_ant", "n_times"):
+            if getattr(args, k, 0):
+                kw[k] = getattr(args, k)
+    w = synth.config2(n_side=128) if small else synth.CONFIGS[cfg](**kw)
     if rank:
         # weak scaling: every rank solves its own independent problem of the same shape
         rng = synth.rng_for(synth.BASE_SEED + 100 * rank + cfg)
@@ -174,7 +187,7 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    w = workload(args.config)
+    w = workload(args.config, 0, args.small, args)
     O = oracle.Problem(w.uvw, w.lm, w.sigma, w.kind, w.weights, w.ant_pair, w.gains)
     rng = np.random.default_rng(0)
     x = np.abs(rng.normal(size=w.n_pix))
@@ -211,10 +224,90 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_serve(args):
+    """Continuous batching: `requests` independent solves arriving as a
+    Poisson stream (`rate` per second), each an independently generated
+    array/sky with 4k-256k pixels and 2k-100k visibilities, Dirac or wide
+    Gaussian pixels, gains on half of them; 200 FISTA steps or relative change
+    of E below 1e-6, L by power iteration.  Reports solves/s, p50/p99 latency
+    (submit to result), pairs/s, and the FP64 plain single-solve path on the
+    smallest requests (serial, same iterations) for comparison."""
+    import torch
+    from paper_1310_2078_gb300 import sl1m, synth
+    sl1m.load()
+    dev = 0
+    torch.cuda.set_device(dev)
+    reqs = [synth.serving_request(i) for i in range(args.requests)]
+    arrive = synth.arrivals(args.requests, args.rate)
+    ctx = sl1m.Context(dev)
+    # data: V = A x_true + noise through the library's forward (mixed), lambda from the dirty image
+    probs, lams = [], []
+    for w in reqs:
+        P = sl1m.problem_from(ctx, w)
+        V = P.forward(w.x_true, sl1m.MIXED) + w.noise
+        P.set_vis_data(V)
+        lams.append(w.lambda_frac * P.adjoint(V, sl1m.MIXED).max())
+        probs.append((P, V))
+    torch.cuda.synchronize()
+    ctx.counters_reset()
+    ctx.server_start(max_slots=64, ticks_per_round=4)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    t0 = time.perf_counter()
+    tickets = []
+    for i, (P, V) in enumerate(probs):
+        dt = t0 + arrive[i] - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(ctx.server_submit(P, lams[i], L=0.0, max_iter=200, rel_tol=1e-6))
+    results = [ctx.server_wait(t, probs[i][0], timeout_s=-1.0) for i, t in enumerate(tickets)]
+    T = time.perf_counter() - t0
+    clk = clocks.stop()
+    info = ctx.server_info()
+    ctx.server_stop()
+    lat = np.array([st["seconds"] for _, st in results])
+    pairs = sum((2 * st["power_iters"] + 2 * st["iters"] + 2) * float(w.n_vis) * w.n_pix
+                for (_, st), w in zip(results, reqs))
+    # FP64 plain single-solve path on the smallest requests (serial, same iterations)
+    order = np.argsort([w.pairs for w in reqs])[:args.fp64_sample]
+    cmp = []
+    for i in order:
+        P, V = probs[i]
+        st_m = results[i][1]
+        t1 = time.perf_counter()
+        img64, st64 = P.solve(lams[i], L=st_m["L"], max_iter=st_m["iters"], precision=sl1m.FP64)
+        t64 = time.perf_counter() - t1
+        t1 = time.perf_counter()
+        imgm, stm = P.solve(lams[i], L=st_m["L"], max_iter=st_m["iters"], precision=sl1m.MIXED)
+        tm = time.perf_counter() - t1
+        cmp.append({"request": int(i), "n_pix": reqs[i].n_pix, "n_vis": reqs[i].n_vis,
+                    "iters": st_m["iters"], "fp64_s": t64, "mixed_alone_s": tm,
+                    "E_rel_diff": abs(stm["E"] - st64["E"]) / st64["E"],
+                    "img_err_of_peak": float(np.max(np.abs(imgm - img64)) / max(img64.max(), 1e-300))})
+    fp64_solves_per_s = len(cmp) / sum(c["fp64_s"] for c in cmp) if cmp else None
+    out = {"metric": "solves/s (continuous batching, mixed precision)", "value": args.requests / T,
+           "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32+f64",
+           "data": "synthetic",
+           "config": {"workload": f"serving: {args.requests} requests, Poisson {args.rate}/s, "
+                                  "pixels logU(4k,256k), visibilities logU(2k,100k), "
+                                  "Dirac/wide-Gaussian 50/50, gains on 50%",
+                      "max_slots": 64, "ticks_per_round": 4},
+           "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                         "mean": float(lat.mean()), "max": float(lat.max())},
+           "pairs_per_s": pairs / T, "wall_s": T,
+           "iters_mean": float(np.mean([st["iters"] for _, st in results])),
+           "server": info, "clocks": clk, "gpu_launches": ctx.counters()["launches"],
+           "fp64_plain_single_solve": {"sample": cmp, "solves_per_s_on_sample": fp64_solves_per_s}}
+    print(json.dumps(out))
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        return run_serve(args)
     import torch
     ws, rank, local = dist_init()
     from paper_1310_2078_gb300 import sl1m
@@ -222,7 +315,7 @@ def main():
     dev = local
     torch.cuda.set_device(dev)
     prec = sl1m.MIXED if args.precision == "mixed" else sl1m.FP64
-    w = workload(args.config, rank)
+    w = workload(args.config, rank, args.small, args)
     stream = torch.cuda.Stream(device=dev)
     ctx = sl1m.Context(dev, stream=stream)
     # synthetic visibilities: V = A x_true + noise, formed by the library's own forward

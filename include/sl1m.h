@@ -166,6 +166,54 @@ typedef struct {
 int sl1m_solve(sl1m_problem* prob, const sl1m_solve_opts* opts, double* img_out,
                sl1m_solve_stats* stats);
 
+/* ---- Continuous-batching solve server ---------------------------------------
+ * Independent solves (the paper solves every channel and polarisation on
+ * its own, Sect. 2 and 4.2) share the same forward and adjoint launches:
+ * a request loop on a host thread admits queued solves as batch slots and the
+ * device-memory budget allow, runs every admitted solve one FISTA step (or one
+ * power-iteration step) per tick inside one captured CUDA graph, and retires
+ * finished solves between rounds.  A request that arrives while others run
+ * joins the next round.  While a server runs on a context, the operator and
+ * solve calls of that context return SL1M_ERR_BUSY. */
+typedef struct {
+    int64_t mem_budget_bytes;   /* 0 = 80% of the device memory free at start   */
+    int32_t max_slots;          /* 0 = 64 concurrent solves                      */
+    int32_t ticks_per_round;    /* 0 = 8 steps between admission/retirement     */
+    int32_t precision;          /* SL1M_MIXED or SL1M_FP64 for every request     */
+} sl1m_server_opts;
+
+/* Start the request loop (opts may be NULL for defaults). */
+int sl1m_server_start(sl1m_ctx* ctx, const sl1m_server_opts* opts);
+
+/* Queue a solve of `prob` with `opts` (opts->precision is ignored; the server's
+ * applies; opts->x0 is copied).  The problem must not be changed or destroyed
+ * until its result has been collected with sl1m_server_wait.  SL1M_ERR_BUSY if
+ * the problem alone exceeds the memory budget. */
+int sl1m_server_submit(sl1m_ctx* ctx, sl1m_problem* prob, const sl1m_solve_opts* opts, uint64_t* ticket);
+
+/* done = 1 once the request has finished (successfully or not). */
+int sl1m_server_poll(sl1m_ctx* ctx, uint64_t ticket, int* done);
+
+/* Wait at most timeout_s seconds (< 0: no limit) for the request, then copy
+ * its image (img_out [n_pix], may be NULL) and stats (stats->seconds = time
+ * from submit to completion) and release the ticket.  SL1M_ERR_TIMEOUT if it
+ * has not finished in time (the ticket stays valid). */
+int sl1m_server_wait(sl1m_ctx* ctx, uint64_t ticket, double timeout_s, double* img_out,
+                     sl1m_solve_stats* stats);
+
+/* Finish every queued and running request, then stop the request loop.
+ * Results not yet collected remain collectable with sl1m_server_wait until
+ * the context is destroyed or a new server is started. */
+int sl1m_server_stop(sl1m_ctx* ctx);
+
+/* Counters of the running (or last) server. */
+typedef struct {
+    int64_t queued, active, finished, max_active;
+    int64_t bytes_in_use, bytes_budget;
+    int64_t ticks, rounds;
+} sl1m_server_info_t;
+int sl1m_server_info(sl1m_ctx* ctx, sl1m_server_info_t* info);
+
 /* Kernel timing with CUDA events on the context's stream (for benchmarks).
  * Kernel ids: 0 forward FP64, 1 adjoint FP64, 2 forward mixed, 3 adjoint
  * mixed, 4 forward finish, 5 adjoint finish (solver vector updates), 6 other.

@@ -61,36 +61,95 @@ struct Side {
 // vis: x,y,z = u,v,w (wavelengths); aux = weight W_k (0 for padding)
 // pix: x,y,z = l, m, n-1 (n-1 = -(l^2+m^2)/(1+n)); aux = 1/n (0 for padding)
 
+// Phases of one solve, advanced on the device by the scalars kernel at the
+// end of every tick (one tick = adjoint, adjoint finish, forward, forward
+// finish, scalars for every problem of a batch):
+//   PINIT  forward of x = 1/sqrt(n) -> r = W A x
+//   POWER  power-iteration step: z = B x_unit, then r = W A z; mu = ||z||
+//   SINIT  forward of I_0 -> A I_0, r = W (A I_0 - V), E_0
+//   SOLVE  one FISTA step (Sect. 3 algorithm box)
+//   DONE   finished (converged, max_iter reached, or non-finite)
+enum Phase : int { PH_IDLE = 0, PH_PINIT = 1, PH_POWER = 2, PH_SINIT = 3, PH_SOLVE = 4, PH_DONE = 5 };
+
+// Solver state of one problem (device resident, FP64 scalars).
+struct SolveState {
+    double lambda, L, tol;
+    double t;            // t_k of the momentum sequence (t_1 = 1)
+    double beta;         // (t_k - 1) / t_{k+1} of the last step
+    double E_prev;       // E(I_{k-1})
+    double E, resid2, l1;
+    long long nnz;
+    int k;               // FISTA steps completed
+    int max_iter;
+    int phase;
+    int converged;
+    int nonfinite;       // 1: a non-finite value was met
+    int power_only;      // 1: stop after the power iteration (L only)
+    // power iteration
+    double mu, mu_prev, inv_mu;
+    int pit, pmax;
+    double ptol;
+};
+
+// Per-problem solver workspace (device pointers).
+struct SolveBufs {
+    double* I[2];        // I_k ping-pong [pix.n_pad]
+    double* y;           // y_k [pix.n_pad]
+    double* xv;          // power-iteration vector [pix.n_pad]
+    double2* AI[2];      // A I_k ping-pong [vis.n_pad]
+    double2* r;          // W (A y - V), or W A x in the power iteration [vis.n_pad]
+    double* blk_r2;      // [vis.n_blk] per-block sum W|A I - V|^2
+    double* blk_l1;      // [pix.n_blk] per-block sum I
+    double* blk_z2;      // [pix.n_blk] per-block sum z^2 (power)
+    int* blk_nnz;        // [pix.n_blk]
+    int* blk_badv;       // [vis.n_blk] non-finite flags
+    int* blk_badp;       // [pix.n_blk] non-finite flags
+};
+
 struct DevProblem {
     Side vis;
     Side pix;
     const int2* ant;          // [vis.n_pad] antenna pair (a, b)
     const double2* V;         // [vis.n_pad] measured visibilities (sorted)
     const float4* pgauss;     // [pix.n_pad] {l, m, (l^2+m^2)/2, nu = n-1+(l^2+m^2)/2}
-    const d4* pgauss64;  // same in FP64
-    const float* gsig;        // [pix.n_gran] sigma per pixel granule
+    const d4* pgauss64;       // same in FP64
+    const float* gsig;        // [pix.n_gran] sigma per pixel granule (FP32 path)
+    const double* gsig64;     // [pix.n_gran] sigma per pixel granule (FP64 path)
     const int* gkind;         // [pix.n_gran] kind per pixel granule
     const float2* gains32;    // [pix.n_pad][n_ant] or null
     const double2* gains64;   // [pix.n_pad][n_ant] or null
     int n_ant;
-    int active;               // 0: skip this problem in batched launches
-    // per-launch operands (sorted layouts)
-    const double* x;          // forward input  [pix.n_pad]
-    const double* xpp[2];     // solve mode: forward input is xpp[*xsel]
-    const int* xsel;          // null: use x
-    const double* xscale;     // optional device scalar multiplying x (power iteration)
-    const double2* r;         // adjoint input  [vis.n_pad]
-    const int* done;          // optional device flag: 1 = problem finished, skip its units
-    double2* fwd_out;         // operator mode: forward result [vis.n_pad]
-    double* adj_out;          // operator mode: adjoint result [pix.n_pad]
+    // operator mode (st == null): one forward x -> fwd_out or adjoint r -> adj_out
+    const double* x;          // [pix.n_pad]
+    const double2* r;         // [vis.n_pad]
+    double2* fwd_out;         // [vis.n_pad]
+    double* adj_out;          // [pix.n_pad]
+    // solver mode
+    SolveState* st;
+    SolveBufs b;
 };
 
-__host__ __device__ inline const double* fwd_input(const DevProblem& P)
+// Forward input of problem P in this launch (false: P takes no part).
+__device__ __forceinline__ bool fwd_role(const DevProblem& P, const double*& X)
 {
-    return P.xsel ? P.xpp[*P.xsel] : P.x;
+    if (!P.st) { X = P.x; return true; }
+    const int ph = P.st->phase;
+    if (ph == PH_PINIT || ph == PH_POWER) { X = P.b.xv; return true; }
+    if (ph == PH_SINIT) { X = P.b.I[0]; return true; }
+    if (ph == PH_SOLVE) { X = P.b.I[(P.st->k + 1) & 1]; return true; }
+    return false;
 }
 
-// Stream-K plan of one launch over a set of problems.
+// Adjoint input of problem P in this launch (false: P takes no part).
+__device__ __forceinline__ bool adj_role(const DevProblem& P, const double2*& R)
+{
+    if (!P.st) { R = P.r; return true; }
+    const int ph = P.st->phase;
+    if (ph == PH_POWER || ph == PH_SOLVE) { R = P.b.r; return true; }
+    return false;
+}
+
+// Stream-K plan of one launch over a batch of problems (device resident).
 struct Plan {
     int n_probs;
     int C;                        // CTAs of the persistent grid
@@ -102,43 +161,6 @@ struct Plan {
     const int* blk_ncon;          // [n_blocks] contributing CTAs
     int n_blocks;
     int n_slots;
-};
-
-// Solver state of one problem (device resident, FP64 scalars).
-struct SolveState {
-    double lambda, L, tol;
-    double t;            // t_k of the momentum sequence (t_1 = 1)
-    double beta;         // (t_k - 1) / t_{k+1} of the step in flight
-    double E_prev;       // E(I_{k-1})
-    double E, resid2, l1;
-    long long nnz;
-    int k;               // FISTA steps completed
-    int max_iter;
-    int done;            // 1: finished (converged or max_iter)
-    int converged;
-    int nonfinite;       // 1: a non-finite value was met
-    // power iteration
-    double mu, mu_prev, inv_mu;
-    int pit, pmax;
-    double ptol;
-    int pdone;
-    int parity;          // k & 1 at the start of the step in flight
-};
-
-// Per-problem solver workspace (device pointers).
-struct SolveBufs {
-    double* I[2];        // I_k ping-pong [pix.n_pad]
-    double* y;           // y_k [pix.n_pad]
-    double* xv;          // power-iteration vector [pix.n_pad]
-    double2* AI[2];      // A I_k ping-pong [vis.n_pad]
-    double2* r;          // W (A y - V) [vis.n_pad]
-    double* blk_r2;      // [vis.n_blk] per-block sum W|A I - V|^2
-    double* blk_l1;      // [pix.n_blk] per-block sum I
-    double* blk_z2;      // [pix.n_blk] per-block sum z^2 (power)
-    int* blk_nnz;        // [pix.n_blk]
-    int* blk_badv;       // [vis.n_blk] non-finite flags
-    int* blk_badp;       // [pix.n_blk] non-finite flags
-    SolveState* st;
 };
 
 }  // namespace sl1m

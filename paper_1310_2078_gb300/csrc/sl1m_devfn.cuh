@@ -12,13 +12,21 @@ namespace sl1m {
 // the exact split instead (its FP32 rounding error grows like 2^-24 |D|).
 constexpr float D_MAX = 6.0f;
 
+// x - rint(x) for |x| < 2^22, exact: adding and removing 1.5 * 2^23 rounds x
+// to the nearest integer (ties to even) on the FP32 add pipe.
+__device__ __forceinline__ float frac_turns(float x)
+{
+    const float M = 12582912.0f;
+    return __fsub_rn(x, __fsub_rn(__fadd_rn(x, M), M));
+}
+
 // frac(a*b) in turns for a = ah + al, b = bh + bl: p + e == ah*bh exactly
 // (TwoProduct with one fma), p - rint(p) is exact, the cross terms are small.
 __device__ __forceinline__ float tp_frac(float ah, float al, float bh, float bl)
 {
     const float p = __fmul_rn(ah, bh);
     const float e = __fmaf_rn(ah, bh, -p);
-    const float f = __fsub_rn(p, rintf(p));
+    const float f = __fsub_rn(p, rintf(p));   // |p| may exceed 2^22: exact rint
     const float lo = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, e));
     return __fadd_rn(f, lo);
 }
@@ -29,7 +37,7 @@ __device__ __forceinline__ float frac_dot3(const float4 ah, const float4 al,
 {
     float s = __fadd_rn(tp_frac(ah.x, al.x, bh.x, bl.x), tp_frac(ah.y, al.y, bh.y, bl.y));
     s = __fadd_rn(s, tp_frac(ah.z, al.z, bh.z, bl.z));
-    return __fsub_rn(s, rintf(s));
+    return frac_turns(s);
 }
 
 __device__ __forceinline__ float ex2_approx(float x)

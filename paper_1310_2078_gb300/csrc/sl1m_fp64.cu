@@ -37,11 +37,12 @@ __device__ __forceinline__ void entry_phase64(int kind, double sigma, double u, 
 }
 
 __global__ void __launch_bounds__(NTHREADS)
-fwd_fp64_kernel(const DevProblem* __restrict__ probs, Plan pl, double2* __restrict__ partial)
+fwd_fp64_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ plp, double2* __restrict__ partial)
 {
     __shared__ d4 s_pd[G];    // {l, m, n-1, a = x/n}
     __shared__ d4 s_pg[G];    // {l, m, r^2/2, nu}
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Plan pl = *plp;
     const long long c = blockIdx.x;
     long long u = (pl.U * c) / pl.C;
     const long long u_end = (pl.U * (c + 1)) / pl.C;
@@ -49,7 +50,8 @@ fwd_fp64_kernel(const DevProblem* __restrict__ probs, Plan pl, double2* __restri
         const int p = find_prob(pl, u);
         const DevProblem& P = probs[p];
         const long long loc = u - pl.prob_u0[p];
-        if (P.done && *P.done) {                  // finished solve: skip its units
+        const double* X;
+        if (!fwd_role(P, X)) {                    // problem not in this step: skip its units
             u = min(u_end, pl.prob_u0[p + 1]);
             continue;
         }
@@ -71,17 +73,15 @@ fwd_fp64_kernel(const DevProblem* __restrict__ probs, Plan pl, double2* __restri
                 if (P.gains64) ant[r] = P.ant[e];
             }
         }
-        const double xs = P.xscale ? *P.xscale : 1.0;
-        const double* X = fwd_input(P);
         double tr[2] = {0.0, 0.0}, ti[2] = {0.0, 0.0};
         for (int g = g0; g < g1; ++g) {
             __syncthreads();
             const int kind = P.gkind[g];
-            const double sigma = P.gsig[g];
+            const double sigma = P.gsig64[g];
             if (threadIdx.x < G) {
                 const int e = g * G + threadIdx.x;
                 d4 d = P.pix.d[e];
-                d.w = X[e] * xs * d.w;
+                d.w = X[e] * d.w;
                 s_pd[threadIdx.x] = d;
                 if (kind != DIRAC) s_pg[threadIdx.x] = P.pgauss64[e];
             }
@@ -123,12 +123,13 @@ fwd_fp64_kernel(const DevProblem* __restrict__ probs, Plan pl, double2* __restri
 }
 
 __global__ void __launch_bounds__(NTHREADS)
-adj_fp64_kernel(const DevProblem* __restrict__ probs, Plan pl, double* __restrict__ partial)
+adj_fp64_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ plp, double* __restrict__ partial)
 {
     __shared__ d4 s_vd[G];    // {u, v, w, W}
     __shared__ double2 s_r[G];
     __shared__ int2 s_ant[G];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Plan pl = *plp;
     const long long c = blockIdx.x;
     long long u = (pl.U * c) / pl.C;
     const long long u_end = (pl.U * (c + 1)) / pl.C;
@@ -136,7 +137,8 @@ adj_fp64_kernel(const DevProblem* __restrict__ probs, Plan pl, double* __restric
         const int p = find_prob(pl, u);
         const DevProblem& P = probs[p];
         const long long loc = u - pl.prob_u0[p];
-        if (P.done && *P.done) {                  // finished solve: skip its units
+        const double2* R;
+        if (!adj_role(P, R)) {                    // problem not in this step: skip its units
             u = min(u_end, pl.prob_u0[p + 1]);
             continue;
         }
@@ -147,7 +149,7 @@ adj_fp64_kernel(const DevProblem* __restrict__ probs, Plan pl, double* __restric
         const int pgi = blk * BLK_GRAN + warp;
         const bool pg_ok = pgi < P.pix.n_gran;
         const int kind = pg_ok ? P.gkind[pgi] : DIRAC;
-        const double sigma = pg_ok ? (double)P.gsig[pgi] : 0.0;
+        const double sigma = pg_ok ? P.gsig64[pgi] : 0.0;
         d4 pd[2], pg[2];
         int eidx[2] = {0, 0};
 #pragma unroll
@@ -166,7 +168,7 @@ adj_fp64_kernel(const DevProblem* __restrict__ probs, Plan pl, double* __restric
             if (threadIdx.x < G) {
                 const int e = g * G + threadIdx.x;
                 s_vd[threadIdx.x] = P.vis.d[e];
-                s_r[threadIdx.x] = P.r[e];
+                s_r[threadIdx.x] = R[e];
                 if (P.gains64) s_ant[threadIdx.x] = P.ant[e];
             }
             __syncthreads();
@@ -208,34 +210,30 @@ adj_fp64_kernel(const DevProblem* __restrict__ probs, Plan pl, double* __restric
 
 // ------------------------------------------------------------- launchers
 
-// ------------------------------------------------------------- launchers
-
-cudaError_t launch_forward_mixed(bool gains, int n_ant, const DevProblem* probs, const Plan& pl,
+cudaError_t launch_forward_mixed(bool gains, int n_ant, const DevProblem* probs, const Plan* plp, int C,
                                  double2* partial, cudaStream_t st);
-cudaError_t launch_adjoint_mixed(bool gains, const DevProblem* probs, const Plan& pl, double* partial,
-                                 cudaStream_t st);
+cudaError_t launch_adjoint_mixed(bool gains, const DevProblem* probs, const Plan* plp, int C,
+                                 double* partial, cudaStream_t st);
 int occupancy_mixed(int op, bool gains, int n_ant);
 
 cudaError_t launch_forward(int precision, bool gains, int n_ant, const DevProblem* probs,
-                           const Plan& pl, double2* partial, cudaStream_t st)
+                           const Plan* plp, int C, double2* partial, cudaStream_t st)
 {
-    if (pl.U == 0) return cudaSuccess;
     if (precision == 0) {
-        fwd_fp64_kernel<<<pl.C, NTHREADS, 0, st>>>(probs, pl, partial);
+        fwd_fp64_kernel<<<C, NTHREADS, 0, st>>>(probs, plp, partial);
         return cudaGetLastError();
     }
-    return launch_forward_mixed(gains, n_ant, probs, pl, partial, st);
+    return launch_forward_mixed(gains, n_ant, probs, plp, C, partial, st);
 }
 
-cudaError_t launch_adjoint(int precision, bool gains, const DevProblem* probs, const Plan& pl,
+cudaError_t launch_adjoint(int precision, bool gains, const DevProblem* probs, const Plan* plp, int C,
                            double* partial, cudaStream_t st)
 {
-    if (pl.U == 0) return cudaSuccess;
     if (precision == 0) {
-        adj_fp64_kernel<<<pl.C, NTHREADS, 0, st>>>(probs, pl, partial);
+        adj_fp64_kernel<<<C, NTHREADS, 0, st>>>(probs, plp, partial);
         return cudaGetLastError();
     }
-    return launch_adjoint_mixed(gains, probs, pl, partial, st);
+    return launch_adjoint_mixed(gains, probs, plp, C, partial, st);
 }
 
 int occupancy(int which, bool gains, int n_ant)

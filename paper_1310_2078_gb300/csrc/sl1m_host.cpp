@@ -240,7 +240,7 @@ cudaError_t build_plan(const std::vector<int>& nb, const std::vector<int>& ns, i
     D.pl.blk_ncon = D.ncon.p;
     D.pl.n_blocks = H.n_blocks;
     D.pl.n_slots = H.n_slots;
-    return cudaSuccess;
+    return D.dpl.upload(&D.pl, 1, st);
 }
 
 // ================================================================ profiling
@@ -296,6 +296,7 @@ sl1m_ctx::~sl1m_ctx()
     cudaSetDevice(device);
     drain_profile();
     for (auto e : ev_pool) cudaEventDestroy(e);
+    if (upstream) cudaStreamDestroy(upstream);
     if (own_stream && stream) cudaStreamDestroy(stream);
 }
 
@@ -308,6 +309,7 @@ struct ProblemDev {
     DBuf<float4> pgauss;
     DBuf<d4> pgauss64;
     DBuf<float> gsig;
+    DBuf<double> gsig64;
     DBuf<int> gkind;
     DBuf<float2> gains32;
     DBuf<double2> gains64;
@@ -319,13 +321,11 @@ struct ProblemDev {
     DBuf<double2> AI0, AI1, rr;
     DBuf<int> blk_nnz, blk_badv, blk_badp;
     DBuf<SolveState> st;
-    DBuf<SolveBufs> bufs;
-    DBuf<DevProblem> desc;
 };
 
-struct sl1m_problem_impl {};
+sl1m_problem::~sl1m_problem() = default;
 
-int sl1m_problem::rebuild()
+int sl1m_problem::rebuild(cudaStream_t st)
 {
     if (!dirty) return SL1M_OK;
     if (n_vis <= 0 || n_pix <= 0)
@@ -338,7 +338,6 @@ int sl1m_problem::rebuild()
                 return sl1m_fail(ctx, SL1M_ERR_ARG, "antenna index out of range at visibility %lld",
                                  (long long)k);
     }
-    cudaStream_t st = ctx->stream;
     if (!dev) dev = std::make_unique<ProblemDev>();
     ProblemDev& D = *dev;
     // ---- visibilities: k-d order on (u, v)
@@ -349,8 +348,7 @@ int sl1m_problem::rebuild()
         kd_append(order, std::move(members), uvw.data(), uvw.data() + 1, 3);
         std::vector<d4> xyz(n_vis);
         for (int64_t k = 0; k < n_vis; ++k)
-            xyz[k] = make_d4(uvw[3 * k], uvw[3 * k + 1], uvw[3 * k + 2],
-                                  weights.empty() ? 1.0 : weights[k]);
+            xyz[k] = make_d4(uvw[3 * k], uvw[3 * k + 1], uvw[3 * k + 2], weights.empty() ? 1.0 : weights[k]);
         HostSide H;
         layout_side(order, xyz, (int)n_vis, H);
         CK(upload_side(H, D.vis, hp.vis, st));
@@ -371,10 +369,9 @@ int sl1m_problem::rebuild()
         std::vector<std::pair<std::pair<int, double>, int>> cls(n_pix);
         for (int64_t j = 0; j < n_pix; ++j)
             cls[j] = {{kind.empty() ? 0 : kind[j], sigma.empty() ? 0.0 : sigma[j]}, (int)j};
-        std::stable_sort(cls.begin(), cls.end(),
-                         [](const auto& a, const auto& b) { return a.first < b.first; });
+        std::stable_sort(cls.begin(), cls.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
         std::vector<int> order;
-        std::vector<std::pair<int, float>> gran_cls;
+        std::vector<std::pair<int, double>> gran_cls;
         size_t i = 0;
         while (i < cls.size()) {
             size_t j = i;
@@ -383,7 +380,7 @@ int sl1m_problem::rebuild()
             const size_t before = order.size();
             kd_append(order, std::move(members), lm.data(), lm.data() + 1, 2);
             for (size_t g = before / G; g < order.size() / G; ++g)
-                gran_cls.push_back({cls[i].first.first, (float)cls[i].first.second});
+                gran_cls.push_back({cls[i].first.first, cls[i].first.second});
             i = j;
         }
         std::vector<d4> xyz(n_pix);
@@ -406,14 +403,19 @@ int sl1m_problem::rebuild()
         CK(D.pgauss.upload(pg.data(), pg.size(), st));
         CK(D.pgauss64.upload(pg64.data(), pg64.size(), st));
         std::vector<float> gs(H.n_gran);
+        std::vector<double> gs64(H.n_gran);
         std::vector<int> gk(H.n_gran);
-        for (int g = 0; g < H.n_gran; ++g) { gk[g] = gran_cls[g].first; gs[g] = gran_cls[g].second; }
+        has_gauss = false;
+        for (int g = 0; g < H.n_gran; ++g) {
+            gk[g] = gran_cls[g].first;
+            gs64[g] = gran_cls[g].second;
+            gs[g] = (float)gs64[g];
+            has_gauss |= gk[g] != DIRAC;
+        }
         CK(D.gsig.upload(gs.data(), gs.size(), st));
+        CK(D.gsig64.upload(gs64.data(), gs64.size(), st));
         CK(D.gkind.upload(gk.data(), gk.size(), st));
         pix_orig = H.orig;
-        has_gauss = false;
-        for (int g = 0; g < H.n_gran; ++g) has_gauss |= gk[g] != DIRAC;
-        // gains in sorted pixel order
         if (n_ant > 0) {
             std::vector<float2> g32((size_t)H.n_pad * n_ant, make_float2(0.f, 0.f));
             std::vector<double2> g64((size_t)H.n_pad * n_ant, make_double2(0.0, 0.0));
@@ -438,93 +440,39 @@ int sl1m_problem::rebuild()
     hp.pgauss = D.pgauss.p;
     hp.pgauss64 = D.pgauss64.p;
     hp.gsig = D.gsig.p;
+    hp.gsig64 = D.gsig64.p;
     hp.gkind = D.gkind.p;
     hp.gains32 = n_ant > 0 ? D.gains32.p : nullptr;
     hp.gains64 = n_ant > 0 ? D.gains64.p : nullptr;
     hp.n_ant = n_ant;
-    hp.active = 1;
+    hp.x = nullptr;
+    hp.r = nullptr;
+    hp.fwd_out = nullptr;
+    hp.adj_out = nullptr;
+    hp.st = nullptr;
     ctx->h2d += (long long)dev_bytes();
-    plans.clear();
+    for (auto& b : op_batch) b.reset();
+    for (auto& b : solve_batch) b.reset();
     solver_ready = false;
-    desc_valid = false;
     dirty = false;
-    return SL1M_OK;
-}
-
-// Plan for (op 0 = forward / 1 = adjoint, precision) of this single problem.
-int sl1m_problem::plan(int op, int precision, const Plan** out)
-{
-    const bool gains = n_ant > 0;
-    const int key = op * 4 + precision * 2 + (gains ? 1 : 0);
-    auto it = plans.find(key);
-    if (it == plans.end()) {
-        const int which = (precision == 0 ? 0 : 2) + op;
-        const int occ = occupancy(which, gains, n_ant);
-        auto D = std::make_unique<DevPlan>();
-        std::vector<int> nb(1), ns(1);
-        nb[0] = op == 0 ? hp.vis.n_blk : hp.pix.n_blk;
-        ns[0] = op == 0 ? hp.pix.n_gran : hp.vis.n_gran;
-        CK(build_plan(nb, ns, ctx->num_sms * occ, *D, ctx->stream));
-        it = plans.emplace(key, std::move(D)).first;
-    }
-    *out = &it->second->pl;
-    const size_t need = (size_t)std::max(1, it->second->pl.n_slots) * BLK;
-    if (op == 0) CK(ctx->partial_f.reserve(need, ctx->stream));
-    else CK(ctx->partial_a.reserve(need, ctx->stream));
-    return SL1M_OK;
-}
-
-// Copy the descriptor to the device only when it changed since the last
-// launch (a solve keeps one descriptor for all its iterations).
-int sl1m_problem::upload_desc()
-{
-    if (desc_valid && memcmp(&hp, &last_desc, sizeof hp) == 0) return SL1M_OK;
-    CK(dev->desc.reserve(1, ctx->stream));
-    CK(cudaMemcpyAsync(dev->desc.p, &hp, sizeof hp, cudaMemcpyHostToDevice, ctx->stream));
-    memcpy(&last_desc, &hp, sizeof hp);
-    desc_valid = true;
     return SL1M_OK;
 }
 
 double sl1m_problem::pairs() const { return (double)n_vis * (double)n_pix; }
 
-// Forward on sorted device input x_sorted (already gathered) -> fwd_sorted.
-int sl1m_problem::run_forward(int precision, int fin_mode, const SolveBufs* bufs_dev)
+// Device bytes a problem will hold once laid out with solver buffers
+// (admission estimate; padded sizes, ~100 B per element and side).
+size_t sl1m_problem::estimate_bytes() const
 {
-    const Plan* pl;
-    RET(plan(0, precision, &pl));
-    RET(upload_desc());
-    ProfTok tk;
-    prof_begin(ctx, precision == 0 ? 0 : 2, tk);
-    CKL(launch_forward(precision, n_ant > 0, n_ant, dev->desc.p, *pl, ctx->partial_f.p, ctx->stream));
-    prof_end(ctx, tk, pairs(), 0.0);
-    prof_begin(ctx, 4, tk);
-    CKL(launch_fwd_finish(dev->desc.p, bufs_dev, *pl, ctx->partial_f.p, fin_mode, ctx->stream));
-    // finish bytes: partial slots + per-vis state traffic
-    const double vb = (double)hp.vis.n_pad;
-    const double fb = (double)pl->n_slots * BLK * 16.0 + vb * (fin_mode == FIN_SOLVE ? 16 * 5 + 32 : 16 + 32);
-    prof_end(ctx, tk, 0.0, fb);
-    return SL1M_OK;
+    const size_t nv = (size_t)((n_vis + G - 1) / G) * G, np = (size_t)((n_pix + G - 1) / G) * G;
+    size_t b = nv * (4 * 16 + 32 + 4 + 8 + 16) + np * (4 * 16 + 32 + 4 + 16 + 32);
+    b += (size_t)n_ant * np * (8 + 16);
+    b += np * 8 * 4 + nv * 16 * 3;                 // solver vectors
+    b += (nv + np) * 16 * 3;                       // operator scratch
+    return b + (1 << 16);
 }
 
-int sl1m_problem::run_adjoint(int precision, int fin_mode, const SolveBufs* bufs_dev)
-{
-    const Plan* pl;
-    RET(plan(1, precision, &pl));
-    RET(upload_desc());
-    ProfTok tk;
-    prof_begin(ctx, precision == 0 ? 1 : 3, tk);
-    CKL(launch_adjoint(precision, n_ant > 0, dev->desc.p, *pl, ctx->partial_a.p, ctx->stream));
-    prof_end(ctx, tk, pairs(), 0.0);
-    prof_begin(ctx, 5, tk);
-    CKL(launch_adj_finish(dev->desc.p, bufs_dev, *pl, ctx->partial_a.p, fin_mode, ctx->stream));
-    const double pb = (double)hp.pix.n_pad;
-    const double ab = (double)pl->n_slots * BLK * 8.0 + pb * (fin_mode == FIN_SOLVE ? 8 * 5 + 4 : 8);
-    prof_end(ctx, tk, 0.0, ab);
-    return SL1M_OK;
-}
-
-int sl1m_problem::ensure_solver()
+int sl1m_problem::ensure_solver(cudaStream_t st)
 {
     if (solver_ready) return SL1M_OK;
     ProblemDev& D = *dev;
@@ -543,69 +491,318 @@ int sl1m_problem::ensure_solver()
     b.AI[0] = D.AI0.p; b.AI[1] = D.AI1.p; b.r = D.rr.p;
     b.blk_r2 = D.blk_r2.p; b.blk_l1 = D.blk_l1.p; b.blk_z2 = D.blk_z2.p;
     b.blk_nnz = D.blk_nnz.p; b.blk_badv = D.blk_badv.p; b.blk_badp = D.blk_badp.p;
-    b.st = D.st.p;
     hbufs = b;
-    CK(D.bufs.upload(&b, 1, ctx->stream));
-    CK(cudaMemsetAsync(D.blk_badp.p, 0, sizeof(int) * std::max(1, hp.pix.n_blk), ctx->stream));
-    CK(cudaMemsetAsync(D.blk_badv.p, 0, sizeof(int) * std::max(1, hp.vis.n_blk), ctx->stream));
+    CK(cudaMemsetAsync(D.blk_badp.p, 0, sizeof(int) * std::max(1, hp.pix.n_blk), st));
+    CK(cudaMemsetAsync(D.blk_badv.p, 0, sizeof(int) * std::max(1, hp.vis.n_blk), st));
     solver_ready = true;
     return SL1M_OK;
 }
 
-void sl1m_problem::reset_operands()
+DevProblem sl1m_problem::solver_desc() const
 {
-    hp.x = nullptr;
-    hp.xpp[0] = hp.xpp[1] = nullptr;
-    hp.xsel = nullptr;
-    hp.xscale = nullptr;
-    hp.r = nullptr;
-    hp.done = nullptr;
-    hp.fwd_out = nullptr;
-    hp.adj_out = nullptr;
+    DevProblem d = hp;
+    d.x = nullptr;
+    d.r = nullptr;
+    d.fwd_out = nullptr;
+    d.adj_out = nullptr;
+    d.st = dev->st.p;
+    d.b = hbufs;
+    return d;
 }
 
-// Power iteration on sorted device vectors; st must be allocated.
-int sl1m_problem::power(int precision, int max_iter, double tol, double* L, int* iters)
+// Step 0 of the algorithm box (y_1 = I_0 = x0, t_1 = 1) and the start of the
+// power iteration (x = 1/sqrt(n_pix)); phase PINIT when L is to be computed,
+// SINIT when it is given.
+int sl1m_problem::init_solve(const sl1m_solve_opts* o, double L, bool power_only, cudaStream_t st)
 {
-    RET(ensure_solver());
+    RET(ensure_solver(st));
     ProblemDev& D = *dev;
+    double l1_0 = 0.0;
+    const size_t np = hp.pix.n_pad;
+    if (o && o->x0) {
+        CK(D.x_user.reserve(n_pix, st));
+        CK(cudaMemcpyAsync(D.x_user.p, o->x0, sizeof(double) * n_pix, cudaMemcpyHostToDevice, st));
+        CKL(launch_gather_real(D.x_user.p, D.I0.p, hp.pix.orig, hp.pix.n_pad, 1.0, st));
+        for (int64_t j = 0; j < n_pix; ++j) l1_0 += o->x0[j];
+        ctx->h2d += (long long)sizeof(double) * n_pix;
+    } else {
+        CK(cudaMemsetAsync(D.I0.p, 0, sizeof(double) * np, st));
+    }
+    CK(cudaMemcpyAsync(D.y.p, D.I0.p, sizeof(double) * np, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(D.I1.p, D.I0.p, sizeof(double) * np, cudaMemcpyDeviceToDevice, st));
+    CKL(launch_fill_valid(D.xv.p, hp.pix.orig, hp.pix.n_pad, 1.0 / std::sqrt((double)n_pix), st));
     SolveState s0;
     memset(&s0, 0, sizeof s0);
+    s0.lambda = o ? o->lambda : 0.0;
+    s0.L = L;
+    s0.tol = o ? o->rel_tol : 0.0;
+    s0.t = 1.0;
+    s0.l1 = l1_0;
+    s0.max_iter = o ? o->max_iter : 0;
     s0.inv_mu = 1.0;
-    s0.pmax = max_iter;
-    s0.ptol = tol;
-    CK(cudaMemcpyAsync(D.st.p, &s0, sizeof s0, cudaMemcpyHostToDevice, ctx->stream));
-    CKL(launch_fill_valid(D.xv.p, hp.pix.orig, hp.pix.n_pad, 1.0 / std::sqrt((double)n_pix), ctx->stream));
-    reset_operands();
-    hp.x = D.xv.p;
-    hp.xscale = &D.st.p->inv_mu;
-    hp.r = D.rr.p;
-    hp.done = &D.st.p->pdone;
-    const int check = 8;
-    SolveState sh;
-    for (int it = 0; it < max_iter; it += check) {
-        for (int q = 0; q < check && it + q < max_iter; ++q) {
-            RET(run_forward(precision, FIN_POWER, D.bufs.p));
-            RET(run_adjoint(precision, FIN_POWER, D.bufs.p));
-            CKL(launch_scalars(D.bufs.p, D.desc.p, 1, FIN_POWER, ctx->stream));
-        }
-        CK(cudaMemcpyAsync(&sh, D.st.p, sizeof sh, cudaMemcpyDeviceToHost, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
-        if (sh.pdone) break;
-    }
-    reset_operands();
-    if (sh.nonfinite) return sl1m_fail(ctx, SL1M_ERR_NONFINITE, "non-finite value in power iteration");
-    if (!(sh.mu > 0.0)) return sl1m_fail(ctx, SL1M_ERR_ARG, "operator is zero (all weights zero?)");
-    *L = sh.mu;
-    if (iters) *iters = sh.pit;
+    s0.pmax = (o && o->power_max_iter > 0) ? o->power_max_iter : 50;
+    s0.ptol = (o && o->power_tol > 0) ? o->power_tol : 1e-6;
+    s0.power_only = power_only ? 1 : 0;
+    s0.phase = (L > 0.0 && !power_only) ? PH_SINIT : PH_PINIT;
+    CK(cudaMemcpyAsync(D.st.p, &s0, sizeof s0, cudaMemcpyHostToDevice, st));
+    // the host struct is a temporary: finish the copy before returning
+    CK(cudaStreamSynchronize(st));
     return SL1M_OK;
 }
 
-// ================================================================ C ABI
+int sl1m_problem::read_state(SolveState& s, cudaStream_t st)
+{
+    CK(cudaMemcpyAsync(&s, dev->st.p, sizeof s, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return SL1M_OK;
+}
 
+// Copy the last I_k (sorted, in I[k & 1]) to the caller's order on the host.
+int sl1m_problem::fetch_image(double* host_out, cudaStream_t st)
+{
+    SolveState s;
+    RET(read_state(s, st));
+    ProblemDev& D = *dev;
+    double* Ik = (s.k & 1) ? D.I1.p : D.I0.p;
+    CK(D.img_user.reserve(n_pix, st));
+    CKL(launch_scatter_real(Ik, D.img_user.p, hp.pix.orig, hp.pix.n_pad, st));
+    CK(cudaMemcpyAsync(host_out, D.img_user.p, sizeof(double) * n_pix, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    ctx->d2h += (long long)sizeof(double) * n_pix;
+    return SL1M_OK;
+}
+
+size_t sl1m_problem::dev_bytes() const
+{
+    if (!dev) return 0;
+    const ProblemDev& D = *dev;
+    size_t b = 0;
+    auto side = [&](const DevSide& s) {
+        b += s.hi.bytes() + s.lo.bytes() + s.off.bytes() + s.offlo.bytes() + s.cen_hi.bytes() +
+             s.cen_lo.bytes() + s.ext.bytes() + s.d.bytes() + s.orig.bytes();
+    };
+    side(D.vis);
+    side(D.pix);
+    b += D.ant.bytes() + D.V.bytes() + D.pgauss.bytes() + D.pgauss64.bytes() + D.gsig.bytes() +
+         D.gsig64.bytes() + D.gkind.bytes() + D.gains32.bytes() + D.gains64.bytes();
+    b += D.x_user.bytes() + D.x_sorted.bytes() + D.adj_sorted.bytes() + D.img_user.bytes() +
+         D.r_user.bytes() + D.r_sorted.bytes() + D.fwd_sorted.bytes() + D.vis_user.bytes();
+    b += D.I0.bytes() + D.I1.bytes() + D.y.bytes() + D.xv.bytes() + D.blk_r2.bytes() + D.blk_l1.bytes() +
+         D.blk_z2.bytes() + D.AI0.bytes() + D.AI1.bytes() + D.rr.bytes() + D.blk_nnz.bytes() +
+         D.blk_badv.bytes() + D.blk_badp.bytes() + D.st.bytes();
+    return b;
+}
+
+// ================================================================ batches
+
+Batch::~Batch()
+{
+    if (gexec) cudaGraphExecDestroy(gexec);
+}
+
+// Set the problems of a batch: descriptors, per (op, gains class) plans,
+// partial-sum scratch.  The captured tick stays valid while every pointer it
+// bakes in (tables, scratch) is unchanged.
+int batch_set(sl1m_ctx* ctx, Batch& B, const std::vector<sl1m_problem*>& probs,
+              const std::vector<DevProblem>& descs, int precision, bool solver)
+{
+    cudaStream_t st = ctx->stream;
+    const int np = (int)probs.size();
+    if (np == 0) return sl1m_fail(ctx, SL1M_ERR_ARG, "empty batch");
+    const void* old_ptrs[6] = {B.desc.p, ctx->partial_f.p, ctx->partial_a.p, B.n_probs_dev.p,
+                               B.plan[0][0].dpl.p, B.plan[1][1].dpl.p};
+    const bool same_set = B.probs == probs && B.precision == precision && B.solver == solver;
+    B.precision = precision;
+    B.solver = solver;
+    B.probs = probs;
+    B.hdesc = descs;
+    if (B.desc.n < (size_t)np) CK(B.desc.reserve(np, st));
+    CK(cudaMemcpyAsync(B.desc.p, B.hdesc.data(), sizeof(DevProblem) * np, cudaMemcpyHostToDevice, st));
+    if (!B.n_probs_dev.p) CK(B.n_probs_dev.alloc(1));
+    CK(cudaMemcpyAsync(B.n_probs_dev.p, &np, sizeof(int), cudaMemcpyHostToDevice, st));
+    if (B.phases_dev.n < (size_t)np) CK(B.phases_dev.reserve(np, st));
+    if (!same_set) {
+        B.has_class[0] = B.has_class[1] = false;
+        B.n_ant_max = 0;
+        B.pairs_class[0] = B.pairs_class[1] = 0;
+        B.fin_bytes[0] = B.fin_bytes[1] = 0;
+        for (int c = 0; c < 2; ++c) {
+            std::vector<int> nbf(np), nsf(np), nba(np), nsa(np);
+            for (int p = 0; p < np; ++p) {
+                const bool g = probs[p]->n_ant > 0;
+                const bool in = (c == 1) == g;
+                const DevProblem& d = descs[p];
+                nbf[p] = in ? d.vis.n_blk : 0;
+                nsf[p] = in ? d.pix.n_gran : 0;
+                nba[p] = in ? d.pix.n_blk : 0;
+                nsa[p] = in ? d.vis.n_gran : 0;
+                if (in) {
+                    B.has_class[c] = true;
+                    B.pairs_class[c] += probs[p]->pairs();
+                    if (g) B.n_ant_max = std::max(B.n_ant_max, probs[p]->n_ant);
+                }
+            }
+            const int occf = occupancy(precision == 0 ? 0 : 2, c == 1, std::max(1, B.n_ant_max));
+            const int occa = occupancy(precision == 0 ? 1 : 3, c == 1, std::max(1, B.n_ant_max));
+            CK(build_plan(nbf, nsf, ctx->num_sms * occf, B.plan[0][c], st));
+            CK(build_plan(nba, nsa, ctx->num_sms * occa, B.plan[1][c], st));
+            CK(ctx->partial_f.reserve((size_t)std::max(1, B.plan[0][c].pl.n_slots) * BLK, st));
+            CK(ctx->partial_a.reserve((size_t)std::max(1, B.plan[1][c].pl.n_slots) * BLK, st));
+            B.fin_bytes[0] += (double)B.plan[0][c].pl.n_slots * BLK * 16.0;
+            B.fin_bytes[1] += (double)B.plan[1][c].pl.n_slots * BLK * 8.0;
+        }
+        int nblk = 0;
+        for (int p = 0; p < np; ++p) {
+            nblk = std::max({nblk, descs[p].vis.n_blk, descs[p].pix.n_blk});
+            B.fin_bytes[0] += descs[p].vis.n_pad * (solver ? 16.0 * 5 + 32 : 48.0);
+            B.fin_bytes[1] += descs[p].pix.n_pad * (solver ? 8.0 * 5 + 4 : 8.0);
+        }
+        B.fin_grid = std::max(1, std::min(4 * ctx->num_sms, nblk * np));
+        B.sc_grid = std::max(1, std::min(ctx->num_sms * 4, np));
+    }
+    const void* new_ptrs[6] = {B.desc.p, ctx->partial_f.p, ctx->partial_a.p, B.n_probs_dev.p,
+                               B.plan[0][0].dpl.p, B.plan[1][1].dpl.p};
+    if (!same_set || memcmp(old_ptrs, new_ptrs, sizeof old_ptrs) != 0) B.graph_ok = false;
+    return SL1M_OK;
+}
+
+static int launch_op_class(sl1m_ctx* ctx, Batch& B, int op, int c)
+{
+    if (!B.has_class[c]) return SL1M_OK;
+    cudaStream_t st = ctx->stream;
+    const DevPlan& P = B.plan[op][c];
+    ProfTok tk;
+    if (op == 0) {
+        prof_begin(ctx, B.precision == 0 ? 0 : 2, tk);
+        CKL(launch_forward(B.precision, c == 1, B.n_ant_max, B.desc.p, P.dpl.p, P.pl.C, ctx->partial_f.p, st));
+        prof_end(ctx, tk, B.pairs_class[c], 0.0);
+        prof_begin(ctx, 4, tk);
+        CKL(launch_fwd_finish(B.desc.p, P.dpl.p, std::min(B.fin_grid, std::max(1, P.pl.n_blocks)),
+                              ctx->partial_f.p, st));
+        prof_end(ctx, tk, 0.0, B.fin_bytes[0]);
+    } else {
+        prof_begin(ctx, B.precision == 0 ? 1 : 3, tk);
+        CKL(launch_adjoint(B.precision, c == 1, B.desc.p, P.dpl.p, P.pl.C, ctx->partial_a.p, st));
+        prof_end(ctx, tk, B.pairs_class[c], 0.0);
+        prof_begin(ctx, 5, tk);
+        CKL(launch_adj_finish(B.desc.p, P.dpl.p, std::min(B.fin_grid, std::max(1, P.pl.n_blocks)),
+                              ctx->partial_a.p, st));
+        prof_end(ctx, tk, 0.0, B.fin_bytes[1]);
+    }
+    return SL1M_OK;
+}
+
+// One operator application (operator-mode batch): forward or adjoint.
+int batch_op(sl1m_ctx* ctx, Batch& B, int op)
+{
+    for (int c = 0; c < 2; ++c) RET(launch_op_class(ctx, B, op, c));
+    return SL1M_OK;
+}
+
+// One tick of every solve of a solver-mode batch: adjoint, adjoint finish,
+// forward, forward finish (per gains class), then the phase machine.
+static int enqueue_tick(sl1m_ctx* ctx, Batch& B)
+{
+    for (int c = 0; c < 2; ++c) RET(launch_op_class(ctx, B, 1, c));
+    for (int c = 0; c < 2; ++c) RET(launch_op_class(ctx, B, 0, c));
+    CKL(launch_scalars(B.desc.p, B.n_probs_dev.p, B.sc_grid, ctx->stream));
+    return SL1M_OK;
+}
+
+// n ticks; replayed from a captured CUDA graph unless profiling (events per
+// kernel) or graphs are off.
+int batch_ticks(sl1m_ctx* ctx, Batch& B, int n)
+{
+    if (!ctx->use_graphs || ctx->prof) {
+        for (int i = 0; i < n; ++i) RET(enqueue_tick(ctx, B));
+        return SL1M_OK;
+    }
+    if (!B.graph_ok) {
+        if (B.gexec) {
+            cudaGraphExecDestroy(B.gexec);
+            B.gexec = nullptr;
+        }
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        const long long l0 = ctx->n_launch;
+        const int rc = enqueue_tick(ctx, B);
+        const cudaError_t ec = cudaStreamEndCapture(ctx->stream, &g);
+        if (rc != SL1M_OK) return rc;
+        CK(ec);
+        CK(cudaGraphInstantiate(&B.gexec, g, 0));
+        cudaGraphDestroy(g);
+        B.graph_ok = true;
+        B.tick_launches = ctx->n_launch - l0;
+        ctx->n_launch = l0;
+    }
+    for (int i = 0; i < n; ++i) {
+        CK(cudaGraphLaunch(B.gexec, ctx->stream));
+        ctx->n_launch += B.tick_launches;
+    }
+    return SL1M_OK;
+}
+
+int batch_phases(sl1m_ctx* ctx, Batch& B, std::vector<int>& out)
+{
+    const int np = (int)B.probs.size();
+    out.resize(np);
+    CKL(launch_phases(B.desc.p, B.n_probs_dev.p, std::max(1, std::min(64, (np + 127) / 128)), B.phases_dev.p,
+                      ctx->stream));
+    CK(cudaMemcpyAsync(out.data(), B.phases_dev.p, sizeof(int) * np, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return SL1M_OK;
+}
+
+// Operator-mode batch of a single problem (cached per precision).
+static int op_prepare(sl1m_problem* prob, int precision, Batch** out)
+{
+    sl1m_ctx* ctx = prob->ctx;
+    RET(prob->rebuild(ctx->stream));
+    auto& B = prob->op_batch[precision];
+    if (!B) B = std::make_unique<Batch>();
+    ProblemDev& D = *prob->dev;
+    CK(D.x_sorted.reserve(prob->hp.pix.n_pad, ctx->stream));
+    CK(D.fwd_sorted.reserve(prob->hp.vis.n_pad, ctx->stream));
+    CK(D.r_sorted.reserve(prob->hp.vis.n_pad, ctx->stream));
+    CK(D.adj_sorted.reserve(prob->hp.pix.n_pad, ctx->stream));
+    DevProblem d = prob->hp;
+    d.st = nullptr;
+    d.x = D.x_sorted.p;
+    d.r = D.r_sorted.p;
+    d.fwd_out = D.fwd_sorted.p;
+    d.adj_out = D.adj_sorted.p;
+    if (B->probs.empty() || memcmp(&B->hdesc[0], &d, sizeof d) != 0)
+        RET(batch_set(ctx, *B, {prob}, {d}, precision, false));
+    *out = B.get();
+    return SL1M_OK;
+}
+
+// Run a single solve (or the power iteration alone) to completion.
+static int run_single(sl1m_problem* prob, int precision, int max_ticks, SolveState& s)
+{
+    sl1m_ctx* ctx = prob->ctx;
+    auto& B = prob->solve_batch[precision];
+    if (!B) B = std::make_unique<Batch>();
+    const DevProblem d = prob->solver_desc();
+    if (B->probs.empty() || memcmp(&B->hdesc[0], &d, sizeof d) != 0)
+        RET(batch_set(ctx, *B, {prob}, {d}, precision, true));
+    const int check = 8;
+    std::vector<int> ph;
+    int issued = 0;
+    while (issued < max_ticks) {
+        const int n = std::min(check, max_ticks - issued);
+        RET(batch_ticks(ctx, *B, n));
+        issued += n;
+        RET(batch_phases(ctx, *B, ph));
+        if (ph[0] == PH_DONE || ph[0] == PH_IDLE) break;
+    }
+    return prob->read_state(s, ctx->stream);
+}
+
+// ================================================================ C ABI
 extern "C" {
 
-int sl1m_version(void) { return 100; }
+int sl1m_version(void) { return 200; }
 
 const char* sl1m_status_string(int s)
 {
@@ -645,6 +842,10 @@ int sl1m_create(sl1m_ctx** out, int device, void* cuda_stream)
         }
         c->own_stream = true;
     }
+    if (cudaStreamCreateWithFlags(&c->upstream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return SL1M_ERR_CUDA;
+    }
     *out = c;
     return SL1M_OK;
 }
@@ -653,6 +854,7 @@ int sl1m_destroy(sl1m_ctx* ctx)
 {
     if (!ctx) return SL1M_ERR_ARG;
     cudaSetDevice(ctx->device);
+    server_destroy(ctx);
     cudaStreamSynchronize(ctx->stream);
     for (auto* p : ctx->problems) delete p;
     ctx->problems.clear();
@@ -661,6 +863,11 @@ int sl1m_destroy(sl1m_ctx* ctx)
 }
 
 const char* sl1m_last_error(const sl1m_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+#define NOT_WHILE_SERVING(ctx)                                                                   \
+    do {                                                                                         \
+        if ((ctx)->server) return sl1m_fail(ctx, SL1M_ERR_BUSY, "a server is running on this context"); \
+    } while (0)
 
 int sl1m_problem_create(sl1m_ctx* ctx, sl1m_problem** out)
 {
@@ -678,6 +885,7 @@ int sl1m_problem_destroy(sl1m_problem* prob)
 {
     if (!prob) return SL1M_ERR_ARG;
     sl1m_ctx* ctx = prob->ctx;
+    if (prob->in_server) return sl1m_fail(ctx, SL1M_ERR_BUSY, "problem is queued on the server");
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     ctx->problems.erase(std::remove(ctx->problems.begin(), ctx->problems.end(), prob), ctx->problems.end());
@@ -692,11 +900,17 @@ static bool all_finite(const double* a, size_t n)
     return true;
 }
 
+#define NOT_QUEUED(prob)                                                                           \
+    do {                                                                                           \
+        if ((prob)->in_server) return sl1m_fail((prob)->ctx, SL1M_ERR_BUSY, "problem is queued on the server"); \
+    } while (0)
+
 int sl1m_set_visibilities(sl1m_problem* prob, int64_t n_vis, const double* uvw, const double* vis,
                           const double* weights, const int32_t* ant_pair)
 {
     if (!prob) return SL1M_ERR_ARG;
     sl1m_ctx* ctx = prob->ctx;
+    NOT_QUEUED(prob);
     if (n_vis <= 0 || !uvw) return sl1m_fail(ctx, SL1M_ERR_ARG, "n_vis must be > 0 and uvw non-null");
     if (n_vis > (int64_t)1 << 30) return sl1m_fail(ctx, SL1M_ERR_ARG, "n_vis too large");
     if (!all_finite(uvw, 3 * n_vis)) return sl1m_fail(ctx, SL1M_ERR_ARG, "non-finite uvw");
@@ -726,6 +940,7 @@ int sl1m_set_vis_data(sl1m_problem* prob, const double* vis)
 {
     if (!prob) return SL1M_ERR_ARG;
     sl1m_ctx* ctx = prob->ctx;
+    NOT_QUEUED(prob);
     if (!vis || prob->n_vis <= 0) return sl1m_fail(ctx, SL1M_ERR_ARG, "no visibilities set");
     if (!all_finite(vis, 2 * prob->n_vis)) return sl1m_fail(ctx, SL1M_ERR_ARG, "non-finite visibilities");
     prob->vis.assign(vis, vis + 2 * prob->n_vis);
@@ -736,8 +951,11 @@ int sl1m_set_vis_data(sl1m_problem* prob, const double* vis)
             const int o = prob->vis_orig[i];
             if (o >= 0) Vs[i] = make_double2(vis[2 * o], vis[2 * o + 1]);
         }
-        CK(prob->dev->V.upload(Vs.data(), Vs.size(), ctx->stream));
+        // same size: copy in place so descriptors and captured graphs stay valid
+        CK(cudaMemcpyAsync(prob->dev->V.p, Vs.data(), sizeof(double2) * Vs.size(), cudaMemcpyHostToDevice,
+                           ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
+        ctx->h2d += (long long)sizeof(double2) * Vs.size();
     }
     return SL1M_OK;
 }
@@ -747,6 +965,7 @@ int sl1m_set_pixels(sl1m_problem* prob, int64_t n_pix, const double* lm, const d
 {
     if (!prob) return SL1M_ERR_ARG;
     sl1m_ctx* ctx = prob->ctx;
+    NOT_QUEUED(prob);
     if (n_pix <= 0 || !lm) return sl1m_fail(ctx, SL1M_ERR_ARG, "n_pix must be > 0 and lm non-null");
     if (n_pix > (int64_t)1 << 30) return sl1m_fail(ctx, SL1M_ERR_ARG, "n_pix too large");
     for (int64_t j = 0; j < n_pix; ++j) {
@@ -765,8 +984,7 @@ int sl1m_set_pixels(sl1m_problem* prob, int64_t n_pix, const double* lm, const d
     else prob->sigma.clear();
     if (kind) {
         prob->kind.assign(kind, kind + n_pix);
-        // Dirac pixels ignore sigma: one class for all of them
-        if (!prob->sigma.empty())
+        if (!prob->sigma.empty())            // Dirac pixels ignore sigma: one class for all
             for (int64_t j = 0; j < n_pix; ++j)
                 if (prob->kind[j] == 0) prob->sigma[j] = 0.0;
     } else {
@@ -785,6 +1003,7 @@ int sl1m_set_gains(sl1m_problem* prob, int32_t n_ant, const double* Gn)
 {
     if (!prob) return SL1M_ERR_ARG;
     sl1m_ctx* ctx = prob->ctx;
+    NOT_QUEUED(prob);
     if (!Gn || n_ant == 0) {
         prob->n_ant = 0;
         prob->gains.clear();
@@ -812,21 +1031,17 @@ int sl1m_forward_dev(sl1m_problem* prob, const double* x_dev, double* vis_out_de
 {
     if (!prob) return SL1M_ERR_ARG;
     sl1m_ctx* ctx = prob->ctx;
+    NOT_WHILE_SERVING(ctx);
     if (!x_dev || !vis_out_dev) return sl1m_fail(ctx, SL1M_ERR_ARG, "null pointer");
     RET(check_prec(ctx, precision));
     CK(cudaSetDevice(ctx->device));
-    RET(prob->rebuild());
+    Batch* B;
+    RET(op_prepare(prob, precision, &B));
     ProblemDev& D = *prob->dev;
-    CK(D.x_sorted.reserve(prob->hp.pix.n_pad, ctx->stream));
-    CK(D.fwd_sorted.reserve(prob->hp.vis.n_pad, ctx->stream));
     CKL(launch_gather_real(x_dev, D.x_sorted.p, prob->hp.pix.orig, prob->hp.pix.n_pad, 1.0, ctx->stream));
-    prob->reset_operands();
-    prob->hp.x = D.x_sorted.p;
-    prob->hp.fwd_out = D.fwd_sorted.p;
-    RET(prob->run_forward(precision, FIN_OP, nullptr));
+    RET(batch_op(ctx, *B, 0));
     CKL(launch_scatter_cplx(D.fwd_sorted.p, (double2*)vis_out_dev, prob->hp.vis.orig, prob->hp.vis.n_pad,
-                           ctx->stream));
-    prob->reset_operands();
+                            ctx->stream));
     return SL1M_OK;
 }
 
@@ -834,21 +1049,17 @@ int sl1m_adjoint_dev(sl1m_problem* prob, const double* r_dev, double* img_out_de
 {
     if (!prob) return SL1M_ERR_ARG;
     sl1m_ctx* ctx = prob->ctx;
+    NOT_WHILE_SERVING(ctx);
     if (!r_dev || !img_out_dev) return sl1m_fail(ctx, SL1M_ERR_ARG, "null pointer");
     RET(check_prec(ctx, precision));
     CK(cudaSetDevice(ctx->device));
-    RET(prob->rebuild());
+    Batch* B;
+    RET(op_prepare(prob, precision, &B));
     ProblemDev& D = *prob->dev;
-    CK(D.r_sorted.reserve(prob->hp.vis.n_pad, ctx->stream));
-    CK(D.adj_sorted.reserve(prob->hp.pix.n_pad, ctx->stream));
     CKL(launch_gather_cplx((const double2*)r_dev, D.r_sorted.p, prob->hp.vis.orig, prob->hp.vis.n_pad,
-                          ctx->stream));
-    prob->reset_operands();
-    prob->hp.r = D.r_sorted.p;
-    prob->hp.adj_out = D.adj_sorted.p;
-    RET(prob->run_adjoint(precision, FIN_OP, nullptr));
+                           ctx->stream));
+    RET(batch_op(ctx, *B, 1));
     CKL(launch_scatter_real(D.adj_sorted.p, img_out_dev, prob->hp.pix.orig, prob->hp.pix.n_pad, ctx->stream));
-    prob->reset_operands();
     return SL1M_OK;
 }
 
@@ -856,19 +1067,20 @@ int sl1m_forward(sl1m_problem* prob, const double* x, double* vis_out, int preci
 {
     if (!prob) return SL1M_ERR_ARG;
     sl1m_ctx* ctx = prob->ctx;
+    NOT_WHILE_SERVING(ctx);
     if (!x || !vis_out) return sl1m_fail(ctx, SL1M_ERR_ARG, "null pointer");
     if (!all_finite(x, prob->n_pix > 0 ? prob->n_pix : 0)) return sl1m_fail(ctx, SL1M_ERR_ARG, "non-finite x");
     CK(cudaSetDevice(ctx->device));
-    RET(prob->rebuild());
+    RET(prob->rebuild(ctx->stream));
     ProblemDev& D = *prob->dev;
     CK(D.x_user.reserve(prob->n_pix, ctx->stream));
     CK(D.vis_user.reserve(prob->n_vis, ctx->stream));
     CK(cudaMemcpyAsync(D.x_user.p, x, sizeof(double) * prob->n_pix, cudaMemcpyHostToDevice, ctx->stream));
     RET(sl1m_forward_dev(prob, D.x_user.p, (double*)D.vis_user.p, precision));
     CK(cudaMemcpyAsync(vis_out, D.vis_user.p, sizeof(double2) * prob->n_vis, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     ctx->h2d += (long long)sizeof(double) * prob->n_pix;
     ctx->d2h += (long long)sizeof(double2) * prob->n_vis;
-    CK(cudaStreamSynchronize(ctx->stream));
     return SL1M_OK;
 }
 
@@ -876,19 +1088,20 @@ int sl1m_adjoint(sl1m_problem* prob, const double* r, double* img_out, int preci
 {
     if (!prob) return SL1M_ERR_ARG;
     sl1m_ctx* ctx = prob->ctx;
+    NOT_WHILE_SERVING(ctx);
     if (!r || !img_out) return sl1m_fail(ctx, SL1M_ERR_ARG, "null pointer");
     if (!all_finite(r, prob->n_vis > 0 ? 2 * prob->n_vis : 0)) return sl1m_fail(ctx, SL1M_ERR_ARG, "non-finite r");
     CK(cudaSetDevice(ctx->device));
-    RET(prob->rebuild());
+    RET(prob->rebuild(ctx->stream));
     ProblemDev& D = *prob->dev;
     CK(D.r_user.reserve(prob->n_vis, ctx->stream));
     CK(D.img_user.reserve(prob->n_pix, ctx->stream));
     CK(cudaMemcpyAsync(D.r_user.p, r, sizeof(double2) * prob->n_vis, cudaMemcpyHostToDevice, ctx->stream));
     RET(sl1m_adjoint_dev(prob, (const double*)D.r_user.p, D.img_user.p, precision));
     CK(cudaMemcpyAsync(img_out, D.img_user.p, sizeof(double) * prob->n_pix, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     ctx->h2d += (long long)sizeof(double2) * prob->n_vis;
     ctx->d2h += (long long)sizeof(double) * prob->n_pix;
-    CK(cudaStreamSynchronize(ctx->stream));
     return SL1M_OK;
 }
 
@@ -896,108 +1109,63 @@ int sl1m_max_eig(sl1m_problem* prob, int max_iter, double tol, int precision, do
 {
     if (!prob) return SL1M_ERR_ARG;
     sl1m_ctx* ctx = prob->ctx;
+    NOT_WHILE_SERVING(ctx);
     if (!L_out || max_iter <= 0 || !(tol >= 0)) return sl1m_fail(ctx, SL1M_ERR_ARG, "bad arguments");
     RET(check_prec(ctx, precision));
     CK(cudaSetDevice(ctx->device));
-    RET(prob->rebuild());
-    return prob->power(precision, max_iter, tol, L_out, iters_out);
+    RET(prob->rebuild(ctx->stream));
+    sl1m_solve_opts o;
+    memset(&o, 0, sizeof o);
+    o.power_max_iter = max_iter;
+    o.power_tol = tol > 0 ? tol : 1e-300;
+    RET(prob->init_solve(&o, 0.0, true, ctx->stream));
+    SolveState s;
+    RET(run_single(prob, precision, max_iter + 2, s));
+    if (s.nonfinite) return sl1m_fail(ctx, SL1M_ERR_NONFINITE, "non-finite value in power iteration");
+    if (!(s.mu > 0.0)) return sl1m_fail(ctx, SL1M_ERR_ARG, "operator is zero (all weights zero?)");
+    *L_out = s.L > 0 ? s.L : s.mu;
+    if (iters_out) *iters_out = s.pit;
+    return SL1M_OK;
+}
+
+static int check_opts(sl1m_ctx* ctx, const sl1m_solve_opts* o)
+{
+    if (!(o->lambda >= 0) || !std::isfinite(o->lambda) || !(o->L >= 0) || !std::isfinite(o->L) ||
+        o->max_iter < 0 || !(o->rel_tol >= 0) || o->power_max_iter < 0 || !(o->power_tol >= 0))
+        return sl1m_fail(ctx, SL1M_ERR_ARG, "bad solver options");
+    return check_prec(ctx, o->precision);
 }
 
 int sl1m_solve(sl1m_problem* prob, const sl1m_solve_opts* o, double* img_out, sl1m_solve_stats* stats)
 {
     if (!prob) return SL1M_ERR_ARG;
     sl1m_ctx* ctx = prob->ctx;
+    NOT_WHILE_SERVING(ctx);
     if (!o || !img_out) return sl1m_fail(ctx, SL1M_ERR_ARG, "null pointer");
-    if (!(o->lambda >= 0) || !std::isfinite(o->lambda) || !(o->L >= 0) || !std::isfinite(o->L) ||
-        o->max_iter < 0 || !(o->rel_tol >= 0))
-        return sl1m_fail(ctx, SL1M_ERR_ARG, "bad solver options");
-    RET(check_prec(ctx, o->precision));
+    RET(check_opts(ctx, o));
+    if (o->x0 && !all_finite(o->x0, prob->n_pix)) return sl1m_fail(ctx, SL1M_ERR_ARG, "non-finite x0");
     const auto t0 = std::chrono::steady_clock::now();
     CK(cudaSetDevice(ctx->device));
-    RET(prob->rebuild());
-    RET(prob->ensure_solver());
-    ProblemDev& D = *prob->dev;
-    const int prec = o->precision;
-    double L = o->L;
-    int pits = 0;
-    if (L == 0.0) {
-        RET(prob->power(prec, o->power_max_iter > 0 ? o->power_max_iter : 50,
-                        o->power_tol > 0 ? o->power_tol : 1e-6, &L, &pits));
-    }
-    // Step 0: y_1 = I_0 = x0 (or 0), t_1 = 1
-    double l1_0 = 0.0;
-    if (o->x0) {
-        if (!all_finite(o->x0, prob->n_pix)) return sl1m_fail(ctx, SL1M_ERR_ARG, "non-finite x0");
-        CK(D.x_user.reserve(prob->n_pix, ctx->stream));
-        CK(cudaMemcpyAsync(D.x_user.p, o->x0, sizeof(double) * prob->n_pix, cudaMemcpyHostToDevice, ctx->stream));
-        CKL(launch_gather_real(D.x_user.p, D.I0.p, prob->hp.pix.orig, prob->hp.pix.n_pad, 1.0, ctx->stream));
-        for (int64_t j = 0; j < prob->n_pix; ++j) l1_0 += o->x0[j];
-        ctx->h2d += (long long)sizeof(double) * prob->n_pix;
-    } else {
-        CK(cudaMemsetAsync(D.I0.p, 0, sizeof(double) * prob->hp.pix.n_pad, ctx->stream));
-    }
-    CK(cudaMemcpyAsync(D.y.p, D.I0.p, sizeof(double) * prob->hp.pix.n_pad, cudaMemcpyDeviceToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(D.I1.p, D.I0.p, sizeof(double) * prob->hp.pix.n_pad, cudaMemcpyDeviceToDevice, ctx->stream));
-    SolveState s0;
-    memset(&s0, 0, sizeof s0);
-    s0.lambda = o->lambda;
-    s0.L = L;
-    s0.tol = o->rel_tol;
-    s0.t = 1.0;
-    s0.l1 = l1_0;
-    s0.max_iter = o->max_iter;
-    s0.inv_mu = 1.0;
-    CK(cudaMemcpyAsync(D.st.p, &s0, sizeof s0, cudaMemcpyHostToDevice, ctx->stream));
-    // A I_0, r_1 = W (A y_1 - V), E_0
-    prob->reset_operands();
-    prob->hp.x = D.I0.p;
-    RET(prob->run_forward(prec, FIN_INIT, D.bufs.p));
-    CKL(launch_scalars(D.bufs.p, D.desc.p, 1, FIN_INIT, ctx->stream));
-    // iterations
-    prob->reset_operands();
-    prob->hp.xpp[0] = D.I0.p;
-    prob->hp.xpp[1] = D.I1.p;
-    prob->hp.xsel = &D.st.p->parity;
-    prob->hp.r = D.rr.p;
-    prob->hp.done = &D.st.p->done;
-    SolveState sh;
-    memset(&sh, 0, sizeof sh);
-    const int check = 8;
-    int issued = 0;
-    bool finished = o->max_iter == 0;
-    while (!finished) {
-        for (int q = 0; q < check && issued < o->max_iter; ++q, ++issued) {
-            RET(prob->run_adjoint(prec, FIN_SOLVE, D.bufs.p));
-            RET(prob->run_forward(prec, FIN_SOLVE, D.bufs.p));
-            CKL(launch_scalars(D.bufs.p, D.desc.p, 1, FIN_SOLVE, ctx->stream));
-        }
-        CK(cudaMemcpyAsync(&sh, D.st.p, sizeof sh, cudaMemcpyDeviceToHost, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
-        finished = sh.done || issued >= o->max_iter;
-    }
-    CK(cudaMemcpyAsync(&sh, D.st.p, sizeof sh, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    // result: I_k lives in I[k & 1]
-    double* Ik = (sh.k & 1) ? D.I1.p : D.I0.p;
-    CK(D.img_user.reserve(prob->n_pix, ctx->stream));
-    CKL(launch_scatter_real(Ik, D.img_user.p, prob->hp.pix.orig, prob->hp.pix.n_pad, ctx->stream));
-    CK(cudaMemcpyAsync(img_out, D.img_user.p, sizeof(double) * prob->n_pix, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    ctx->d2h += (long long)sizeof(double) * prob->n_pix;
-    prob->reset_operands();
+    RET(prob->rebuild(ctx->stream));
+    RET(prob->init_solve(o, o->L, false, ctx->stream));
+    const int pmax = o->power_max_iter > 0 ? o->power_max_iter : 50;
+    SolveState s;
+    RET(run_single(prob, o->precision, o->max_iter + (o->L > 0 ? 0 : pmax + 1) + 2, s));
+    RET(prob->fetch_image(img_out, ctx->stream));
     if (stats) {
-        stats->iters = sh.k;
-        stats->converged = sh.converged;
-        stats->E = sh.E;
-        stats->E_paper = sh.resid2 + o->lambda * sh.l1;
-        stats->resid2 = sh.resid2;
-        stats->l1 = sh.l1;
-        stats->nnz = sh.nnz;
-        stats->L = L;
-        stats->power_iters = pits;
+        stats->iters = s.k;
+        stats->converged = s.converged;
+        stats->E = s.E;
+        stats->E_paper = s.resid2 + o->lambda * s.l1;
+        stats->resid2 = s.resid2;
+        stats->l1 = s.l1;
+        stats->nnz = s.nnz;
+        stats->L = s.L;
+        stats->power_iters = s.pit;
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
-    if (sh.nonfinite) return sl1m_fail(ctx, SL1M_ERR_NONFINITE, "non-finite value during the solve");
+    if (s.nonfinite) return sl1m_fail(ctx, SL1M_ERR_NONFINITE, "non-finite value during the solve");
+    if (s.phase != PH_DONE) return sl1m_fail(ctx, SL1M_ERR_STATE, "solve did not finish");
     return SL1M_OK;
 }
 
@@ -1094,26 +1262,3 @@ int sl1m_problem_bytes(const sl1m_problem* prob, int64_t* bytes)
 }
 
 }  // extern "C"
-
-size_t sl1m_problem::dev_bytes() const
-{
-    if (!dev) return 0;
-    const ProblemDev& D = *dev;
-    size_t b = 0;
-    auto side = [&](const DevSide& s) {
-        b += s.hi.bytes() + s.lo.bytes() + s.off.bytes() + s.offlo.bytes() + s.cen_hi.bytes() +
-             s.cen_lo.bytes() + s.ext.bytes() + s.d.bytes() + s.orig.bytes();
-    };
-    side(D.vis);
-    side(D.pix);
-    b += D.ant.bytes() + D.V.bytes() + D.pgauss.bytes() + D.pgauss64.bytes() + D.gsig.bytes() +
-         D.gkind.bytes() + D.gains32.bytes() + D.gains64.bytes();
-    b += D.x_user.bytes() + D.x_sorted.bytes() + D.adj_sorted.bytes() + D.img_user.bytes() +
-         D.r_user.bytes() + D.r_sorted.bytes() + D.fwd_sorted.bytes() + D.vis_user.bytes();
-    b += D.I0.bytes() + D.I1.bytes() + D.y.bytes() + D.xv.bytes() + D.blk_r2.bytes() + D.blk_l1.bytes() +
-         D.blk_z2.bytes() + D.AI0.bytes() + D.AI1.bytes() + D.rr.bytes() + D.blk_nnz.bytes() +
-         D.blk_badv.bytes() + D.blk_badp.bytes() + D.st.bytes() + D.bufs.bytes() + D.desc.bytes();
-    return b;
-}
-
-sl1m_problem::~sl1m_problem() = default;

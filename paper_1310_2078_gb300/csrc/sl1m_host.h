@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "sl1m.h"
 #include "sl1m_dev.h"
 
 // Device buffer owned by the library (cudaMalloc / cudaFree).
@@ -43,15 +44,15 @@ struct DBuf {
         cudaStreamSynchronize(st);
         return alloc(count);
     }
-    // Allocate exactly `count` and copy from host (zero-fill when `zero`).
+    // Allocate exactly `count` and copy from host (zero-fill when `zero`);
+    // returns after the copy (the host source may be a temporary).
     cudaError_t upload(const T* src, size_t count, cudaStream_t st, bool zero = false)
     {
         cudaError_t e = alloc(count);
         if (e != cudaSuccess || count == 0) return e;
-        if (zero) return cudaMemsetAsync(p, 0, count * sizeof(T), st);
-        e = cudaMemcpyAsync(p, src, count * sizeof(T), cudaMemcpyHostToDevice, st);
+        if (zero) e = cudaMemsetAsync(p, 0, count * sizeof(T), st);
+        else e = cudaMemcpyAsync(p, src, count * sizeof(T), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return e;
-        // the host source may be a temporary: finish the copy before returning
         return cudaStreamSynchronize(st);
     }
     size_t bytes() const { return n * sizeof(T); }
@@ -65,12 +66,13 @@ struct HostPlan {
 };
 void plan_host(const std::vector<int>& nb, const std::vector<int>& ns, int Cmax, HostPlan& H);
 
+// A plan whose tables and header live on the device (kernels take Plan*).
 struct DevPlan {
-    sl1m::Plan pl{};
+    sl1m::Plan pl{};          // host copy of the header
     DBuf<long long> u0;
     DBuf<int> b0, poff, clo, ncon;
+    DBuf<sl1m::Plan> dpl;     // device header
 };
-
 cudaError_t build_plan(const std::vector<int>& nb, const std::vector<int>& ns, int Cmax, DevPlan& D,
                        cudaStream_t st);
 
@@ -89,17 +91,44 @@ struct ProfTok {
 };
 
 struct sl1m_problem;
+struct Server;
+
+// Device tables of a set of problems run together (one precision).
+struct Batch {
+    int precision = 1;
+    bool solver = false;
+    std::vector<sl1m_problem*> probs;
+    std::vector<sl1m::DevProblem> hdesc;
+    DBuf<sl1m::DevProblem> desc;
+    DBuf<int> n_probs_dev;
+    DBuf<int> phases_dev;
+    DevPlan plan[2][2];        // [0 forward / 1 adjoint][0 no gains / 1 gains]
+    bool has_class[2] = {false, false};
+    int n_ant_max = 0;
+    int fin_grid = 1, sc_grid = 1;
+    double pairs_class[2] = {0, 0};
+    double fin_bytes[2] = {0, 0};   // [forward finish, adjoint finish] per tick
+    // captured tick
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_ok = false;
+    long long tick_launches = 0;
+    ~Batch();
+};
 
 struct sl1m_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t upstream = nullptr;     // uploads of problems joining a running server
     bool own_stream = false;
     int num_sms = 1;
     std::string err;
     DBuf<double2> partial_f;
     DBuf<double> partial_a;
     std::vector<sl1m_problem*> problems;
-    // profiling
+    Server* server = nullptr;            // running request loop
+    Server* server_done = nullptr;       // stopped loop whose results are still collectable
+    bool use_graphs = true;
+    // profiling and counters
     bool prof = false;
     std::vector<ProfRec> pending;
     std::vector<cudaEvent_t> ev_pool;
@@ -128,23 +157,31 @@ struct sl1m_problem {
     bool dirty = true;
     bool has_gauss = false;
     bool solver_ready = false;
+    bool in_server = false;
     std::unique_ptr<ProblemDev> dev;
-    sl1m::DevProblem hp{};
-    sl1m::DevProblem last_desc{};
-    bool desc_valid = false;
+    sl1m::DevProblem hp{};          // layout part of the descriptor
     sl1m::SolveBufs hbufs{};
     std::vector<int> vis_orig, pix_orig;
-    std::map<int, std::unique_ptr<DevPlan>> plans;
+    std::unique_ptr<Batch> op_batch[2], solve_batch[2];
 
-    int rebuild();
-    int plan(int op, int precision, const sl1m::Plan** out);
-    int upload_desc();
-    int run_forward(int precision, int fin_mode, const sl1m::SolveBufs* bufs_dev);
-    int run_adjoint(int precision, int fin_mode, const sl1m::SolveBufs* bufs_dev);
-    int ensure_solver();
-    void reset_operands();
-    int power(int precision, int max_iter, double tol, double* L, int* iters);
+    int rebuild(cudaStream_t st);
+    int ensure_solver(cudaStream_t st);
+    int init_solve(const sl1m_solve_opts* o, double L, bool power_only, cudaStream_t st);
+    int read_state(sl1m::SolveState& s, cudaStream_t st);
+    int fetch_image(double* host_out, cudaStream_t st);
+    sl1m::DevProblem solver_desc() const;
     double pairs() const;
     size_t dev_bytes() const;
+    size_t estimate_bytes() const;
     ~sl1m_problem();
 };
+
+// batches (sl1m_host.cpp)
+int batch_set(sl1m_ctx* ctx, Batch& B, const std::vector<sl1m_problem*>& probs,
+              const std::vector<sl1m::DevProblem>& descs, int precision, bool solver);
+int batch_op(sl1m_ctx* ctx, Batch& B, int op);
+int batch_ticks(sl1m_ctx* ctx, Batch& B, int n);
+int batch_phases(sl1m_ctx* ctx, Batch& B, std::vector<int>& out);
+
+// server (sl1m_server.cpp)
+void server_destroy(sl1m_ctx* ctx);

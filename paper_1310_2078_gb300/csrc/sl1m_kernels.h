@@ -6,10 +6,11 @@ namespace sl1m {
 
 enum FinishMode : int { FIN_OP = 0, FIN_POWER = 1, FIN_SOLVE = 2, FIN_INIT = 3 };
 
-// operator kernels (sl1m_ops.cu); precision 0 = FP64, 1 = mixed
+// operator kernels (sl1m_mixed.cu, sl1m_fp64.cu); precision 0 = FP64, 1 = mixed.
+// plp: device-resident plan; C: its grid size (known on the host).
 cudaError_t launch_forward(int precision, bool gains, int n_ant, const DevProblem* probs,
-                           const Plan& pl, double2* partial, cudaStream_t st);
-cudaError_t launch_adjoint(int precision, bool gains, const DevProblem* probs, const Plan& pl,
+                           const Plan* plp, int C, double2* partial, cudaStream_t st);
+cudaError_t launch_adjoint(int precision, bool gains, const DevProblem* probs, const Plan* plp, int C,
                            double* partial, cudaStream_t st);
 // which: 0 fwd fp64, 1 adj fp64, 2 fwd mixed, 3 adj mixed
 int occupancy(int which, bool gains, int n_ant);
@@ -25,11 +26,11 @@ cudaError_t launch_scatter_real(const double* src, double* dst, const int* orig,
 cudaError_t launch_scatter_cplx(const double2* src, double2* dst, const int* orig, int n_pad,
                                 cudaStream_t st);
 cudaError_t launch_fill_valid(double* dst, const int* orig, int n_pad, double val, cudaStream_t st);
-cudaError_t launch_fwd_finish(const DevProblem* probs, const SolveBufs* bufs, const Plan& pl,
-                              const double2* partial, int mode, cudaStream_t st);
-cudaError_t launch_adj_finish(const DevProblem* probs, const SolveBufs* bufs, const Plan& pl,
-                              const double* partial, int mode, cudaStream_t st);
-cudaError_t launch_scalars(const SolveBufs* bufs, const DevProblem* probs, int n_probs, int mode,
-                           cudaStream_t st);
+cudaError_t launch_fwd_finish(const DevProblem* probs, const Plan* plp, int grid, const double2* partial,
+                              cudaStream_t st);
+cudaError_t launch_adj_finish(const DevProblem* probs, const Plan* plp, int grid, const double* partial,
+                              cudaStream_t st);
+cudaError_t launch_scalars(const DevProblem* probs, const int* n_probs, int grid, cudaStream_t st);
+cudaError_t launch_phases(const DevProblem* probs, const int* n_probs, int grid, int* out, cudaStream_t st);
 
 }  // namespace sl1m

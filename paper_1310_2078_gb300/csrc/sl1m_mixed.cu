@@ -52,7 +52,7 @@ __device__ __forceinline__ void fwd_dirac_tile(const float4* __restrict__ s_off,
             float ph;
             if (EXACT) ph = b + frac_dot3(dx[r], dxl[r], o, ol);
             else ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, b)));
-            ph = ph - rintf(ph);
+            ph = frac_turns(ph);
             float sn, cs;
             __sincosf(ph * TWO_PI_F, &sn, &cs);
             if (GAINS) {
@@ -95,7 +95,7 @@ __device__ __forceinline__ void fwd_gauss_tile(const float4* __restrict__ s_off,
             const float t = fmaf(uf, pg.x, fmaf(vf, pg.y, -wf * pg.z));
             ph = fmaf(-gc[r].gam, t, ph);
             if (par) ph = fmaf(-wf, pg.w, ph);
-            ph = ph - rintf(ph);
+            ph = frac_turns(ph);
             float sn, cs;
             __sincosf(ph * TWO_PI_F, &sn, &cs);
             const float e1 = fmaf(-wf, pg.x, uf), e2 = fmaf(-wf, pg.y, vf);
@@ -115,20 +115,28 @@ __device__ __forceinline__ void fwd_gauss_tile(const float4* __restrict__ s_off,
     }
 }
 
+// Streamed granules staged per barrier pair (the gains tables of one granule
+// already fill most of shared memory, so the gains kernels stage one).
+template <bool GAINS> struct Stage { static constexpr int N = GAINS ? 1 : 4; };
+
 // Owned: visibilities (warp = one vis granule, lane = 2 visibilities).
-// Streamed: pixel granules through shared memory.
+// Streamed: pixel granules through shared memory, NST per stage.
 template <bool GAINS>
-__global__ void __launch_bounds__(NTHREADS)
-fwd_mixed_kernel(const DevProblem* __restrict__ probs, Plan pl, double2* __restrict__ partial)
+__global__ void __launch_bounds__(NTHREADS, 3)
+fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ plp, double2* __restrict__ partial)
 {
-    __shared__ float4 s_off[G];            // {dl, dm, dn, a = x/n}
-    __shared__ float4 s_lo[G];             // offset residuals
-    __shared__ float4 s_pg[G];             // {l, m, r^2/2, nu}
-    __shared__ float s_B[BLK_GRAN][G];
-    __shared__ float4 s_cen[3];            // centre hi, lo, extent
+    constexpr int NST = Stage<GAINS>::N;
+    __shared__ float4 s_off[NST][G];       // {dl, dm, dn, a = x/n}
+    __shared__ float4 s_lo[NST][G];        // offset residuals
+    __shared__ float4 s_pg[NST][G];        // {l, m, r^2/2, nu}
+    __shared__ float s_B[BLK_GRAN][NST][G];
+    __shared__ float4 s_cen[NST][3];       // centre hi, lo, extent
+    __shared__ int s_kind[NST];
+    __shared__ float s_sig[NST];
     extern __shared__ float2 s_gain[];     // GAINS: [G][n_ant]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Plan pl = *plp;
     const long long c = blockIdx.x;
     long long u = (pl.U * c) / pl.C;
     const long long u_end = (pl.U * (c + 1)) / pl.C;
@@ -137,7 +145,8 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, Plan pl, double2* __restr
         const int p = find_prob(pl, u);
         const DevProblem& P = probs[p];
         const long long loc = u - pl.prob_u0[p];
-        if (P.done && *P.done) {                  // finished solve: skip its units
+        const double* X;
+        if (!fwd_role(P, X)) {                    // problem not in this step: skip its units
             u = min(u_end, pl.prob_u0[p + 1]);
             continue;
         }
@@ -148,9 +157,10 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, Plan pl, double2* __restr
         const int vg = blk * BLK_GRAN + warp;
         const bool vg_ok = vg < P.vis.n_gran;
         const int n_ant = P.n_ant;
+        const int e0 = (vg_ok ? vg : 0) * G + lane;     // this lane's visibilities: e0, e0 + 32
 
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 xh[2] = {z4, z4}, xl[2] = {z4, z4}, dx[2] = {z4, z4}, dxl[2] = {z4, z4};
+        float4 xh[2] = {z4, z4}, dx[2] = {z4, z4};
         int2 ant[2] = {make_int2(0, 0), make_int2(0, 0)};
         float4 ch = z4, cl = z4, ext = z4;
         if (vg_ok) {
@@ -159,88 +169,98 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, Plan pl, double2* __restr
             ext = P.vis.ext[vg];
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
-                const int e = vg * G + lane + 32 * r;
-                xh[r] = P.vis.hi[e];
-                xl[r] = P.vis.lo[e];
-                dx[r] = P.vis.off[e];
-                dxl[r] = P.vis.offlo[e];
-                if (GAINS) ant[r] = P.ant[e];
+                xh[r] = P.vis.hi[e0 + 32 * r];
+                dx[r] = P.vis.off[e0 + 32 * r];
+                if (GAINS) ant[r] = P.ant[e0 + 32 * r];
             }
         }
-        const double xs = P.xscale ? *P.xscale : 1.0;
-        const double* X = fwd_input(P);
         double tr[2] = {0.0, 0.0}, ti[2] = {0.0, 0.0};
 
-        for (int g = g0; g < g1; ++g) {
-            __syncthreads();                       // previous tile consumed
-            const int kind = P.gkind[g];
-            if (threadIdx.x < G) {
-                const int e = g * G + threadIdx.x;
+        for (int gs = g0; gs < g1; gs += NST) {
+            const int ns = min(NST, g1 - gs);
+            __syncthreads();                       // previous stage consumed
+            for (int t = threadIdx.x; t < ns * G; t += NTHREADS) {
+                const int q = t / G, i = t % G;
+                const int g = gs + q;
+                const int e = g * G + i;
                 float4 o = P.pix.off[e];
-                o.w = (float)(X[e] * xs * P.pix.d[e].w);     // x / n (0 on padding)
-                s_off[threadIdx.x] = o;
-                s_lo[threadIdx.x] = P.pix.offlo[e];
-                if (kind != DIRAC) s_pg[threadIdx.x] = P.pgauss[e];
-            } else if (threadIdx.x == G) {
-                s_cen[0] = P.pix.cen_hi[g];
-                s_cen[1] = P.pix.cen_lo[g];
-                s_cen[2] = P.pix.ext[g];
+                o.w = (float)(X[e] * P.pix.d[e].w);     // x / n (0 on padding)
+                s_off[q][i] = o;
+                s_lo[q][i] = P.pix.offlo[e];
+                if (P.gkind[g] != DIRAC) s_pg[q][i] = P.pgauss[e];
+            }
+            if (threadIdx.x < ns) {
+                const int g = gs + threadIdx.x;
+                s_cen[threadIdx.x][0] = P.pix.cen_hi[g];
+                s_cen[threadIdx.x][1] = P.pix.cen_lo[g];
+                s_cen[threadIdx.x][2] = P.pix.ext[g];
+                s_kind[threadIdx.x] = P.gkind[g];
+                s_sig[threadIdx.x] = P.gsig[g];
             }
             if (GAINS) {
-                const float2* src = P.gains32 + (size_t)g * G * n_ant;
+                const float2* src = P.gains32 + (size_t)gs * G * n_ant;
                 for (int i = threadIdx.x; i < G * n_ant; i += NTHREADS) s_gain[i] = src[i];
             }
             __syncthreads();
             // B_j = frac(Xc . (Y_j - Yc)) for this warp's granule centre
+            for (int q = 0; q < ns; ++q) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int j = lane + 32 * h;
-                s_B[warp][j] = frac_dot3(ch, cl, s_off[j], s_lo[j]);
+                for (int h = 0; h < 2; ++h) {
+                    const int j = lane + 32 * h;
+                    s_B[warp][q][j] = frac_dot3(ch, cl, s_off[q][j], s_lo[q][j]);
+                }
             }
             __syncwarp();
-            const float4 yc_h = s_cen[0], yc_l = s_cen[1];
-            const bool exact = dot3(ext, s_cen[2]) > D_MAX;       // warp-uniform
-            float C[2];
+            for (int q = 0; q < ns; ++q) {
+                const int kind = s_kind[q];
+                const float4 yc_h = s_cen[q][0], yc_l = s_cen[q][1];
+                const bool exact = dot3(ext, s_cen[q][2]) > D_MAX;       // warp-uniform
+                float C[2];
 #pragma unroll
-            for (int r = 0; r < 2; ++r) C[r] = frac_dot3(xh[r], xl[r], yc_h, yc_l);
-            float sr[2] = {0.f, 0.f}, si[2] = {0.f, 0.f};
-            if (kind == DIRAC) {
-                if (exact)
-                    fwd_dirac_tile<GAINS, true>(s_off, s_lo, s_B[warp], s_gain, n_ant, dx, dxl, ant, sr, si);
-                else
-                    fwd_dirac_tile<GAINS, false>(s_off, s_lo, s_B[warp], s_gain, n_ant, dx, dxl, ant, sr, si);
+                for (int r = 0; r < 2; ++r) C[r] = frac_dot3(xh[r], P.vis.lo[e0 + 32 * r], yc_h, yc_l);
+                float sr[2] = {0.f, 0.f}, si[2] = {0.f, 0.f};
+                if (kind == DIRAC) {
+                    if (exact) {
+                        const float4 dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
+                        fwd_dirac_tile<GAINS, true>(s_off[q], s_lo[q], s_B[warp][q], s_gain, n_ant, dx, dxl, ant,
+                                                    sr, si);
+                    } else {
+                        fwd_dirac_tile<GAINS, false>(s_off[q], s_lo[q], s_B[warp][q], s_gain, n_ant, dx, dx, ant,
+                                                     sr, si);
+                    }
 #pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    float sn, cs;
-                    __sincosf(C[r] * TWO_PI_F, &sn, &cs);          // rotate by exp(-2 pi i C)
-                    tr[r] += (double)fmaf(cs, sr[r], sn * si[r]);
-                    ti[r] += (double)fmaf(cs, si[r], -sn * sr[r]);
-                }
-            } else {
-                const float sigma = P.gsig[g];
-                const bool par = (kind == PARAXIAL);
-                GaussConst gc[2];
+                    for (int r = 0; r < 2; ++r) {
+                        float sn, cs;
+                        __sincosf(C[r] * TWO_PI_F, &sn, &cs);          // rotate by exp(-2 pi i C)
+                        tr[r] += (double)fmaf(cs, sr[r], sn * si[r]);
+                        ti[r] += (double)fmaf(cs, si[r], -sn * sr[r]);
+                    }
+                } else {
+                    const bool par = (kind == PARAXIAL);
+                    GaussConst gc[2];
 #pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    gc[r] = gauss_const(xh[r].x, xh[r].y, xh[r].z, sigma);
-                    const float cc = C[r] + gc[r].cphase;
-                    C[r] = cc - rintf(cc);
-                }
-                if (exact)
-                    fwd_gauss_tile<GAINS, true>(s_off, s_lo, s_pg, s_B[warp], s_gain, n_ant, par, xh, dx,
-                                                dxl, gc, ant, sr, si);
-                else
-                    fwd_gauss_tile<GAINS, false>(s_off, s_lo, s_pg, s_B[warp], s_gain, n_ant, par, xh, dx,
-                                                 dxl, gc, ant, sr, si);
+                    for (int r = 0; r < 2; ++r) {
+                        gc[r] = gauss_const(xh[r].x, xh[r].y, xh[r].z, s_sig[q]);
+                        C[r] = frac_turns(C[r] + gc[r].cphase);
+                    }
+                    if (exact) {
+                        const float4 dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
+                        fwd_gauss_tile<GAINS, true>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], s_gain, n_ant, par, xh,
+                                                    dx, dxl, gc, ant, sr, si);
+                    } else {
+                        fwd_gauss_tile<GAINS, false>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], s_gain, n_ant, par,
+                                                     xh, dx, dx, gc, ant, sr, si);
+                    }
 #pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    // S id (1 + i beta), then rotate by exp(-2 pi i C)
-                    const float ar = gc[r].id * fmaf(-gc[r].beta, si[r], sr[r]);
-                    const float ai = gc[r].id * fmaf(gc[r].beta, sr[r], si[r]);
-                    float sn, cs;
-                    __sincosf(C[r] * TWO_PI_F, &sn, &cs);
-                    tr[r] += (double)fmaf(cs, ar, sn * ai);
-                    ti[r] += (double)fmaf(cs, ai, -sn * ar);
+                    for (int r = 0; r < 2; ++r) {
+                        // S id (1 + i beta), then rotate by exp(-2 pi i C)
+                        const float ar = gc[r].id * fmaf(-gc[r].beta, si[r], sr[r]);
+                        const float ai = gc[r].id * fmaf(gc[r].beta, sr[r], si[r]);
+                        float sn, cs;
+                        __sincosf(C[r] * TWO_PI_F, &sn, &cs);
+                        tr[r] += (double)fmaf(cs, ar, sn * ai);
+                        ti[r] += (double)fmaf(cs, ai, -sn * ar);
+                    }
                 }
             }
         }
@@ -278,7 +298,7 @@ __device__ __forceinline__ void adj_dirac_tile(const float4* __restrict__ s_off,
             float ph;
             if (EXACT) ph = (C[r] + b) + frac_dot3(dx[r], dxl[r], o, ol);
             else ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, C[r] + b)));
-            ph = ph - rintf(ph);
+            ph = frac_turns(ph);
             float sn, cs;
             __sincosf(ph * TWO_PI_F, &sn, &cs);           // exp(+2 pi i ph) = cs + i sn
             if (GAINS) {
@@ -324,7 +344,7 @@ __device__ __forceinline__ void adj_gauss_tile(const float4* __restrict__ s_off,
             const float t = fmaf(va.x, pgd[r].x, fmaf(va.y, pgd[r].y, -va.z * pgd[r].z));
             ph = fmaf(-gw.x, t, ph);
             if (par) ph = fmaf(-va.z, pgd[r].w, ph);
-            ph = ph - rintf(ph);
+            ph = frac_turns(ph);
             float sn, cs;
             __sincosf(ph * TWO_PI_F, &sn, &cs);
             const float e1 = fmaf(-va.z, pgd[r].x, va.x), e2 = fmaf(-va.z, pgd[r].y, va.y);
@@ -346,21 +366,24 @@ __device__ __forceinline__ void adj_gauss_tile(const float4* __restrict__ s_off,
 }
 
 // Owned: pixels (warp = one pixel granule, lane = 2 pixels).
-// Streamed: visibility granules through shared memory.
+// Streamed: visibility granules through shared memory, NSA per stage.
+constexpr int NSA = 4;
+
 template <bool GAINS>
-__global__ void __launch_bounds__(NTHREADS)
-adj_mixed_kernel(const DevProblem* __restrict__ probs, Plan pl, double* __restrict__ partial)
+__global__ void __launch_bounds__(NTHREADS, 3)
+adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ plp, double* __restrict__ partial)
 {
-    __shared__ float4 s_off[G];            // {du, dv, dw, W}
-    __shared__ float4 s_lo[G];
-    __shared__ float4 s_abs[G];            // {u, v, w, 0} (Gaussian owners)
-    __shared__ float2 s_r[G];
-    __shared__ int2 s_ant[G];
-    __shared__ float s_B[BLK_GRAN][G];
-    __shared__ float4 s_gw[BLK_GRAN][G];   // Gaussian owners: {gam, coef, r're, r'im}
-    __shared__ float4 s_cen[3];
+    __shared__ float4 s_off[NSA][G];            // {du, dv, dw, W}
+    __shared__ float4 s_lo[NSA][G];
+    __shared__ float4 s_abs[NSA][G];            // {u, v, w, 0} (Gaussian owners)
+    __shared__ float2 s_r[NSA][G];
+    __shared__ int2 s_ant[NSA][G];
+    __shared__ float s_B[BLK_GRAN][NSA][G];
+    __shared__ float4 s_gw[BLK_GRAN][NSA][G];   // Gaussian owners: {gam, coef, r're, r'im}
+    __shared__ float4 s_cen[NSA][3];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Plan pl = *plp;
     const long long c = blockIdx.x;
     long long u = (pl.U * c) / pl.C;
     const long long u_end = (pl.U * (c + 1)) / pl.C;
@@ -369,7 +392,8 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, Plan pl, double* __restri
         const int p = find_prob(pl, u);
         const DevProblem& P = probs[p];
         const long long loc = u - pl.prob_u0[p];
-        if (P.done && *P.done) {
+        const double2* R;
+        if (!adj_role(P, R)) {
             u = min(u_end, pl.prob_u0[p + 1]);
             continue;
         }
@@ -380,12 +404,11 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, Plan pl, double* __restri
         const int pgi = blk * BLK_GRAN + warp;
         const bool pg_ok = pgi < P.pix.n_gran;
         const int n_ant = P.n_ant;
+        const int e0 = (pg_ok ? pgi : 0) * G + lane;     // this lane's pixels: e0, e0 + 32
 
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 xh[2] = {z4, z4}, xl[2] = {z4, z4}, dx[2] = {z4, z4}, dxl[2] = {z4, z4};
-        float4 pgd[2] = {z4, z4};
-        double invn[2] = {0.0, 0.0};
-        int eidx[2] = {0, 0};
+        float4 xh[2] = {z4, z4}, dx[2] = {z4, z4}, pgd[2] = {z4, z4};
+        const int eidx[2] = {e0, e0 + 32};
         float4 ch = z4, cl = z4, ext = z4;
         int kind = DIRAC;
         float sigma = 0.f;
@@ -397,82 +420,88 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, Plan pl, double* __restri
             sigma = P.gsig[pgi];
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
-                const int e = pgi * G + lane + 32 * r;
-                eidx[r] = e;
-                xh[r] = P.pix.hi[e];
-                xl[r] = P.pix.lo[e];
-                dx[r] = P.pix.off[e];
-                dxl[r] = P.pix.offlo[e];
-                invn[r] = P.pix.d[e].w;
-                if (kind != DIRAC) pgd[r] = P.pgauss[e];
+                xh[r] = P.pix.hi[eidx[r]];
+                dx[r] = P.pix.off[eidx[r]];
+                if (kind != DIRAC) pgd[r] = P.pgauss[eidx[r]];
             }
         }
         const bool gauss = (kind != DIRAC);
         const bool par = (kind == PARAXIAL);
         double tot[2] = {0.0, 0.0};
 
-        for (int g = g0; g < g1; ++g) {
+        for (int gs = g0; gs < g1; gs += NSA) {
+            const int ns = min(NSA, g1 - gs);
             __syncthreads();
-            if (threadIdx.x < G) {
-                const int e = g * G + threadIdx.x;
-                s_off[threadIdx.x] = P.vis.off[e];
-                s_lo[threadIdx.x] = P.vis.offlo[e];
-                s_abs[threadIdx.x] = P.vis.hi[e];
-                const double2 rr = P.r[e];
-                s_r[threadIdx.x] = make_float2((float)rr.x, (float)rr.y);
-                if (GAINS) s_ant[threadIdx.x] = P.ant[e];
-            } else if (threadIdx.x == G) {
-                s_cen[0] = P.vis.cen_hi[g];
-                s_cen[1] = P.vis.cen_lo[g];
-                s_cen[2] = P.vis.ext[g];
+            for (int t = threadIdx.x; t < ns * G; t += NTHREADS) {
+                const int q = t / G, i = t % G;
+                const int e = (gs + q) * G + i;
+                s_off[q][i] = P.vis.off[e];
+                s_lo[q][i] = P.vis.offlo[e];
+                s_abs[q][i] = P.vis.hi[e];
+                const double2 rr = R[e];
+                s_r[q][i] = make_float2((float)rr.x, (float)rr.y);
+                if (GAINS) s_ant[q][i] = P.ant[e];
+            }
+            if (threadIdx.x < ns) {
+                const int g = gs + threadIdx.x;
+                s_cen[threadIdx.x][0] = P.vis.cen_hi[g];
+                s_cen[threadIdx.x][1] = P.vis.cen_lo[g];
+                s_cen[threadIdx.x][2] = P.vis.ext[g];
             }
             __syncthreads();
+            for (int q = 0; q < ns; ++q) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int k = lane + 32 * h;
-                float b = frac_dot3(ch, cl, s_off[k], s_lo[k]);
-                if (gauss) {
-                    const float4 va = s_abs[k];
-                    const GaussConst gc = gauss_const(va.x, va.y, va.z, sigma);
-                    b += gc.cphase;
-                    b -= rintf(b);
-                    const float2 rr = s_r[k];
-                    // r' = id (1 - i beta) r
-                    s_gw[warp][k] = make_float4(gc.gam, gc.coef, gc.id * fmaf(gc.beta, rr.y, rr.x),
-                                                gc.id * fmaf(-gc.beta, rr.x, rr.y));
+                for (int h = 0; h < 2; ++h) {
+                    const int k = lane + 32 * h;
+                    float b = frac_dot3(ch, cl, s_off[q][k], s_lo[q][k]);
+                    if (gauss) {
+                        const float4 va = s_abs[q][k];
+                        const GaussConst gc = gauss_const(va.x, va.y, va.z, sigma);
+                        b = frac_turns(b + gc.cphase);
+                        const float2 rr = s_r[q][k];
+                        // r' = id (1 - i beta) r
+                        s_gw[warp][q][k] = make_float4(gc.gam, gc.coef, gc.id * fmaf(gc.beta, rr.y, rr.x),
+                                                       gc.id * fmaf(-gc.beta, rr.x, rr.y));
+                    }
+                    s_B[warp][q][k] = b;
                 }
-                s_B[warp][k] = b;
             }
             __syncwarp();
-            const float4 yc_h = s_cen[0], yc_l = s_cen[1];
-            const bool exact = dot3(ext, s_cen[2]) > D_MAX;
-            float C[2];
+            for (int q = 0; q < ns; ++q) {
+                const float4 yc_h = s_cen[q][0], yc_l = s_cen[q][1];
+                const bool exact = dot3(ext, s_cen[q][2]) > D_MAX;
+                float C[2];
 #pragma unroll
-            for (int r = 0; r < 2; ++r) C[r] = frac_dot3(xh[r], xl[r], yc_h, yc_l);
-            float acc[2] = {0.f, 0.f};
-            if (!gauss) {
-                if (exact)
-                    adj_dirac_tile<GAINS, true>(s_off, s_lo, s_r, s_ant, s_B[warp], P.gains32, n_ant, eidx, C,
-                                                dx, dxl, acc);
-                else
-                    adj_dirac_tile<GAINS, false>(s_off, s_lo, s_r, s_ant, s_B[warp], P.gains32, n_ant, eidx, C,
-                                                 dx, dxl, acc);
-            } else {
-                if (exact)
-                    adj_gauss_tile<GAINS, true>(s_off, s_lo, s_abs, s_ant, s_B[warp], s_gw[warp], P.gains32,
-                                                n_ant, par, eidx, C, dx, dxl, pgd, acc);
-                else
-                    adj_gauss_tile<GAINS, false>(s_off, s_lo, s_abs, s_ant, s_B[warp], s_gw[warp], P.gains32,
-                                                 n_ant, par, eidx, C, dx, dxl, pgd, acc);
+                for (int r = 0; r < 2; ++r) C[r] = frac_dot3(xh[r], P.pix.lo[eidx[r]], yc_h, yc_l);
+                float acc[2] = {0.f, 0.f};
+                if (!gauss) {
+                    if (exact) {
+                        const float4 dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
+                        adj_dirac_tile<GAINS, true>(s_off[q], s_lo[q], s_r[q], s_ant[q], s_B[warp][q], P.gains32,
+                                                    n_ant, eidx, C, dx, dxl, acc);
+                    } else {
+                        adj_dirac_tile<GAINS, false>(s_off[q], s_lo[q], s_r[q], s_ant[q], s_B[warp][q], P.gains32,
+                                                     n_ant, eidx, C, dx, dx, acc);
+                    }
+                } else {
+                    if (exact) {
+                        const float4 dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
+                        adj_gauss_tile<GAINS, true>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[warp][q],
+                                                    s_gw[warp][q], P.gains32, n_ant, par, eidx, C, dx, dxl, pgd, acc);
+                    } else {
+                        adj_gauss_tile<GAINS, false>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[warp][q],
+                                                     s_gw[warp][q], P.gains32, n_ant, par, eidx, C, dx, dx, pgd, acc);
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < 2; ++r) tot[r] += (double)acc[r];
             }
-#pragma unroll
-            for (int r = 0; r < 2; ++r) tot[r] += (double)acc[r];
         }
         if (pg_ok) {
             const int gb = pl.prob_b0[p] + blk;
             double* dst = partial + (size_t)slot_of(pl, gb) * BLK + warp * G + lane;
 #pragma unroll
-            for (int r = 0; r < 2; ++r) dst[32 * r] = tot[r] * invn[r];
+            for (int r = 0; r < 2; ++r) dst[32 * r] = tot[r] * P.pix.d[eidx[r]].w;
         }
         u += g1 - g0;
     }
@@ -482,34 +511,39 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, Plan pl, double* __restri
 
 int fwd_smem_bytes(int n_ant, bool gains) { return gains ? G * n_ant * (int)sizeof(float2) : 0; }
 
-cudaError_t launch_forward_mixed(bool gains, int n_ant, const DevProblem* probs, const Plan& pl,
+cudaError_t launch_forward_mixed(bool gains, int n_ant, const DevProblem* probs, const Plan* plp, int C,
                                  double2* partial, cudaStream_t st)
 {
     if (gains) {
+        // the dynamic shared-memory limit was raised by occupancy_mixed()
+        // when the batch was built (not here: this may run under capture)
         const int sm = fwd_smem_bytes(n_ant, true);
-        cudaFuncSetAttribute(fwd_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        fwd_mixed_kernel<true><<<pl.C, NTHREADS, sm, st>>>(probs, pl, partial);
+        fwd_mixed_kernel<true><<<C, NTHREADS, sm, st>>>(probs, plp, partial);
     } else {
-        fwd_mixed_kernel<false><<<pl.C, NTHREADS, 0, st>>>(probs, pl, partial);
+        fwd_mixed_kernel<false><<<C, NTHREADS, 0, st>>>(probs, plp, partial);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_mixed(bool gains, const DevProblem* probs, const Plan& pl, double* partial,
-                                 cudaStream_t st)
+cudaError_t launch_adjoint_mixed(bool gains, const DevProblem* probs, const Plan* plp, int C,
+                                 double* partial, cudaStream_t st)
 {
-    if (gains) adj_mixed_kernel<true><<<pl.C, NTHREADS, 0, st>>>(probs, pl, partial);
-    else adj_mixed_kernel<false><<<pl.C, NTHREADS, 0, st>>>(probs, pl, partial);
+    if (gains) adj_mixed_kernel<true><<<C, NTHREADS, 0, st>>>(probs, plp, partial);
+    else adj_mixed_kernel<false><<<C, NTHREADS, 0, st>>>(probs, plp, partial);
     return cudaGetLastError();
 }
 
 int occupancy_mixed(int op, bool gains, int n_ant)
 {
+    static int smem_limit = 0;   // only ever raised, so every earlier batch stays launchable
     int n = 0;
     if (op == 0) {
         if (gains) {
             const int sm = fwd_smem_bytes(n_ant, true);
-            cudaFuncSetAttribute(fwd_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            if (sm > smem_limit) {
+                cudaFuncSetAttribute(fwd_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                smem_limit = sm;
+            }
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fwd_mixed_kernel<true>, NTHREADS, sm);
         } else {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fwd_mixed_kernel<false>, NTHREADS, 0);

@@ -135,9 +135,33 @@ __device__ int block_sum_int(int v, int* sh)
     return r;
 }
 
+// Mode of problem P in a finish kernel: FIN_OP (operator call), FIN_POWER,
+// FIN_INIT, FIN_SOLVE, or -1 (P takes no part in this step).
+__device__ __forceinline__ int fwd_finish_mode(const DevProblem& P)
+{
+    if (!P.st) return FIN_OP;
+    switch (P.st->phase) {
+    case PH_PINIT:
+    case PH_POWER: return FIN_POWER;
+    case PH_SINIT: return FIN_INIT;
+    case PH_SOLVE: return FIN_SOLVE;
+    default: return -1;
+    }
+}
+
+__device__ __forceinline__ int adj_finish_mode(const DevProblem& P)
+{
+    if (!P.st) return FIN_OP;
+    switch (P.st->phase) {
+    case PH_POWER: return FIN_POWER;
+    case PH_SOLVE: return FIN_SOLVE;
+    default: return -1;
+    }
+}
+
 // ---------------------------------------------------------- forward finish
-// One CTA per global owned block (BLK visibilities): sums the block's partial
-// slots in CTA order, then
+// Grid-stride over the plan's owned blocks (BLK visibilities each): sums the
+// block's partial slots in CTA order, then per problem
 //   FIN_OP    : fwd_out = A x
 //   FIN_POWER : r = W (A x)                      (input of the next adjoint)
 //   FIN_INIT  : AI_0 = A I_0, r = W (A I_0 - V), block sum W|A I_0 - V|^2
@@ -145,148 +169,149 @@ __device__ int block_sum_int(int v, int* sh)
 //               A y_{k+1} = AI_k + beta_k (AI_k - AI_{k-1})  (linearity),
 //               r = W (A y_{k+1} - V)
 __global__ void __launch_bounds__(256)
-fwd_finish_kernel(const DevProblem* __restrict__ probs, const SolveBufs* __restrict__ bufs, Plan pl,
-                  const double2* __restrict__ partial, int mode)
+fwd_finish_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ plp,
+                  const double2* __restrict__ partial)
 {
     __shared__ double sh[256];
     __shared__ int shi[256];
-    const int gb = blockIdx.x;
-    const int p = find_blk_prob(pl, gb);
-    const DevProblem& P = probs[p];
-    if (mode != FIN_INIT && P.done && *P.done) return;
-    const int blk = gb - pl.prob_b0[p];
-    const int poff = pl.blk_poff[gb], ncon = pl.blk_ncon[gb];
-    double beta = 0.0;
-    int par = 0;
-    if (mode == FIN_SOLVE) {
-        const SolveState& S = *bufs[p].st;
-        double tn;
-        fista_beta(S.t, tn, beta);
-        par = (S.k + 1) & 1;
-    }
-    double bn = 0.0;
-    int bad = 0;
-    for (int h = 0; h < 2; ++h) {
-        const int i = threadIdx.x + 256 * h;
-        const int e = blk * BLK + i;
-        if (e >= P.vis.n_pad) continue;
-        double2 s = make_double2(0.0, 0.0);
-        for (int c = 0; c < ncon; ++c) {
-            const double2 q = partial[(size_t)(poff + c) * BLK + i];
-            s.x += q.x;
-            s.y += q.y;
+    const Plan pl = *plp;
+    for (int gb = blockIdx.x; gb < pl.n_blocks; gb += gridDim.x) {
+        const int p = find_blk_prob(pl, gb);
+        const DevProblem& P = probs[p];
+        const int mode = fwd_finish_mode(P);
+        if (mode < 0) continue;
+        const int blk = gb - pl.prob_b0[p];
+        const int poff = pl.blk_poff[gb], ncon = pl.blk_ncon[gb];
+        double beta = 0.0;
+        int par = 0;
+        if (mode == FIN_SOLVE) {
+            const SolveState& S = *P.st;
+            double tn;
+            fista_beta(S.t, tn, beta);
+            par = (S.k + 1) & 1;
         }
-        if (!isfinite(s.x) || !isfinite(s.y)) bad = 1;
-        if (mode == FIN_OP) {
-            P.fwd_out[e] = s;
-            continue;
+        double bn = 0.0;
+        int bad = 0;
+        for (int h = 0; h < 2; ++h) {
+            const int i = threadIdx.x + 256 * h;
+            const int e = blk * BLK + i;
+            if (e >= P.vis.n_pad) continue;
+            double2 s = make_double2(0.0, 0.0);
+            for (int c = 0; c < ncon; ++c) {
+                const double2 q = partial[(size_t)(poff + c) * BLK + i];
+                s.x += q.x;
+                s.y += q.y;
+            }
+            if (!isfinite(s.x) || !isfinite(s.y)) bad = 1;
+            if (mode == FIN_OP) {
+                P.fwd_out[e] = s;
+                continue;
+            }
+            const SolveBufs& B = P.b;
+            const double W = P.vis.d[e].w;
+            if (mode == FIN_POWER) {
+                B.r[e] = make_double2(W * s.x, W * s.y);
+                continue;
+            }
+            const double2 V = P.V[e];
+            const double dr = s.x - V.x, di = s.y - V.y;
+            bn += W * (dr * dr + di * di);
+            if (mode == FIN_INIT) {
+                B.AI[0][e] = s;
+                B.r[e] = make_double2(W * dr, W * di);
+            } else {
+                const double2 old = B.AI[par ^ 1][e];
+                B.AI[par][e] = s;
+                const double ayr = s.x + beta * (s.x - old.x);
+                const double ayi = s.y + beta * (s.y - old.y);
+                B.r[e] = make_double2(W * (ayr - V.x), W * (ayi - V.y));
+            }
         }
-        const SolveBufs& B = bufs[p];
-        const double W = P.vis.d[e].w;
-        if (mode == FIN_POWER) {
-            B.r[e] = make_double2(W * s.x, W * s.y);
-            continue;
+        if (mode == FIN_OP) continue;
+        const int nb = block_sum_int(bad, shi);
+        const double tot = block_sum(bn, sh);
+        if (threadIdx.x == 0) {
+            P.b.blk_badv[blk] = nb;
+            if (mode != FIN_POWER) P.b.blk_r2[blk] = tot;
         }
-        const double2 V = P.V[e];
-        const double dr = s.x - V.x, di = s.y - V.y;
-        bn += W * (dr * dr + di * di);
-        if (mode == FIN_INIT) {
-            B.AI[0][e] = s;
-            B.r[e] = make_double2(W * dr, W * di);
-        } else {
-            const double2 old = B.AI[par ^ 1][e];
-            B.AI[par][e] = s;
-            const double ayr = s.x + beta * (s.x - old.x);
-            const double ayi = s.y + beta * (s.y - old.y);
-            B.r[e] = make_double2(W * (ayr - V.x), W * (ayi - V.y));
-        }
-    }
-    if (mode == FIN_OP || mode == FIN_POWER) {
-        if (mode == FIN_POWER) {
-            const int nb = block_sum_int(bad, shi);
-            if (threadIdx.x == 0) bufs[p].blk_badv[blk] = nb;
-        }
-        return;
-    }
-    const double tot = block_sum(bn, sh);
-    const int nb = block_sum_int(bad, shi);
-    if (threadIdx.x == 0) {
-        bufs[p].blk_r2[blk] = tot;
-        bufs[p].blk_badv[blk] = nb;
     }
 }
 
 // ---------------------------------------------------------- adjoint finish
 //   FIN_OP    : adj_out = Re A^H r
-//   FIN_POWER : z = Re A^H W A x into xv, block sum z^2
+//   FIN_POWER : z = (Re A^H W A x) * inv_mu into xv (= B x_unit), block sum z^2
 //   FIN_SOLVE : I_k = T^{lambda/L}(y_k - g/L)                 (Eq. threshp)
 //               y_{k+1} = I_k + beta_k (I_k - I_{k-1})        (FISTA box)
 //               block sums of I_k and of nnz
 __global__ void __launch_bounds__(256)
-adj_finish_kernel(const DevProblem* __restrict__ probs, const SolveBufs* __restrict__ bufs, Plan pl,
-                  const double* __restrict__ partial, int mode)
+adj_finish_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ plp,
+                  const double* __restrict__ partial)
 {
     __shared__ double sh[256];
     __shared__ int shi[256];
-    const int gb = blockIdx.x;
-    const int p = find_blk_prob(pl, gb);
-    const DevProblem& P = probs[p];
-    if (P.done && *P.done) return;
-    const int blk = gb - pl.prob_b0[p];
-    const int poff = pl.blk_poff[gb], ncon = pl.blk_ncon[gb];
-    double inv_L = 0.0, thr = 0.0, beta = 0.0;
-    int par = 0;
-    if (mode == FIN_SOLVE) {
-        const SolveState& S = *bufs[p].st;
-        double tn;
-        fista_beta(S.t, tn, beta);
-        inv_L = 1.0 / S.L;
-        thr = S.lambda / S.L;
-        par = (S.k + 1) & 1;
-        if (gb == pl.prob_b0[p] && threadIdx.x == 0) bufs[p].st->parity = par;
-    }
-    double acc = 0.0;
-    int cnt = 0, bad = 0;
-    for (int h = 0; h < 2; ++h) {
-        const int i = threadIdx.x + 256 * h;
-        const int e = blk * BLK + i;
-        if (e >= P.pix.n_pad) continue;
-        double s = 0.0;
-        for (int c = 0; c < ncon; ++c) s += partial[(size_t)(poff + c) * BLK + i];
-        if (!isfinite(s)) bad = 1;
-        if (mode == FIN_OP) {
-            P.adj_out[e] = s;
-            continue;
+    const Plan pl = *plp;
+    for (int gb = blockIdx.x; gb < pl.n_blocks; gb += gridDim.x) {
+        const int p = find_blk_prob(pl, gb);
+        const DevProblem& P = probs[p];
+        const int mode = adj_finish_mode(P);
+        if (mode < 0) continue;
+        const int blk = gb - pl.prob_b0[p];
+        const int poff = pl.blk_poff[gb], ncon = pl.blk_ncon[gb];
+        double inv_L = 0.0, thr = 0.0, beta = 0.0, scale = 1.0;
+        int par = 0;
+        if (mode == FIN_SOLVE) {
+            const SolveState& S = *P.st;
+            double tn;
+            fista_beta(S.t, tn, beta);
+            inv_L = 1.0 / S.L;
+            thr = S.lambda / S.L;
+            par = (S.k + 1) & 1;
+        } else if (mode == FIN_POWER) {
+            scale = P.st->inv_mu;
         }
-        const SolveBufs& B = bufs[p];
-        if (mode == FIN_POWER) {
-            B.xv[e] = s;
-            acc += s * s;
-            continue;
+        double acc = 0.0;
+        int cnt = 0, bad = 0;
+        for (int h = 0; h < 2; ++h) {
+            const int i = threadIdx.x + 256 * h;
+            const int e = blk * BLK + i;
+            if (e >= P.pix.n_pad) continue;
+            double s = 0.0;
+            for (int c = 0; c < ncon; ++c) s += partial[(size_t)(poff + c) * BLK + i];
+            if (!isfinite(s)) bad = 1;
+            if (mode == FIN_OP) {
+                P.adj_out[e] = s;
+                continue;
+            }
+            const SolveBufs& B = P.b;
+            if (mode == FIN_POWER) {
+                const double z = s * scale;
+                B.xv[e] = z;
+                acc += z * z;
+                continue;
+            }
+            // FIN_SOLVE
+            const double v = B.y[e] - s * inv_L;
+            double In = v > thr ? v - thr : 0.0;
+            if (P.pix.orig[e] < 0) In = 0.0;
+            const double Io = B.I[par ^ 1][e];
+            B.I[par][e] = In;
+            B.y[e] = In + beta * (In - Io);
+            acc += In;
+            cnt += In > 0.0;
         }
-        // FIN_SOLVE
-        const double v = B.y[e] - s * inv_L;
-        double In = v > thr ? v - thr : 0.0;
-        if (P.pix.orig[e] < 0) In = 0.0;
-        const double Io = B.I[par ^ 1][e];
-        B.I[par][e] = In;
-        B.y[e] = In + beta * (In - Io);
-        acc += In;
-        cnt += In > 0.0;
-    }
-    if (mode == FIN_OP) return;
-    const double tot = block_sum(acc, sh);
-    const int nb = block_sum_int(bad, shi);
-    int nz = 0;
-    if (mode == FIN_SOLVE) nz = block_sum_int(cnt, shi);
-    if (threadIdx.x == 0) {
-        const SolveBufs& B = bufs[p];
-        if (mode == FIN_POWER) B.blk_z2[blk] = tot;
-        else {
-            B.blk_l1[blk] = tot;
-            B.blk_nnz[blk] = nz;
+        if (mode == FIN_OP) continue;
+        const double tot = block_sum(acc, sh);
+        const int nb = block_sum_int(bad, shi);
+        const int nz = block_sum_int(cnt, shi);
+        if (threadIdx.x == 0) {
+            const SolveBufs& B = P.b;
+            if (mode == FIN_POWER) B.blk_z2[blk] = tot;
+            else {
+                B.blk_l1[blk] = tot;
+                B.blk_nnz[blk] = nz;
+            }
+            B.blk_badp[blk] = nb;
         }
-        B.blk_badp[blk] = nb;
     }
 }
 
@@ -308,100 +333,118 @@ __device__ long long warp_sum_fixed_i(const int* a, int n)
     return s;
 }
 
-__global__ void scalars_kernel(const SolveBufs* __restrict__ bufs, const DevProblem* __restrict__ probs,
-                               int mode)
+// The phase machine of every solve in the batch (end of a tick).
+__global__ void scalars_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ n_probs)
 {
-    const int p = blockIdx.x;
-    const SolveBufs& B = bufs[p];
-    const DevProblem& P = probs[p];
-    SolveState& S = *B.st;
-    const int nvb = P.vis.n_blk, npb = P.pix.n_blk;
-    if (mode == FIN_POWER) {
-        if (S.pdone) return;
-        const double z2 = warp_sum_fixed(B.blk_z2, npb);
-        const long long bad = warp_sum_fixed_i(B.blk_badv, nvb) + warp_sum_fixed_i(B.blk_badp, npb);
-        if (threadIdx.x == 0) {
-            const double mu = sqrt(z2);
-            S.pit += 1;
-            if (bad || !isfinite(mu)) {
-                S.nonfinite = 1;
-                S.pdone = 1;
-            } else {
-                if ((S.pit > 1 && fabs(mu - S.mu_prev) <= S.ptol * mu) || S.pit >= S.pmax || mu == 0.0)
-                    S.pdone = 1;
+    const int np = *n_probs;
+    for (int p = blockIdx.x; p < np; p += gridDim.x) {
+        const DevProblem& P = probs[p];
+        if (!P.st) continue;
+        SolveState& S = *P.st;
+        const SolveBufs& B = P.b;
+        const int nvb = P.vis.n_blk, npb = P.pix.n_blk;
+        const int ph = S.phase;
+        if (ph == PH_PINIT) {
+            if (threadIdx.x == 0) S.phase = PH_POWER;
+        } else if (ph == PH_POWER) {
+            const double z2 = warp_sum_fixed(B.blk_z2, npb);
+            const long long bad = warp_sum_fixed_i(B.blk_badv, nvb) + warp_sum_fixed_i(B.blk_badp, npb);
+            if (threadIdx.x == 0) {
+                const double mu = sqrt(z2);
+                S.pit += 1;
+                if (bad || !isfinite(mu) || mu == 0.0) {
+                    S.nonfinite = (bad || !isfinite(mu)) ? 1 : 0;
+                    S.mu = mu;
+                    S.phase = PH_DONE;
+                } else {
+                    const bool conv = (S.pit > 1 && fabs(mu - S.mu_prev) <= S.ptol * mu) || S.pit >= S.pmax;
+                    S.mu = mu;
+                    S.mu_prev = mu;
+                    S.inv_mu = 1.0 / mu;
+                    if (conv) {
+                        S.L = mu;
+                        S.phase = S.power_only ? PH_DONE : PH_SINIT;
+                    }
+                }
             }
-            S.mu = mu;
-            S.mu_prev = mu;
-            S.inv_mu = mu > 0.0 ? 1.0 / mu : 0.0;
+        } else if (ph == PH_SINIT) {
+            const double r2 = warp_sum_fixed(B.blk_r2, nvb);
+            const long long bad = warp_sum_fixed_i(B.blk_badv, nvb);
+            if (threadIdx.x == 0) {
+                S.resid2 = r2;
+                S.E_prev = 0.5 * r2 + S.lambda * S.l1;
+                S.E = S.E_prev;
+                S.k = 0;
+                S.t = 1.0;
+                S.converged = 0;
+                S.nonfinite = bad ? 1 : 0;
+                S.phase = (S.max_iter <= 0 || bad) ? PH_DONE : PH_SOLVE;
+            }
+        } else if (ph == PH_SOLVE) {
+            const double r2 = warp_sum_fixed(B.blk_r2, nvb);
+            const double l1 = warp_sum_fixed(B.blk_l1, npb);
+            const long long nnz = warp_sum_fixed_i(B.blk_nnz, npb);
+            const long long bad = warp_sum_fixed_i(B.blk_badv, nvb) + warp_sum_fixed_i(B.blk_badp, npb);
+            if (threadIdx.x == 0) {
+                double tn, beta;
+                fista_beta(S.t, tn, beta);
+                const double E = 0.5 * r2 + S.lambda * l1;
+                S.k += 1;
+                S.t = tn;
+                S.beta = beta;
+                S.resid2 = r2;
+                S.l1 = l1;
+                S.nnz = nnz;
+                S.E = E;
+                bool done = false;
+                if (bad || !isfinite(E)) {
+                    S.nonfinite = 1;
+                    done = true;
+                }
+                if (S.tol > 0.0 && fabs(E - S.E_prev) <= S.tol * S.E_prev) {
+                    S.converged = 1;
+                    done = true;
+                }
+                if (S.k >= S.max_iter) done = true;
+                S.E_prev = E;
+                if (done) S.phase = PH_DONE;
+            }
         }
-        return;
-    }
-    if (mode == FIN_INIT) {
-        const double r2 = warp_sum_fixed(B.blk_r2, nvb);
-        const long long bad = warp_sum_fixed_i(B.blk_badv, nvb);
-        if (threadIdx.x == 0) {
-            S.resid2 = r2;
-            S.E_prev = 0.5 * r2 + S.lambda * S.l1;
-            S.E = S.E_prev;
-            S.k = 0;
-            S.t = 1.0;
-            S.converged = 0;
-            S.nonfinite = bad ? 1 : 0;
-            S.done = (S.max_iter <= 0 || bad) ? 1 : 0;
-        }
-        return;
-    }
-    // FIN_SOLVE
-    if (S.done) return;
-    const double r2 = warp_sum_fixed(B.blk_r2, nvb);
-    const double l1 = warp_sum_fixed(B.blk_l1, npb);
-    const long long nnz = warp_sum_fixed_i(B.blk_nnz, npb);
-    const long long bad = warp_sum_fixed_i(B.blk_badv, nvb) + warp_sum_fixed_i(B.blk_badp, npb);
-    if (threadIdx.x == 0) {
-        double tn, beta;
-        fista_beta(S.t, tn, beta);
-        const double E = 0.5 * r2 + S.lambda * l1;
-        S.k += 1;
-        S.t = tn;
-        S.beta = beta;
-        S.resid2 = r2;
-        S.l1 = l1;
-        S.nnz = nnz;
-        S.E = E;
-        if (bad || !isfinite(E)) {
-            S.nonfinite = 1;
-            S.done = 1;
-        }
-        if (S.tol > 0.0 && fabs(E - S.E_prev) <= S.tol * S.E_prev) {
-            S.converged = 1;
-            S.done = 1;
-        }
-        if (S.k >= S.max_iter) S.done = 1;
-        S.E_prev = E;
     }
 }
 
-cudaError_t launch_fwd_finish(const DevProblem* probs, const SolveBufs* bufs, const Plan& pl,
-                              const double2* partial, int mode, cudaStream_t st)
+// Phase of every problem of a batch, for the host (one int per problem).
+__global__ void phases_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ n_probs,
+                              int* __restrict__ out)
 {
-    if (pl.n_blocks == 0) return cudaSuccess;
-    fwd_finish_kernel<<<pl.n_blocks, 256, 0, st>>>(probs, bufs, pl, partial, mode);
+    const int np = *n_probs;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x)
+        out[p] = probs[p].st ? probs[p].st->phase : PH_IDLE;
+}
+
+cudaError_t launch_fwd_finish(const DevProblem* probs, const Plan* plp, int grid, const double2* partial,
+                              cudaStream_t st)
+{
+    fwd_finish_kernel<<<grid, 256, 0, st>>>(probs, plp, partial);
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_finish(const DevProblem* probs, const SolveBufs* bufs, const Plan& pl,
-                              const double* partial, int mode, cudaStream_t st)
+cudaError_t launch_adj_finish(const DevProblem* probs, const Plan* plp, int grid, const double* partial,
+                              cudaStream_t st)
 {
-    if (pl.n_blocks == 0) return cudaSuccess;
-    adj_finish_kernel<<<pl.n_blocks, 256, 0, st>>>(probs, bufs, pl, partial, mode);
+    adj_finish_kernel<<<grid, 256, 0, st>>>(probs, plp, partial);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scalars(const SolveBufs* bufs, const DevProblem* probs, int n_probs, int mode,
-                           cudaStream_t st)
+cudaError_t launch_scalars(const DevProblem* probs, const int* n_probs, int grid, cudaStream_t st)
 {
-    if (n_probs <= 0) return cudaSuccess;
-    scalars_kernel<<<n_probs, 32, 0, st>>>(bufs, probs, mode);
+    scalars_kernel<<<grid, 32, 0, st>>>(probs, n_probs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phases(const DevProblem* probs, const int* n_probs, int grid, int* out, cudaStream_t st)
+{
+    phases_kernel<<<grid, 128, 0, st>>>(probs, n_probs, out);
     return cudaGetLastError();
 }
 

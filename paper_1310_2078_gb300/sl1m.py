@@ -33,6 +33,8 @@ EXPORTS = [
     "sl1m_forward_dev", "sl1m_adjoint_dev", "sl1m_max_eig", "sl1m_solve",
     "sl1m_profile_enable", "sl1m_profile_reset", "sl1m_profile_read", "sl1m_problem_bytes",
     "sl1m_counters", "sl1m_counters_reset", "sl1m_plan_preview", "sl1m_granule_order",
+    "sl1m_server_start", "sl1m_server_submit", "sl1m_server_poll", "sl1m_server_wait",
+    "sl1m_server_stop", "sl1m_server_info",
 ]
 
 
@@ -41,6 +43,20 @@ class SolveOpts(C.Structure):
                 ("max_iter", C.c_int32), ("precision", C.c_int32),
                 ("power_max_iter", C.c_int32), ("power_tol", C.c_double),
                 ("x0", C.c_void_p)]
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("mem_budget_bytes", C.c_int64), ("max_slots", C.c_int32),
+                ("ticks_per_round", C.c_int32), ("precision", C.c_int32)]
+
+
+class ServerInfo(C.Structure):
+    _fields_ = [("queued", C.c_int64), ("active", C.c_int64), ("finished", C.c_int64),
+                ("max_active", C.c_int64), ("bytes_in_use", C.c_int64),
+                ("bytes_budget", C.c_int64), ("ticks", C.c_int64), ("rounds", C.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class SolveStats(C.Structure):
@@ -102,6 +118,12 @@ def load():
             "sl1m_plan_preview": ([i32, vp, vp, i32, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32),
                                    vp, vp, vp], C.c_int),
             "sl1m_granule_order": ([i64, vp, vp, C.POINTER(i64)], C.c_int),
+            "sl1m_server_start": ([vp, C.POINTER(ServerOpts)], C.c_int),
+            "sl1m_server_submit": ([vp, vp, C.POINTER(SolveOpts), C.POINTER(C.c_uint64)], C.c_int),
+            "sl1m_server_poll": ([vp, C.c_uint64, C.POINTER(C.c_int)], C.c_int),
+            "sl1m_server_wait": ([vp, C.c_uint64, d, vp, C.POINTER(SolveStats)], C.c_int),
+            "sl1m_server_stop": ([vp], C.c_int),
+            "sl1m_server_info": ([vp, C.POINTER(ServerInfo)], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -215,6 +237,40 @@ class Context:
 
     def counters_reset(self):
         self.check(self.lib.sl1m_counters_reset(self.h))
+
+    # ---- continuous-batching server (sl1m_server_*)
+    def server_start(self, mem_budget_bytes=0, max_slots=0, ticks_per_round=0, precision=MIXED):
+        o = ServerOpts(int(mem_budget_bytes), int(max_slots), int(ticks_per_round), int(precision))
+        self.check(self.lib.sl1m_server_start(self.h, C.byref(o)))
+
+    def server_submit(self, problem, lam, L=0.0, max_iter=200, rel_tol=0.0, x0=None,
+                      power_max_iter=0, power_tol=0.0):
+        x0a = _f64(x0)
+        o = SolveOpts(float(lam), float(L), float(rel_tol), int(max_iter), MIXED,
+                      int(power_max_iter), float(power_tol), _ptr(x0a))
+        t = C.c_uint64()
+        self.check(self.lib.sl1m_server_submit(self.h, problem.h, C.byref(o), C.byref(t)))
+        return t.value
+
+    def server_poll(self, ticket):
+        d = C.c_int()
+        self.check(self.lib.sl1m_server_poll(self.h, C.c_uint64(ticket), C.byref(d)))
+        return bool(d.value)
+
+    def server_wait(self, ticket, problem, timeout_s=-1.0):
+        img = np.zeros(problem.n_pix)
+        st = SolveStats()
+        self.check(self.lib.sl1m_server_wait(self.h, C.c_uint64(ticket), float(timeout_s), _ptr(img),
+                                             C.byref(st)))
+        return img, st.as_dict()
+
+    def server_stop(self):
+        self.check(self.lib.sl1m_server_stop(self.h))
+
+    def server_info(self):
+        i = ServerInfo()
+        self.check(self.lib.sl1m_server_info(self.h, C.byref(i)))
+        return i.as_dict()
 
     def close(self):
         if getattr(self, "h", None):
