@@ -119,6 +119,28 @@ int sl1m_adjoint(sl1m_problem* prob, const double* r, double* img_out, int preci
 int sl1m_forward_dev(sl1m_problem* prob, const double* x_dev, double* vis_out_dev, int precision);
 int sl1m_adjoint_dev(sl1m_problem* prob, const double* r_dev, double* img_out_dev, int precision);
 
+/* Forward operator for callers that cannot allocate device memory at the time
+ * of the call (device memory owned by a pool or another framework, or a loop
+ * that must not enter the allocator).  Same result as sl1m_forward_dev; the
+ * paper has no counterpart (this is plumbing, not a step of the method).
+ *   - Allocates nothing: all of its scratch (descriptor, work-split tables,
+ *     input in the library's pixel order, partial sums, output before
+ *     reordering) lives in one static device array of 32 MiB that every GPU
+ *     loading libsl1m holds until the process exits.  Problems needing more
+ *     return SL1M_ERR_ARG with the size they need.
+ *   - The problem must already be laid out on the device by an earlier,
+ *     allocating call of this library (e.g. sl1m_forward); otherwise
+ *     SL1M_ERR_STATE.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before any
+ *     stream capture.
+ *   - All calls share the one array and each leaves its data there: calls
+ *     whose work overlaps on the GPU (other streams, other contexts, other
+ *     host threads) race and must be serialised by the caller.
+ *   - x_dev [n_pix] and vis_out_dev [n_vis][2] are device pointers in the
+ *     caller's order; asynchronous on the context's stream. */
+int sl1m_forward_noalloc(sl1m_problem* prob, const double* x_dev, double* vis_out_dev, int precision);
+
 /* Step constant of FISTA (Sect. 3, algorithm box: L = largest eigenvalue of
  * M*M; the paper uses "an algorithm to calculate the largest eigenvalue",
  * Sect. 3.1).  Power iteration on B = Re(A^H W A) from x = 1/sqrt(n_pix):

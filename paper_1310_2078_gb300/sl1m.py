@@ -34,7 +34,7 @@ EXPORTS = [
     "sl1m_profile_enable", "sl1m_profile_reset", "sl1m_profile_read", "sl1m_problem_bytes",
     "sl1m_counters", "sl1m_counters_reset", "sl1m_plan_preview", "sl1m_granule_order",
     "sl1m_server_start", "sl1m_server_submit", "sl1m_server_poll", "sl1m_server_wait",
-    "sl1m_server_stop", "sl1m_server_info",
+    "sl1m_server_stop", "sl1m_server_info", "sl1m_forward_noalloc",
 ]
 
 
@@ -105,6 +105,7 @@ def load():
             "sl1m_forward": ([vp, vp, vp, C.c_int], C.c_int),
             "sl1m_adjoint": ([vp, vp, vp, C.c_int], C.c_int),
             "sl1m_forward_dev": ([vp, vp, vp, C.c_int], C.c_int),
+            "sl1m_forward_noalloc": ([vp, vp, vp, C.c_int], C.c_int),
             "sl1m_adjoint_dev": ([vp, vp, vp, C.c_int], C.c_int),
             "sl1m_max_eig": ([vp, C.c_int, d, C.c_int, C.POINTER(d), C.POINTER(C.c_int)], C.c_int),
             "sl1m_solve": ([vp, C.POINTER(SolveOpts), vp, C.POINTER(SolveStats)], C.c_int),
@@ -338,6 +339,10 @@ class Problem:
     def forward_dev(self, x_t, out_t, precision=MIXED):
         """x_t: float64 CUDA tensor [n_pix]; out_t: float64 CUDA tensor [n_vis, 2]."""
         self.ctx.check(self.lib.sl1m_forward_dev(self.h, _tptr(x_t), _tptr(out_t), int(precision)))
+
+    def forward_noalloc(self, x_t, out_t, precision=MIXED):
+        """sl1m_forward_noalloc: like forward_dev, scratch in a static device array."""
+        self.ctx.check(self.lib.sl1m_forward_noalloc(self.h, _tptr(x_t), _tptr(out_t), int(precision)))
 
     def adjoint_dev(self, r_t, out_t, precision=MIXED):
         """r_t: float64 CUDA tensor [n_vis, 2]; out_t: float64 CUDA tensor [n_pix]."""
