@@ -53,12 +53,17 @@ def parse():
     ap.add_argument("--iters", type=int, default=200)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the (untimed) tile-shape autotuner")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ops-only", action="store_true",
+                    help="a step is one forward + one adjoint through the C ABI (device pointers)")
     ap.add_argument("--serve", action="store_true",
                     help="serving workload: Poisson stream of independent solves through the server")
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--fp64-sample", type=int, default=3)
+    ap.add_argument("--ticks", type=int, default=4, help="serving: ticks per round")
+    ap.add_argument("--max-pairs", type=float, default=4e9, help="serving: work in flight per tick")
     return ap.parse_args()
 
 
@@ -250,7 +255,7 @@ def run_serve(args):
         probs.append((P, V))
     torch.cuda.synchronize()
     ctx.counters_reset()
-    ctx.server_start(max_slots=64, ticks_per_round=4)
+    ctx.server_start(max_slots=64, ticks_per_round=args.ticks, max_pairs_per_tick=args.max_pairs)
     clocks = ClockSampler(dev)
     clocks.start()
     t0 = time.perf_counter()
@@ -291,7 +296,8 @@ def run_serve(args):
            "config": {"workload": f"serving: {args.requests} requests, Poisson {args.rate}/s, "
                                   "pixels logU(4k,256k), visibilities logU(2k,100k), "
                                   "Dirac/wide-Gaussian 50/50, gains on 50%",
-                      "max_slots": 64, "ticks_per_round": 4},
+                      "max_slots": 64, "ticks_per_round": args.ticks,
+                      "max_pairs_per_tick": args.max_pairs},
            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                          "mean": float(lat.mean()), "max": float(lat.max())},
            "pairs_per_s": pairs / T, "wall_s": T,
@@ -327,10 +333,21 @@ def main():
     V = P.forward(w.x_true, sl1m.FP64 if w.n_vis * w.n_pix < 5e9 else sl1m.MIXED) + w.noise
     P.set_vis_data(V)
     lam = w.lambda_frac * P.adjoint(V * (1 if w.weights is None else w.weights), prec).max()
+    tuned = None if args.no_autotune else P.autotune(prec)      # untimed set-up
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
 
-    def one_step():
-        return P.solve(lam, L=0.0, max_iter=args.iters, precision=prec)
+    if args.ops_only:
+        xs = torch.tensor(np.abs(w.x_true) + 0.01, dtype=torch.float64, device=f"cuda:{dev}")
+        vs = torch.zeros((w.n_vis, 2), dtype=torch.float64, device=f"cuda:{dev}")
+        img_d = torch.zeros(w.n_pix, dtype=torch.float64, device=f"cuda:{dev}")
+
+        def one_step():
+            P.forward_dev(xs, vs, prec)
+            P.adjoint_dev(vs, img_d, prec)
+            return None, {"iters": 0, "power_iters": 0, "E": 0.0, "resid2": 0.0, "nnz": 0, "L": 0.0}
+    else:
+        def one_step():
+            return P.solve(lam, L=0.0, max_iter=args.iters, precision=prec)
 
     for _ in range(args.warmup):
         one_step()
@@ -397,7 +414,7 @@ def main():
            "share_of_step": fin_ms / (T * 1e3)}
 
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not args.ops_only:
         e2e = run_e2e(ctx, w, V, lam, prec, args, sl1m, stream)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -409,9 +426,11 @@ def main():
                "scaling": "weak", "vs_baseline": None,
                "dtype": "f32+f64" if prec == sl1m.MIXED else "f64", "data": "synthetic",
                "config": {"workload": w.name, "n_pix": w.n_pix, "n_vis": w.n_vis,
-                          "step": f"one solve: power iteration (<=50) + {args.iters} FISTA steps",
+                          "step": ("one forward + one adjoint (device pointers)" if args.ops_only else
+                                   f"one solve: power iteration (<=50) + {args.iters} FISTA steps"),
                           "precision": args.precision, "lambda": lam,
                           "l2": "flushed between steps (268 MB write)",
+                          "tile_shape": tuned,
                           "parallelism": f"replicas{ws}" if ws > 1 else "1 GPU"},
                "solves_per_s": solves_per_s,
                "iters": [s["iters"] for s in stats], "power_iters": stats[-1]["power_iters"],

@@ -102,8 +102,8 @@ int sl1m_set_pixels(sl1m_problem* prob, int64_t n_pix, const double* lm,
  * between each pixel and each antenna element"): G [n_pix][n_ant][2],
  * per pixel and antenna; the entry for visibility k is multiplied by
  * g_jk = G[j][a_k] * conj(G[j][b_k]).  G == NULL or n_ant == 0 removes the
- * gains.  The mixed-precision forward holds a pixel tile's gains for all
- * antennas in shared memory and supports n_ant <= 400. */
+ * gains.  The mixed-precision kernels hold one pixel granule's gains for all
+ * antennas in shared memory: n_ant <= 320 (SL1M_ERR_ARG above). */
 int sl1m_set_gains(sl1m_problem* prob, int32_t n_ant, const double* G);
 
 /* Forward operator, Eq. sme: vis_out_k = sum_j A_kj x_j.
@@ -140,6 +140,13 @@ int sl1m_adjoint_dev(sl1m_problem* prob, const double* r_dev, double* img_out_de
  *   - x_dev [n_pix] and vis_out_dev [n_vis][2] are device pointers in the
  *     caller's order; asynchronous on the context's stream. */
 int sl1m_forward_noalloc(sl1m_problem* prob, const double* x_dev, double* vis_out_dev, int precision);
+
+/* Dirty image: the back-projection of the measured data, Re(A^H W V)
+ * (Sect. 3: the gradient at I = 0; Sect. 4.4 proposes it as a starting
+ * point).  img_out [n_pix] (host, may be NULL); lambda_max_out (may be NULL)
+ * receives max_j of it, the smallest lambda for which the solution of the
+ * algorithm box is exactly zero.  Synchronous. */
+int sl1m_dirty_image(sl1m_problem* prob, int precision, double* img_out, double* lambda_max_out);
 
 /* Step constant of FISTA (Sect. 3, algorithm box: L = largest eigenvalue of
  * M*M; the paper uses "an algorithm to calculate the largest eigenvalue",
@@ -200,8 +207,13 @@ int sl1m_solve(sl1m_problem* prob, const sl1m_solve_opts* opts, double* img_out,
 typedef struct {
     int64_t mem_budget_bytes;   /* 0 = 80% of the device memory free at start   */
     int32_t max_slots;          /* 0 = 64 concurrent solves                      */
-    int32_t ticks_per_round;    /* 0 = 8 steps between admission/retirement     */
+    int32_t ticks_per_round;    /* 0 = 4 steps between admission/retirement     */
     int32_t precision;          /* SL1M_MIXED or SL1M_FP64 for every request     */
+    int32_t reserved;
+    double max_pairs_per_tick;  /* work in flight: admit (in arrival order) while
+                                   the summed n_vis*n_pix of running solves stays
+                                   below this; 0 = 4e9 (enough to fill the GPU);
+                                   one request is always admitted              */
 } sl1m_server_opts;
 
 /* Start the request loop (opts may be NULL for defaults). */
@@ -236,6 +248,50 @@ typedef struct {
 } sl1m_server_info_t;
 int sl1m_server_info(sl1m_ctx* ctx, sl1m_server_info_t* info);
 
+/* Autotuner of the operator kernels' tile shape: for the forward and the
+ * adjoint of this problem it times every candidate -- streamed granules per
+ * shared-memory stage (2, 4 or 8; the mixed no-gains kernels) times the
+ * persistent grid (1 .. occupancy CTAs per SM) -- with CUDA events and keeps
+ * the fastest in the context, keyed by (precision, operator, gains, Gaussian
+ * pixels, log2 of the work units).  Later launches of problems with the same
+ * key -- single solves and server batches -- use it.  nst_out and
+ * ctas_per_sm_out ([2]: forward, adjoint) may be NULL.  Synchronous. */
+int sl1m_autotune(sl1m_problem* prob, int precision, int32_t* nst_out, int32_t* ctas_per_sm_out);
+
+/* ---- Adaptive quadtree refinement (Sect. 4.4) ---------------------------
+ * The pixels set on the problem (Dirac, a regular grid of spacing delta0, no
+ * gains) are solved first; then, level by level, every pixel above
+ * refine_frac * (peak of the last image) is replaced by its four quadrant
+ * children at half its spacing (offsets +-spacing/4), unrefined pixels are
+ * kept when keep_unrefined, and the problem is solved again with `opts`
+ * (L recomputed per level when opts->L == 0), starting from each parent's
+ * flux shared equally among its children.  The paper splits every pixel
+ * above 1% of the maximum, from 64" to 2" (5 levels).  On return the problem
+ * holds the final pixel set; sl1m_get_solution gives it and the image. */
+typedef struct {
+    int32_t levels;          /* refinements after the first solve (0..16)      */
+    double refine_frac;      /* split pixels above this fraction of the peak   */
+    int32_t keep_unrefined;  /* 1: keep the pixels that are not split          */
+} sl1m_refine_opts;
+
+typedef struct {
+    int32_t levels_done;         /* solves run                                   */
+    int64_t n_pix[17];           /* pixels per solve                             */
+    int32_t iters[17];           /* FISTA steps per solve                        */
+    int32_t power_iters[17];     /* power-iteration steps per solve              */
+    int64_t final_n_pix;
+    double total_pair_evals;     /* pixel-visibility pairs evaluated, all solves */
+    sl1m_solve_stats last;       /* stats of the last solve                      */
+} sl1m_refine_stats;
+
+int sl1m_solve_refine(sl1m_problem* prob, const sl1m_solve_opts* opts, const sl1m_refine_opts* ropts,
+                      double delta0, sl1m_refine_stats* stats);
+
+/* The problem's current pixels (lm_out [n_pix][2]) and the image of its last
+ * refinement (img_out [n_pix]); any pointer may be NULL (n_pix alone sizes
+ * the buffers). */
+int sl1m_get_solution(const sl1m_problem* prob, int64_t* n_pix, double* lm_out, double* img_out);
+
 /* Kernel timing with CUDA events on the context's stream (for benchmarks).
  * Kernel ids: 0 forward FP64, 1 adjoint FP64, 2 forward mixed, 3 adjoint
  * mixed, 4 forward finish, 5 adjoint finish (solver vector updates), 6 other.
@@ -256,13 +312,17 @@ int sl1m_counters_reset(sl1m_ctx* ctx);
 /* Host-only inspection of the work split (no GPU needed).  Work on a batch
  * of problems is cut into units (owned block of 512 elements x streamed
  * granule of 64), owned_blocks[p] * streamed_granules[p] per problem, and
- * spread over n_ctas = min(max_ctas, units) persistent CTAs: CTA c takes units
- * [c U / C, (c+1) U / C).  For every block (problems in order) the call
- * returns the first contributing CTA, their count and the first partial-sum
- * slot; arrays are sized by the total number of blocks. */
+ * spread over n_ctas = min(max_ctas, units) persistent CTAs.  Without
+ * unit_costs, CTA c takes units [c U / C, (c+1) U / C); with unit_costs
+ * [total units] (relative cost of each unit, problems in order, block-major)
+ * the boundaries cut the summed cost into n_ctas equal parts, as the library
+ * does for tiles of unequal cost.  Returns, per block (problems in order), the
+ * first contributing CTA, their count and the first partial-sum slot, and the
+ * first unit of every CTA in cta_first_unit [n_ctas+1] (may be NULL). */
 int sl1m_plan_preview(int32_t n_probs, const int32_t* owned_blocks, const int32_t* streamed_granules,
-                      int32_t max_ctas, int32_t* n_ctas, int64_t* n_units, int32_t* n_slots,
-                      int32_t* blk_first_cta, int32_t* blk_n_ctas, int32_t* blk_first_slot);
+                      int32_t max_ctas, const float* unit_costs, int32_t* n_ctas, int64_t* n_units,
+                      int32_t* n_slots, int32_t* blk_first_cta, int32_t* blk_n_ctas, int32_t* blk_first_slot,
+                      int64_t* cta_first_unit);
 
 /* Host-only: the granule order the library uses for n points xy [n][2]:
  * order [n_pad] receives point indices, -1 for padding, so that each run of

@@ -42,6 +42,11 @@ constexpr int MAX_PROBS = 1024;       // problems per batched launch
 
 enum Kind : int { DIRAC = 0, PARAXIAL = 1, WIDE = 2 };
 
+// A tile (owned granule x streamed granule) whose offsets can make the FP32
+// product term D = (X - Xc).(Y - Yc) exceed D_MAX turns is evaluated with
+// the exact split instead (its FP32 rounding error grows like 2^-24 |D|).
+constexpr float D_MAX = 6.0f;
+
 // One side (visibilities or pixels) of a problem, sorted and padded.
 struct Side {
     int n;              // real elements
@@ -159,8 +164,22 @@ struct Plan {
     const int* blk_poff;          // [n_blocks] first partial slot of the block
     const int* blk_clo;           // [n_blocks] first CTA contributing to it
     const int* blk_ncon;          // [n_blocks] contributing CTAs
+    const long long* cta_u0;      // [C+1] first unit of each CTA (cost-weighted split),
+                                  // or null: CTA c takes [c U / C, (c+1) U / C)
     int n_blocks;
     int n_slots;
 };
+
+// Unit range [u, u_end) of CTA c.
+__host__ __device__ inline void cta_range(const Plan& pl, long long c, long long& u, long long& u_end)
+{
+    if (pl.cta_u0) {
+        u = pl.cta_u0[c];
+        u_end = pl.cta_u0[c + 1];
+    } else {
+        u = (pl.U * c) / pl.C;
+        u_end = (pl.U * (c + 1)) / pl.C;
+    }
+}
 
 }  // namespace sl1m

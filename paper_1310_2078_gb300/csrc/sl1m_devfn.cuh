@@ -7,11 +7,6 @@ namespace sl1m {
 #define TWO_PI_F 6.283185307179586f
 #define LOG2E_F 1.4426950408889634f
 
-// A tile (owned granule x streamed granule) whose offsets can make the FP32
-// product term D = (X - Xc).(Y - Yc) exceed D_MAX turns is evaluated with
-// the exact split instead (its FP32 rounding error grows like 2^-24 |D|).
-constexpr float D_MAX = 6.0f;
-
 // x - rint(x) for |x| < 2^22, exact: adding and removing 1.5 * 2^23 rounds x
 // to the nearest integer (ties to even) on the FP32 add pipe.
 __device__ __forceinline__ float frac_turns(float x)

@@ -44,8 +44,8 @@ fwd_fp64_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ p
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Plan pl = *plp;
     const long long c = blockIdx.x;
-    long long u = (pl.U * c) / pl.C;
-    const long long u_end = (pl.U * (c + 1)) / pl.C;
+    long long u, u_end;
+    cta_range(pl, c, u, u_end);
     while (u < u_end) {
         const int p = find_prob(pl, u);
         const DevProblem& P = probs[p];
@@ -131,8 +131,8 @@ adj_fp64_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ p
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Plan pl = *plp;
     const long long c = blockIdx.x;
-    long long u = (pl.U * c) / pl.C;
-    const long long u_end = (pl.U * (c + 1)) / pl.C;
+    long long u, u_end;
+    cta_range(pl, c, u, u_end);
     while (u < u_end) {
         const int p = find_prob(pl, u);
         const DevProblem& P = probs[p];
@@ -210,40 +210,40 @@ adj_fp64_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ p
 
 // ------------------------------------------------------------- launchers
 
-cudaError_t launch_forward_mixed(bool gains, int n_ant, const DevProblem* probs, const Plan* plp, int C,
+cudaError_t launch_forward_mixed(bool gains, int n_ant, int nst, const DevProblem* probs, const Plan* plp, int C,
                                  double2* partial, cudaStream_t st);
-cudaError_t launch_adjoint_mixed(bool gains, const DevProblem* probs, const Plan* plp, int C,
+cudaError_t launch_adjoint_mixed(bool gains, int n_ant, int nst, const DevProblem* probs, const Plan* plp, int C,
                                  double* partial, cudaStream_t st);
-int occupancy_mixed(int op, bool gains, int n_ant);
+int occupancy_mixed(int op, bool gains, int n_ant, int nst);
 
 cudaError_t launch_forward(int precision, bool gains, int n_ant, const DevProblem* probs,
-                           const Plan* plp, int C, double2* partial, cudaStream_t st)
+                           const Plan* plp, int C, double2* partial, cudaStream_t st, int nst)
 {
     if (precision == 0) {
         fwd_fp64_kernel<<<C, NTHREADS, 0, st>>>(probs, plp, partial);
         return cudaGetLastError();
     }
-    return launch_forward_mixed(gains, n_ant, probs, plp, C, partial, st);
+    return launch_forward_mixed(gains, n_ant, nst, probs, plp, C, partial, st);
 }
 
-cudaError_t launch_adjoint(int precision, bool gains, const DevProblem* probs, const Plan* plp, int C,
-                           double* partial, cudaStream_t st)
+cudaError_t launch_adjoint(int precision, bool gains, int n_ant, const DevProblem* probs, const Plan* plp, int C,
+                           double* partial, cudaStream_t st, int nst)
 {
     if (precision == 0) {
         adj_fp64_kernel<<<C, NTHREADS, 0, st>>>(probs, plp, partial);
         return cudaGetLastError();
     }
-    return launch_adjoint_mixed(gains, probs, plp, C, partial, st);
+    return launch_adjoint_mixed(gains, n_ant, nst, probs, plp, C, partial, st);
 }
 
-int occupancy(int which, bool gains, int n_ant)
+int occupancy(int which, bool gains, int n_ant, int nst)
 {
     int n = 0;
     switch (which) {
     case 0: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fwd_fp64_kernel, NTHREADS, 0); break;
     case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adj_fp64_kernel, NTHREADS, 0); break;
-    case 2: return occupancy_mixed(0, gains, n_ant);
-    case 3: return occupancy_mixed(1, gains, n_ant);
+    case 2: return occupancy_mixed(0, gains, n_ant, nst);
+    case 3: return occupancy_mixed(1, gains, n_ant, nst);
     }
     return n < 1 ? 1 : n;
 }

@@ -96,6 +96,38 @@ static void kd_append(std::vector<int>& order, std::vector<int> members, const d
     while (order.size() % G) order.push_back(-1);
 }
 
+// With gains, the forward kernel's lanes gather G[j][a_k] and G[j][b_k] from
+// a shared-memory row of 8-byte words: 16 lanes are served together, without
+// conflict when their antennas differ modulo 16.  Lane t owns slots t and
+// t+32 of a granule, so slots {0-15, 16-31, 32-47, 48-63} form the groups.
+// Reorder each granule (its members stay the same) greedily so that every
+// group holds distinct a mod 16 and b mod 16 as far as possible.
+static void spread_antennas(std::vector<int>& order, const std::vector<int>& ant)
+{
+    for (size_t g0 = 0; g0 + G <= order.size(); g0 += G) {
+        std::vector<int> pool(order.begin() + g0, order.begin() + g0 + G);
+        std::vector<int> out;
+        out.reserve(G);
+        for (int grp = 0; grp < 4; ++grp) {
+            int ca[16] = {0}, cb[16] = {0};
+            for (int s = 0; s < 16; ++s) {
+                size_t best = 0;
+                int best_cost = 1 << 30;
+                for (size_t i = 0; i < pool.size(); ++i) {
+                    const int o = pool[i];
+                    const int cost = o < 0 ? 1 : ca[ant[2 * o] & 15] + cb[ant[2 * o + 1] & 15];
+                    if (cost < best_cost) { best_cost = cost; best = i; if (cost == 0) break; }
+                }
+                const int o = pool[best];
+                pool.erase(pool.begin() + best);
+                if (o >= 0) { ca[ant[2 * o] & 15]++; cb[ant[2 * o + 1] & 15]++; }
+                out.push_back(o);
+            }
+        }
+        std::copy(out.begin(), out.end(), order.begin() + g0);
+    }
+}
+
 struct HostSide {
     int n = 0, n_pad = 0, n_gran = 0, n_blk = 0;
     std::vector<float4> hi, lo, off, offlo, cen_hi, cen_lo, ext;
@@ -180,7 +212,8 @@ static cudaError_t upload_side(const HostSide& H, DevSide& D, Side& S, cudaStrea
 // Stream-K schedule (host part): units = nb[p] * ns[p] per problem, CTA c
 // takes units [c U / C, (c+1) U / C); block gb is touched by CTAs
 // clo..clo+ncon-1 and owns partial slots poff..poff+ncon-1.
-void plan_host(const std::vector<int>& nb, const std::vector<int>& ns, int Cmax, HostPlan& H)
+void plan_host(const std::vector<int>& nb, const std::vector<int>& ns, int Cmax, HostPlan& H,
+               const std::vector<const UnitCost*>* costs)
 {
     const int np = (int)nb.size();
     H.u0.assign(np + 1, 0);
@@ -191,7 +224,58 @@ void plan_host(const std::vector<int>& nb, const std::vector<int>& ns, int Cmax,
     }
     const long long U = H.u0[np];
     const int C = (int)std::max(1LL, std::min((long long)std::max(1, Cmax), U));
-    auto cta_of = [&](long long x) { return (int)(((x + 1) * C + U - 1) / U - 1); };
+    H.cta_u0.clear();
+    if (costs && U > 0) {
+        // cumulative cost per problem; boundaries at multiples of total / C
+        std::vector<double> W(np + 1, 0.0);
+        for (int p = 0; p < np; ++p) {
+            const UnitCost* uc = (*costs)[p];
+            const long long up = H.u0[p + 1] - H.u0[p];
+            double w = 0.0;
+            if (uc && !uc->unit.empty() && (long long)uc->unit.size() == up) {
+                for (float f : uc->unit) w += f;
+            } else {
+                w = (uc ? uc->uniform : 1.0) * (double)up;
+            }
+            W[p + 1] = W[p] + w;
+        }
+        const double T = W[np];
+        H.cta_u0.assign(C + 1, 0);
+        H.cta_u0[C] = U;
+        int p = 0;
+        std::vector<double> pref;
+        int pref_of = -1;
+        for (int c = 1; c < C; ++c) {
+            const double t = T * (double)c / (double)C;
+            while (p < np - 1 && W[p + 1] < t) ++p;
+            const UnitCost* uc = (*costs)[p];
+            const long long up = H.u0[p + 1] - H.u0[p];
+            long long i;
+            if (uc && !uc->unit.empty() && (long long)uc->unit.size() == up) {
+                if (pref_of != p) {
+                    pref.assign(up + 1, 0.0);
+                    for (long long k = 0; k < up; ++k) pref[k + 1] = pref[k] + uc->unit[k];
+                    pref_of = p;
+                }
+                i = std::lower_bound(pref.begin(), pref.end(), t - W[p]) - pref.begin();
+            } else {
+                const double w = (uc ? uc->uniform : 1.0);
+                i = (long long)std::ceil((t - W[p]) / w - 1e-9);
+            }
+            i = std::max(0LL, std::min(up, i));
+            H.cta_u0[c] = H.u0[p] + i;
+        }
+        // every CTA gets at least one unit (C <= U): a block's partial slots
+        // are those of every CTA between its first and last, so none may be
+        // empty in between
+        for (int c = 1; c < C; ++c)
+            H.cta_u0[c] = std::min(std::max(H.cta_u0[c], H.cta_u0[c - 1] + 1), U - (C - c));
+    }
+    auto cta_of = [&](long long x) {
+        if (H.cta_u0.empty()) return (int)(((x + 1) * C + U - 1) / U - 1);
+        const int c = (int)(std::upper_bound(H.cta_u0.begin(), H.cta_u0.end(), x) - H.cta_u0.begin()) - 1;
+        return std::max(0, std::min(C - 1, c));
+    };
     const int nblocks = H.b0[np];
     H.poff.assign(nblocks, 0);
     H.clo.assign(nblocks, 0);
@@ -217,10 +301,10 @@ void plan_host(const std::vector<int>& nb, const std::vector<int>& ns, int Cmax,
 // Build a stream-K plan over problems with owned blocks nb[p] and streamed
 // granules ns[p]; C CTAs at most.  Uploads the tables.
 cudaError_t build_plan(const std::vector<int>& nb, const std::vector<int>& ns, int Cmax,
-                       DevPlan& D, cudaStream_t st)
+                       DevPlan& D, cudaStream_t st, const std::vector<const UnitCost*>* costs)
 {
     HostPlan H;
-    plan_host(nb, ns, Cmax, H);
+    plan_host(nb, ns, Cmax, H, costs);
     cudaError_t err;
     auto up = [&](DBuf<int>& b, const std::vector<int>& v) {
         return b.upload(v.data(), std::max<size_t>(1, v.size()), st, v.empty());
@@ -230,6 +314,11 @@ cudaError_t build_plan(const std::vector<int>& nb, const std::vector<int>& ns, i
     if ((err = up(D.poff, H.poff))) return err;
     if ((err = up(D.clo, H.clo))) return err;
     if ((err = up(D.ncon, H.ncon))) return err;
+    if (!H.cta_u0.empty()) {
+        if ((err = D.cta.upload(H.cta_u0.data(), H.cta_u0.size(), st))) return err;
+    } else {
+        D.cta.free();
+    }
     D.pl.n_probs = (int)nb.size();
     D.pl.C = H.C;
     D.pl.U = H.U;
@@ -238,6 +327,7 @@ cudaError_t build_plan(const std::vector<int>& nb, const std::vector<int>& ns, i
     D.pl.blk_poff = D.poff.p;
     D.pl.blk_clo = D.clo.p;
     D.pl.blk_ncon = D.ncon.p;
+    D.pl.cta_u0 = H.cta_u0.empty() ? nullptr : D.cta.p;
     D.pl.n_blocks = H.n_blocks;
     D.pl.n_slots = H.n_slots;
     return D.dpl.upload(&D.pl, 1, st);
@@ -346,12 +436,14 @@ int sl1m_problem::rebuild(cudaStream_t st)
         for (int64_t k = 0; k < n_vis; ++k) members[k] = (int)k;
         std::vector<int> order;
         kd_append(order, std::move(members), uvw.data(), uvw.data() + 1, 3);
+        if (n_ant > 0) spread_antennas(order, ant);
         std::vector<d4> xyz(n_vis);
         for (int64_t k = 0; k < n_vis; ++k)
             xyz[k] = make_d4(uvw[3 * k], uvw[3 * k + 1], uvw[3 * k + 2], weights.empty() ? 1.0 : weights[k]);
         HostSide H;
         layout_side(order, xyz, (int)n_vis, H);
         CK(upload_side(H, D.vis, hp.vis, st));
+        gext_vis = H.ext;
         std::vector<int2> a(H.n_pad, make_int2(0, 0));
         std::vector<double2> Vs(H.n_pad, make_double2(0.0, 0.0));
         for (int i = 0; i < H.n_pad; ++i) {
@@ -392,6 +484,7 @@ int sl1m_problem::rebuild(cudaStream_t st)
         HostSide H;
         layout_side(order, xyz, (int)n_pix, H);
         CK(upload_side(H, D.pix, hp.pix, st));
+        gext_pix = H.ext;
         std::vector<float4> pg(H.n_pad);
         std::vector<d4> pg64(H.n_pad);
         for (int t = 0; t < H.n_pad; ++t) {
@@ -415,6 +508,7 @@ int sl1m_problem::rebuild(cudaStream_t st)
         CK(D.gsig.upload(gs.data(), gs.size(), st));
         CK(D.gsig64.upload(gs64.data(), gs64.size(), st));
         CK(D.gkind.upload(gk.data(), gk.size(), st));
+        gkind_pix = gk;
         pix_orig = H.orig;
         if (n_ant > 0) {
             std::vector<float2> g32((size_t)H.n_pad * n_ant, make_float2(0.f, 0.f));
@@ -453,12 +547,59 @@ int sl1m_problem::rebuild(cudaStream_t st)
     ctx->h2d += (long long)dev_bytes();
     for (auto& b : op_batch) b.reset();
     for (auto& b : solve_batch) b.reset();
+    for (auto& r : ucost_ok) r[0] = r[1] = false;
     solver_ready = false;
     dirty = false;
     return SL1M_OK;
 }
 
 double sl1m_problem::pairs() const { return (double)n_vis * (double)n_pix; }
+
+// Relative cost of the units (owned block x streamed granule) of one operator:
+// a Gaussian pixel granule costs 1.6 (three SFU ops per pair and the extra
+// FMAs, against two), a tile taking the exact phase path 3x, and gains 1.4x.
+// A block's 8 warps meet at each shared-memory stage, so a unit costs what
+// its slowest warp costs.  Uniform problems return a constant.
+const UnitCost& sl1m_problem::unit_cost(int precision, int op)
+{
+    UnitCost& uc = ucost[precision][op];
+    if (ucost_ok[precision][op]) return uc;
+    ucost_ok[precision][op] = true;
+    uc.unit.clear();
+    const double gfac = n_ant > 0 ? 1.4 : 1.0;
+    const auto base = [](int kind) { return kind == DIRAC ? 1.0 : 1.6; };
+    int k0 = gkind_pix.empty() ? 0 : gkind_pix[0];
+    bool one_kind = true;
+    for (int k : gkind_pix) one_kind &= k == k0;
+    const std::vector<float4>& own = op == 0 ? gext_vis : gext_pix;
+    const std::vector<float4>& str = op == 0 ? gext_pix : gext_vis;
+    float4 mo = make_float4(0.f, 0.f, 0.f, 0.f), ms = mo;
+    for (const float4& e : own) { mo.x = std::max(mo.x, e.x); mo.y = std::max(mo.y, e.y); mo.z = std::max(mo.z, e.z); }
+    for (const float4& e : str) { ms.x = std::max(ms.x, e.x); ms.y = std::max(ms.y, e.y); ms.z = std::max(ms.z, e.z); }
+    const bool any_exact = precision == 1 && (mo.x * ms.x + mo.y * ms.y + mo.z * ms.z) > D_MAX;
+    uc.uniform = base(k0) * gfac;
+    if (one_kind && !any_exact) return uc;
+    const int ng_own = (int)own.size(), ng_str = (int)str.size();
+    const int nblk = (ng_own + BLK_GRAN - 1) / BLK_GRAN;
+    uc.unit.resize((size_t)nblk * ng_str);
+    for (int b = 0; b < nblk; ++b) {
+        const int w1 = std::min(ng_own, (b + 1) * BLK_GRAN);
+        double kb = 1.0;
+        if (op == 1)
+            for (int w = b * BLK_GRAN; w < w1; ++w) kb = std::max(kb, base(gkind_pix[w]));
+        for (int g = 0; g < ng_str; ++g) {
+            bool ex = false;
+            if (any_exact) {
+                const float4 s4 = str[g];
+                for (int w = b * BLK_GRAN; w < w1 && !ex; ++w)
+                    ex = own[w].x * s4.x + own[w].y * s4.y + own[w].z * s4.z > D_MAX;
+            }
+            const double kbase = op == 0 ? base(gkind_pix[g]) : kb;
+            uc.unit[(size_t)b * ng_str + g] = (float)(kbase * (ex ? 3.0 : 1.0) * gfac);
+        }
+    }
+    return uc;
+}
 
 // Device bytes a problem will hold once laid out with solver buffers
 // (admission estimate; padded sizes, ~100 B per element and side).
@@ -593,6 +734,14 @@ size_t sl1m_problem::dev_bytes() const
     return b;
 }
 
+long long tune_key(int precision, int op, bool gains, bool gauss, long long units)
+{
+    int lg = 0;
+    while (units > 1 && lg < 62) { units >>= 1; ++lg; }
+    return ((long long)precision << 12) | ((long long)op << 11) | ((long long)gains << 10) |
+           ((long long)gauss << 9) | lg;
+}
+
 // ================================================================ batches
 
 Batch::~Batch()
@@ -642,10 +791,31 @@ int batch_set(sl1m_ctx* ctx, Batch& B, const std::vector<sl1m_problem*>& probs,
                     if (g) B.n_ant_max = std::max(B.n_ant_max, probs[p]->n_ant);
                 }
             }
-            const int occf = occupancy(precision == 0 ? 0 : 2, c == 1, std::max(1, B.n_ant_max));
-            const int occa = occupancy(precision == 0 ? 1 : 3, c == 1, std::max(1, B.n_ant_max));
-            CK(build_plan(nbf, nsf, ctx->num_sms * occf, B.plan[0][c], st));
-            CK(build_plan(nba, nsa, ctx->num_sms * occa, B.plan[1][c], st));
+            // tile shape and grid: autotuned choice for this shape, else the default
+            bool gauss = false;
+            long long uf = 0, ua = 0;
+            for (int p = 0; p < np; ++p) {
+                gauss |= probs[p]->has_gauss && nbf[p] > 0;
+                uf += (long long)nbf[p] * nsf[p];
+                ua += (long long)nba[p] * nsa[p];
+            }
+            int kf = 0, ka = 0;
+            B.nst[0][c] = B.nst[1][c] = NST_DEFAULT;
+            const auto tf = ctx->tune.find(tune_key(precision, 0, c == 1, gauss, uf));
+            const auto ta = ctx->tune.find(tune_key(precision, 1, c == 1, gauss, ua));
+            if (tf != ctx->tune.end()) { B.nst[0][c] = tf->second.first; kf = tf->second.second; }
+            if (ta != ctx->tune.end()) { B.nst[1][c] = ta->second.first; ka = ta->second.second; }
+            const int occf = occupancy(precision == 0 ? 0 : 2, c == 1, std::max(1, B.n_ant_max), B.nst[0][c]);
+            const int occa = occupancy(precision == 0 ? 1 : 3, c == 1, std::max(1, B.n_ant_max), B.nst[1][c]);
+            kf = kf > 0 ? std::min(kf, occf) : occf;
+            ka = ka > 0 ? std::min(ka, occa) : occa;
+            std::vector<const UnitCost*> cf(np), ca(np);
+            for (int p = 0; p < np; ++p) {
+                cf[p] = &probs[p]->unit_cost(precision == 0 ? 0 : 1, 0);
+                ca[p] = &probs[p]->unit_cost(precision == 0 ? 0 : 1, 1);
+            }
+            CK(build_plan(nbf, nsf, ctx->num_sms * kf, B.plan[0][c], st, &cf));
+            CK(build_plan(nba, nsa, ctx->num_sms * ka, B.plan[1][c], st, &ca));
             CK(ctx->partial_f.reserve((size_t)std::max(1, B.plan[0][c].pl.n_slots) * BLK, st));
             CK(ctx->partial_a.reserve((size_t)std::max(1, B.plan[1][c].pl.n_slots) * BLK, st));
             B.fin_bytes[0] += (double)B.plan[0][c].pl.n_slots * BLK * 16.0;
@@ -674,7 +844,8 @@ static int launch_op_class(sl1m_ctx* ctx, Batch& B, int op, int c)
     ProfTok tk;
     if (op == 0) {
         prof_begin(ctx, B.precision == 0 ? 0 : 2, tk);
-        CKL(launch_forward(B.precision, c == 1, B.n_ant_max, B.desc.p, P.dpl.p, P.pl.C, ctx->partial_f.p, st));
+        CKL(launch_forward(B.precision, c == 1, B.n_ant_max, B.desc.p, P.dpl.p, P.pl.C, ctx->partial_f.p, st,
+                           B.nst[0][c]));
         prof_end(ctx, tk, B.pairs_class[c], 0.0);
         prof_begin(ctx, 4, tk);
         CKL(launch_fwd_finish(B.desc.p, P.dpl.p, std::min(B.fin_grid, std::max(1, P.pl.n_blocks)),
@@ -682,7 +853,8 @@ static int launch_op_class(sl1m_ctx* ctx, Batch& B, int op, int c)
         prof_end(ctx, tk, 0.0, B.fin_bytes[0]);
     } else {
         prof_begin(ctx, B.precision == 0 ? 1 : 3, tk);
-        CKL(launch_adjoint(B.precision, c == 1, B.desc.p, P.dpl.p, P.pl.C, ctx->partial_a.p, st));
+        CKL(launch_adjoint(B.precision, c == 1, B.n_ant_max, B.desc.p, P.dpl.p, P.pl.C, ctx->partial_a.p, st,
+                           B.nst[1][c]));
         prof_end(ctx, tk, B.pairs_class[c], 0.0);
         prof_begin(ctx, 5, tk);
         CKL(launch_adj_finish(B.desc.p, P.dpl.p, std::min(B.fin_grid, std::max(1, P.pl.n_blocks)),
@@ -1010,7 +1182,7 @@ int sl1m_set_gains(sl1m_problem* prob, int32_t n_ant, const double* Gn)
         prob->dirty = true;
         return SL1M_OK;
     }
-    if (n_ant < 0 || n_ant > 400) return sl1m_fail(ctx, SL1M_ERR_ARG, "n_ant must be in [1, 400]");
+    if (n_ant < 0 || n_ant > 320) return sl1m_fail(ctx, SL1M_ERR_ARG, "n_ant must be in [1, 320]");
     if (prob->n_pix <= 0) return sl1m_fail(ctx, SL1M_ERR_STATE, "set pixels before gains");
     const size_t cnt = (size_t)2 * prob->n_pix * n_ant;
     if (!all_finite(Gn, cnt)) return sl1m_fail(ctx, SL1M_ERR_ARG, "non-finite gains");
@@ -1105,6 +1277,31 @@ int sl1m_adjoint(sl1m_problem* prob, const double* r, double* img_out, int preci
     return SL1M_OK;
 }
 
+int sl1m_dirty_image(sl1m_problem* prob, int precision, double* img_out, double* lambda_max_out)
+{
+    if (!prob) return SL1M_ERR_ARG;
+    sl1m_ctx* ctx = prob->ctx;
+    NOT_WHILE_SERVING(ctx);
+    if (!img_out && !lambda_max_out) return sl1m_fail(ctx, SL1M_ERR_ARG, "null pointer");
+    RET(check_prec(ctx, precision));
+    CK(cudaSetDevice(ctx->device));
+    Batch* B;
+    RET(op_prepare(prob, precision, &B));
+    ProblemDev& D = *prob->dev;
+    cudaStream_t st = ctx->stream;
+    CKL(launch_weighted_vis(prob->hp.V, prob->hp.vis.d, D.r_sorted.p, prob->hp.vis.n_pad, st));
+    RET(batch_op(ctx, *B, 1));
+    CK(D.img_user.reserve(prob->n_pix, st));
+    CKL(launch_scatter_real(D.adj_sorted.p, D.img_user.p, prob->hp.pix.orig, prob->hp.pix.n_pad, st));
+    std::vector<double> img(prob->n_pix);
+    CK(cudaMemcpyAsync(img.data(), D.img_user.p, sizeof(double) * prob->n_pix, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    ctx->d2h += (long long)sizeof(double) * prob->n_pix;
+    if (img_out) std::copy(img.begin(), img.end(), img_out);
+    if (lambda_max_out) *lambda_max_out = *std::max_element(img.begin(), img.end());
+    return SL1M_OK;
+}
+
 int sl1m_max_eig(sl1m_problem* prob, int max_iter, double tol, int precision, double* L_out, int* iters_out)
 {
     if (!prob) return SL1M_ERR_ARG;
@@ -1169,6 +1366,74 @@ int sl1m_solve(sl1m_problem* prob, const sl1m_solve_opts* o, double* img_out, sl
     return SL1M_OK;
 }
 
+int sl1m_autotune(sl1m_problem* prob, int precision, int32_t* nst_out, int32_t* ctas_per_sm_out)
+{
+    if (!prob) return SL1M_ERR_ARG;
+    sl1m_ctx* ctx = prob->ctx;
+    NOT_WHILE_SERVING(ctx);
+    RET(check_prec(ctx, precision));
+    CK(cudaSetDevice(ctx->device));
+    Batch* Bop;
+    RET(op_prepare(prob, precision, &Bop));
+    ProblemDev& D = *prob->dev;
+    cudaStream_t st = ctx->stream;
+    CK(cudaMemsetAsync(D.x_sorted.p, 0, sizeof(double) * prob->hp.pix.n_pad, st));
+    CK(cudaMemsetAsync(D.r_sorted.p, 0, sizeof(double2) * prob->hp.vis.n_pad, st));
+    const bool gains = prob->n_ant > 0;
+    const DevProblem& d = Bop->hdesc[0];
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int rc = SL1M_OK;
+    for (int op = 0; op < 2 && rc == SL1M_OK; ++op) {
+        const std::vector<int> nb = {op == 0 ? d.vis.n_blk : d.pix.n_blk};
+        const std::vector<int> ns = {op == 0 ? d.pix.n_gran : d.vis.n_gran};
+        const std::vector<const UnitCost*> uc = {&prob->unit_cost(precision, op)};
+        const long long units = (long long)nb[0] * ns[0];
+        const std::vector<int> cands = (precision == SL1M_MIXED && !gains) ? std::vector<int>{2, 4, 8}
+                                                                           : std::vector<int>{NST_DEFAULT};
+        float best = 1e30f;
+        int bnst = NST_DEFAULT, bk = 0;
+        for (int nst : cands) {
+            const int occ = occupancy((precision == SL1M_FP64 ? 0 : 2) + op, gains, std::max(1, prob->n_ant), nst);
+            for (int k = 1; k <= occ && rc == SL1M_OK; ++k) {
+                DevPlan P;
+                if (build_plan(nb, ns, ctx->num_sms * k, P, st, &uc) != cudaSuccess) { rc = SL1M_ERR_CUDA; break; }
+                const size_t need = (size_t)std::max(1, P.pl.n_slots) * BLK;
+                if ((op == 0 ? ctx->partial_f.reserve(need, st) : ctx->partial_a.reserve(need, st)) != cudaSuccess) {
+                    rc = SL1M_ERR_OOM;
+                    break;
+                }
+                float ms = 0.f;
+                for (int rep = 0; rep < 4; ++rep) {
+                    if (rep == 1) cudaEventRecord(e0, st);
+                    cudaError_t e = op == 0 ? launch_forward(precision, gains, prob->n_ant, Bop->desc.p, P.dpl.p,
+                                                             P.pl.C, ctx->partial_f.p, st, nst)
+                                            : launch_adjoint(precision, gains, prob->n_ant, Bop->desc.p, P.dpl.p,
+                                                             P.pl.C, ctx->partial_a.p, st, nst);
+                    if (e != cudaSuccess) { rc = SL1M_ERR_CUDA; break; }
+                    ctx->n_launch += 1;
+                }
+                cudaEventRecord(e1, st);
+                if (cudaEventSynchronize(e1) != cudaSuccess) { rc = SL1M_ERR_CUDA; break; }
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) { best = ms; bnst = nst; bk = k; }
+            }
+        }
+        if (rc != SL1M_OK) break;
+        ctx->tune[tune_key(precision, op, gains, prob->has_gauss, units)] = {bnst, bk};
+        if (nst_out) nst_out[op] = bnst;
+        if (ctas_per_sm_out) ctas_per_sm_out[op] = bk;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // cached batches of this problem were built with the old choice
+    for (auto& b : prob->op_batch) b.reset();
+    for (auto& b : prob->solve_batch) b.reset();
+    if (rc != SL1M_OK) return sl1m_fail(ctx, rc, "autotune failed");
+    return SL1M_OK;
+}
+
 int sl1m_profile_enable(sl1m_ctx* ctx, int on)
 {
     if (!ctx) return SL1M_ERR_ARG;
@@ -1203,8 +1468,9 @@ int sl1m_profile_read(sl1m_ctx* ctx, int kid, double* ms, int64_t* launches, dou
 }
 
 int sl1m_plan_preview(int32_t n_probs, const int32_t* owned_blocks, const int32_t* streamed_granules,
-                      int32_t max_ctas, int32_t* n_ctas, int64_t* n_units, int32_t* n_slots,
-                      int32_t* blk_first_cta, int32_t* blk_n_ctas, int32_t* blk_first_slot)
+                      int32_t max_ctas, const float* unit_costs, int32_t* n_ctas, int64_t* n_units,
+                      int32_t* n_slots, int32_t* blk_first_cta, int32_t* blk_n_ctas, int32_t* blk_first_slot,
+                      int64_t* cta_first_unit)
 {
     if (n_probs <= 0 || !owned_blocks || !streamed_granules || max_ctas <= 0) return SL1M_ERR_ARG;
     std::vector<int> nb(n_probs), ns(n_probs);
@@ -1213,8 +1479,21 @@ int sl1m_plan_preview(int32_t n_probs, const int32_t* owned_blocks, const int32_
         nb[p] = owned_blocks[p];
         ns[p] = streamed_granules[p];
     }
+    std::vector<UnitCost> uc(n_probs);
+    std::vector<const UnitCost*> ucp(n_probs);
+    if (unit_costs) {
+        long long off = 0;
+        for (int p = 0; p < n_probs; ++p) {
+            const long long up = (long long)nb[p] * ns[p];
+            for (long long k = 0; k < up; ++k)
+                if (!(unit_costs[off + k] > 0.f) || !std::isfinite(unit_costs[off + k])) return SL1M_ERR_ARG;
+            uc[p].unit.assign(unit_costs + off, unit_costs + off + up);
+            ucp[p] = &uc[p];
+            off += up;
+        }
+    }
     HostPlan H;
-    plan_host(nb, ns, max_ctas, H);
+    plan_host(nb, ns, max_ctas, H, unit_costs ? &ucp : nullptr);
     if (n_ctas) *n_ctas = H.C;
     if (n_units) *n_units = H.U;
     if (n_slots) *n_slots = H.n_slots;
@@ -1223,6 +1502,9 @@ int sl1m_plan_preview(int32_t n_probs, const int32_t* owned_blocks, const int32_
         if (blk_n_ctas) blk_n_ctas[b] = H.ncon[b];
         if (blk_first_slot) blk_first_slot[b] = H.poff[b];
     }
+    if (cta_first_unit)
+        for (int c = 0; c <= H.C; ++c)
+            cta_first_unit[c] = H.cta_u0.empty() ? (H.U * c) / H.C : H.cta_u0[c];
     return SL1M_OK;
 }
 

@@ -61,20 +61,33 @@ struct DBuf {
 struct HostPlan {
     std::vector<long long> u0;
     std::vector<int> b0, poff, clo, ncon;
+    std::vector<long long> cta_u0;   // empty: uniform split
     long long U = 0;
     int C = 1, n_blocks = 0, n_slots = 0;
 };
-void plan_host(const std::vector<int>& nb, const std::vector<int>& ns, int Cmax, HostPlan& H);
+
+// Relative cost of the units of one problem in a plan: a constant per unit,
+// or one value per unit (block-major, streamed granule minor).
+struct UnitCost {
+    double uniform = 1.0;
+    std::vector<float> unit;
+};
+
+// costs == null: every unit costs the same; otherwise the CTA boundaries cut
+// the summed cost into C equal parts.
+void plan_host(const std::vector<int>& nb, const std::vector<int>& ns, int Cmax, HostPlan& H,
+               const std::vector<const UnitCost*>* costs = nullptr);
 
 // A plan whose tables and header live on the device (kernels take Plan*).
 struct DevPlan {
     sl1m::Plan pl{};          // host copy of the header
     DBuf<long long> u0;
     DBuf<int> b0, poff, clo, ncon;
+    DBuf<long long> cta;
     DBuf<sl1m::Plan> dpl;     // device header
 };
 cudaError_t build_plan(const std::vector<int>& nb, const std::vector<int>& ns, int Cmax, DevPlan& D,
-                       cudaStream_t st);
+                       cudaStream_t st, const std::vector<const UnitCost*>* costs = nullptr);
 
 constexpr int NPROF = 7;
 
@@ -104,6 +117,7 @@ struct Batch {
     DBuf<int> phases_dev;
     DevPlan plan[2][2];        // [0 forward / 1 adjoint][0 no gains / 1 gains]
     bool has_class[2] = {false, false};
+    int nst[2][2] = {{4, 4}, {4, 4}};   // tile shape per [op][class] (autotuned or default)
     int n_ant_max = 0;
     int fin_grid = 1, sc_grid = 1;
     double pairs_class[2] = {0, 0};
@@ -125,6 +139,9 @@ struct sl1m_ctx {
     DBuf<double2> partial_f;
     DBuf<double> partial_a;
     std::vector<sl1m_problem*> problems;
+    // autotuned (streamed granules per stage, CTAs per SM), keyed by
+    // (precision, op, gains, Gaussian pixels, log2 of the units)
+    std::map<long long, std::pair<int, int>> tune;
     Server* server = nullptr;            // running request loop
     Server* server_done = nullptr;       // stopped loop whose results are still collectable
     bool use_graphs = true;
@@ -162,7 +179,13 @@ struct sl1m_problem {
     sl1m::DevProblem hp{};          // layout part of the descriptor
     sl1m::SolveBufs hbufs{};
     std::vector<int> vis_orig, pix_orig;
+    std::vector<double> last_img;             // image of the last refinement (caller's order)
+    std::vector<float4> gext_vis, gext_pix;   // granule extents (host copies)
+    std::vector<int> gkind_pix;               // pixel granule kinds
+    UnitCost ucost[2][2];                      // [precision][0 forward / 1 adjoint]
+    bool ucost_ok[2][2] = {{false, false}, {false, false}};
     std::unique_ptr<Batch> op_batch[2], solve_batch[2];
+    const UnitCost& unit_cost(int precision, int op);
 
     int rebuild(cudaStream_t st);
     int ensure_solver(cudaStream_t st);
@@ -175,6 +198,8 @@ struct sl1m_problem {
     size_t estimate_bytes() const;
     ~sl1m_problem();
 };
+
+long long tune_key(int precision, int op, bool gains, bool gauss, long long units);
 
 // batches (sl1m_host.cpp)
 int batch_set(sl1m_ctx* ctx, Batch& B, const std::vector<sl1m_problem*>& probs,

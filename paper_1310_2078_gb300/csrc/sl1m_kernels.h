@@ -8,12 +8,15 @@ enum FinishMode : int { FIN_OP = 0, FIN_POWER = 1, FIN_SOLVE = 2, FIN_INIT = 3 }
 
 // operator kernels (sl1m_mixed.cu, sl1m_fp64.cu); precision 0 = FP64, 1 = mixed.
 // plp: device-resident plan; C: its grid size (known on the host).
+// nst: streamed granules per shared-memory stage of the mixed no-gains
+// kernels (2, 4 or 8; the tile shape the autotuner picks).
+constexpr int NST_DEFAULT = 4;
 cudaError_t launch_forward(int precision, bool gains, int n_ant, const DevProblem* probs,
-                           const Plan* plp, int C, double2* partial, cudaStream_t st);
-cudaError_t launch_adjoint(int precision, bool gains, const DevProblem* probs, const Plan* plp, int C,
-                           double* partial, cudaStream_t st);
+                           const Plan* plp, int C, double2* partial, cudaStream_t st, int nst = NST_DEFAULT);
+cudaError_t launch_adjoint(int precision, bool gains, int n_ant, const DevProblem* probs, const Plan* plp, int C,
+                           double* partial, cudaStream_t st, int nst = NST_DEFAULT);
 // which: 0 fwd fp64, 1 adj fp64, 2 fwd mixed, 3 adj mixed
-int occupancy(int which, bool gains, int n_ant);
+int occupancy(int which, bool gains, int n_ant, int nst = NST_DEFAULT);
 int fwd_smem_bytes(int n_ant, bool gains);
 
 // solver kernels (sl1m_solver.cu)
@@ -26,6 +29,7 @@ cudaError_t launch_scatter_real(const double* src, double* dst, const int* orig,
 cudaError_t launch_scatter_cplx(const double2* src, double2* dst, const int* orig, int n_pad,
                                 cudaStream_t st);
 cudaError_t launch_fill_valid(double* dst, const int* orig, int n_pad, double val, cudaStream_t st);
+cudaError_t launch_weighted_vis(const double2* V, const d4* vd, double2* r, int n_pad, cudaStream_t st);
 cudaError_t launch_fwd_finish(const DevProblem* probs, const Plan* plp, int grid, const double2* partial,
                               cudaStream_t st);
 cudaError_t launch_adj_finish(const DevProblem* probs, const Plan* plp, int grid, const double* partial,

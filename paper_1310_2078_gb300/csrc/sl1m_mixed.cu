@@ -115,17 +115,14 @@ __device__ __forceinline__ void fwd_gauss_tile(const float4* __restrict__ s_off,
     }
 }
 
-// Streamed granules staged per barrier pair (the gains tables of one granule
-// already fill most of shared memory, so the gains kernels stage one).
-template <bool GAINS> struct Stage { static constexpr int N = GAINS ? 1 : 4; };
-
 // Owned: visibilities (warp = one vis granule, lane = 2 visibilities).
-// Streamed: pixel granules through shared memory, NST per stage.
-template <bool GAINS>
+// Streamed: pixel granules through shared memory, NST per barrier pair (a
+// tile shape the autotuner picks; the gains kernel stages one, since one
+// granule's gains for all antennas already fill most of shared memory).
+template <bool GAINS, int NST>
 __global__ void __launch_bounds__(NTHREADS, 3)
 fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ plp, double2* __restrict__ partial)
 {
-    constexpr int NST = Stage<GAINS>::N;
     __shared__ float4 s_off[NST][G];       // {dl, dm, dn, a = x/n}
     __shared__ float4 s_lo[NST][G];        // offset residuals
     __shared__ float4 s_pg[NST][G];        // {l, m, r^2/2, nu}
@@ -138,8 +135,8 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Plan pl = *plp;
     const long long c = blockIdx.x;
-    long long u = (pl.U * c) / pl.C;
-    const long long u_end = (pl.U * (c + 1)) / pl.C;
+    long long u, u_end;
+    cta_range(pl, c, u, u_end);
 
     while (u < u_end) {
         const int p = find_prob(pl, u);
@@ -276,14 +273,24 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
 
 // ----------------------------------------------------------- adjoint tiles
 
-template <bool GAINS, bool EXACT>
+// Gain of owned pixel r (0/1 of this lane) at antenna a.
+struct NoGain {
+    __device__ float2 operator()(int, int) const { return make_float2(1.f, 0.f); }
+};
+// gains in shared memory, [antenna][pixel of the owned granule]
+struct SmemGain {
+    const float2* tab;
+    int lane;
+    __device__ float2 operator()(int a, int r) const { return tab[a * G + lane + 32 * r]; }
+};
+
+template <bool GAINS, bool EXACT, class GF>
 __device__ __forceinline__ void adj_dirac_tile(const float4* __restrict__ s_off,
                                                const float4* __restrict__ s_lo,
                                                const float2* __restrict__ s_r,
                                                const int2* __restrict__ s_ant,
-                                               const float* __restrict__ sB,
-                                               const float2* __restrict__ gains, int n_ant,
-                                               const int (&eidx)[2], const float (&C)[2],
+                                               const float* __restrict__ sB, const GF& gain,
+                                               const float (&C)[2],
                                                const float4 (&dx)[2], const float4 (&dxl)[2],
                                                float (&acc)[2])
 {
@@ -303,8 +310,8 @@ __device__ __forceinline__ void adj_dirac_tile(const float4* __restrict__ s_off,
             __sincosf(ph * TWO_PI_F, &sn, &cs);           // exp(+2 pi i ph) = cs + i sn
             if (GAINS) {
                 const int2 ab = s_ant[k];
-                const float2 ga = gains[(size_t)eidx[r] * n_ant + ab.x];
-                const float2 gb = gains[(size_t)eidx[r] * n_ant + ab.y];
+                const float2 ga = gain(ab.x, r);
+                const float2 gb = gain(ab.y, r);
                 const float gr = fmaf(ga.x, gb.x, ga.y * gb.y);
                 const float gi = fmaf(ga.y, gb.x, -ga.x * gb.y);
                 const float zr = fmaf(cs, rr.x, -sn * rr.y);
@@ -317,15 +324,14 @@ __device__ __forceinline__ void adj_dirac_tile(const float4* __restrict__ s_off,
     }
 }
 
-template <bool GAINS, bool EXACT>
+template <bool GAINS, bool EXACT, class GF>
 __device__ __forceinline__ void adj_gauss_tile(const float4* __restrict__ s_off,
                                                const float4* __restrict__ s_lo,
                                                const float4* __restrict__ s_abs,
                                                const int2* __restrict__ s_ant,
                                                const float* __restrict__ sB,
-                                               const float4* __restrict__ s_gw,
-                                               const float2* __restrict__ gains, int n_ant, bool par,
-                                               const int (&eidx)[2], const float (&C)[2],
+                                               const float4* __restrict__ s_gw, const GF& gain, bool par,
+                                               const float (&C)[2],
                                                const float4 (&dx)[2], const float4 (&dxl)[2],
                                                const float4 (&pgd)[2], float (&acc)[2])
 {
@@ -352,8 +358,8 @@ __device__ __forceinline__ void adj_gauss_tile(const float4* __restrict__ s_off,
             const float zr = fmaf(cs, gw.z, -sn * gw.w);
             if (GAINS) {
                 const int2 ab = s_ant[k];
-                const float2 ga = gains[(size_t)eidx[r] * n_ant + ab.x];
-                const float2 gb = gains[(size_t)eidx[r] * n_ant + ab.y];
+                const float2 ga = gain(ab.x, r);
+                const float2 gb = gain(ab.y, r);
                 const float gr = fmaf(ga.x, gb.x, ga.y * gb.y);
                 const float gi = fmaf(ga.y, gb.x, -ga.x * gb.y);
                 const float zi = fmaf(cs, gw.w, sn * gw.z);
@@ -367,9 +373,7 @@ __device__ __forceinline__ void adj_gauss_tile(const float4* __restrict__ s_off,
 
 // Owned: pixels (warp = one pixel granule, lane = 2 pixels).
 // Streamed: visibility granules through shared memory, NSA per stage.
-constexpr int NSA = 4;
-
-template <bool GAINS>
+template <int NSA>
 __global__ void __launch_bounds__(NTHREADS, 3)
 adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ plp, double* __restrict__ partial)
 {
@@ -377,7 +381,7 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
     __shared__ float4 s_lo[NSA][G];
     __shared__ float4 s_abs[NSA][G];            // {u, v, w, 0} (Gaussian owners)
     __shared__ float2 s_r[NSA][G];
-    __shared__ int2 s_ant[NSA][G];
+    __shared__ int2 s_ant[NSA][G];      // unused without gains
     __shared__ float s_B[BLK_GRAN][NSA][G];
     __shared__ float4 s_gw[BLK_GRAN][NSA][G];   // Gaussian owners: {gam, coef, r're, r'im}
     __shared__ float4 s_cen[NSA][3];
@@ -385,8 +389,8 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Plan pl = *plp;
     const long long c = blockIdx.x;
-    long long u = (pl.U * c) / pl.C;
-    const long long u_end = (pl.U * (c + 1)) / pl.C;
+    long long u, u_end;
+    cta_range(pl, c, u, u_end);
 
     while (u < u_end) {
         const int p = find_prob(pl, u);
@@ -403,7 +407,6 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
         const int g1 = (int)min((long long)upb, (long long)g0 + (u_end - u));
         const int pgi = blk * BLK_GRAN + warp;
         const bool pg_ok = pgi < P.pix.n_gran;
-        const int n_ant = P.n_ant;
         const int e0 = (pg_ok ? pgi : 0) * G + lane;     // this lane's pixels: e0, e0 + 32
 
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -440,7 +443,6 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                 s_abs[q][i] = P.vis.hi[e];
                 const double2 rr = R[e];
                 s_r[q][i] = make_float2((float)rr.x, (float)rr.y);
-                if (GAINS) s_ant[q][i] = P.ant[e];
             }
             if (threadIdx.x < ns) {
                 const int g = gs + threadIdx.x;
@@ -474,23 +476,24 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
 #pragma unroll
                 for (int r = 0; r < 2; ++r) C[r] = frac_dot3(xh[r], P.pix.lo[eidx[r]], yc_h, yc_l);
                 float acc[2] = {0.f, 0.f};
+                const NoGain ng;
                 if (!gauss) {
                     if (exact) {
                         const float4 dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
-                        adj_dirac_tile<GAINS, true>(s_off[q], s_lo[q], s_r[q], s_ant[q], s_B[warp][q], P.gains32,
-                                                    n_ant, eidx, C, dx, dxl, acc);
+                        adj_dirac_tile<false, true>(s_off[q], s_lo[q], s_r[q], s_ant[q], s_B[warp][q], ng, C, dx,
+                                                    dxl, acc);
                     } else {
-                        adj_dirac_tile<GAINS, false>(s_off[q], s_lo[q], s_r[q], s_ant[q], s_B[warp][q], P.gains32,
-                                                     n_ant, eidx, C, dx, dx, acc);
+                        adj_dirac_tile<false, false>(s_off[q], s_lo[q], s_r[q], s_ant[q], s_B[warp][q], ng, C, dx,
+                                                     dx, acc);
                     }
                 } else {
                     if (exact) {
                         const float4 dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
-                        adj_gauss_tile<GAINS, true>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[warp][q],
-                                                    s_gw[warp][q], P.gains32, n_ant, par, eidx, C, dx, dxl, pgd, acc);
+                        adj_gauss_tile<false, true>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[warp][q],
+                                                    s_gw[warp][q], ng, par, C, dx, dxl, pgd, acc);
                     } else {
-                        adj_gauss_tile<GAINS, false>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[warp][q],
-                                                     s_gw[warp][q], P.gains32, n_ant, par, eidx, C, dx, dx, pgd, acc);
+                        adj_gauss_tile<false, false>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[warp][q],
+                                                     s_gw[warp][q], ng, par, C, dx, dx, pgd, acc);
                     }
                 }
 #pragma unroll
@@ -507,52 +510,217 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
     }
 }
 
+// Adjoint with gains.  The CTA's 8 warps share one owned pixel granule at a
+// time -- its gains for all antennas in shared memory as [antenna][pixel], so
+// a lane's loads never conflict -- and split the streamed visibility granules
+// of the run among themselves (warp w takes the w-th of every 8).  For each
+// owned granule the 8 warp sums are added in warp order (deterministic).
+__global__ void __launch_bounds__(NTHREADS, 2)
+adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ plp,
+                       double* __restrict__ partial)
+{
+    __shared__ float4 s_off[BLK_GRAN][G];
+    __shared__ float4 s_lo[BLK_GRAN][G];
+    __shared__ float4 s_abs[BLK_GRAN][G];
+    __shared__ float2 s_r[BLK_GRAN][G];
+    __shared__ int2 s_ant[BLK_GRAN][G];
+    __shared__ float s_B[BLK_GRAN][G];
+    __shared__ float4 s_gw[BLK_GRAN][G];
+    __shared__ float4 s_cen[BLK_GRAN][3];
+    __shared__ double s_red[BLK_GRAN][G];
+    extern __shared__ float2 s_gain[];      // [n_ant][G]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Plan pl = *plp;
+    const long long c = blockIdx.x;
+    long long u, u_end;
+    cta_range(pl, c, u, u_end);
+
+    while (u < u_end) {
+        const int p = find_prob(pl, u);
+        const DevProblem& P = probs[p];
+        const long long loc = u - pl.prob_u0[p];
+        const double2* R;
+        if (!adj_role(P, R)) {
+            u = min(u_end, pl.prob_u0[p + 1]);
+            continue;
+        }
+        const int upb = P.vis.n_gran;
+        const int blk = (int)(loc / upb);
+        const int g0 = (int)(loc % upb);
+        const int g1 = (int)min((long long)upb, (long long)g0 + (u_end - u));
+        const int n_ant = P.n_ant;
+        const int gb = pl.prob_b0[p] + blk;
+        double* dst = partial + (size_t)slot_of(pl, gb) * BLK;
+        for (int og = 0; og < BLK_GRAN; ++og) {
+            const int pgi = blk * BLK_GRAN + og;
+            if (pgi >= P.pix.n_gran) break;                  // uniform over the CTA
+            __syncthreads();                                 // s_gain / s_red free again
+            for (int i = threadIdx.x; i < G * n_ant; i += NTHREADS) {
+                const int j = i / n_ant, a = i - j * n_ant;  // coalesced read of [pixel][antenna]
+                s_gain[a * G + j] = P.gains32[(size_t)(pgi * G + j) * n_ant + a];
+            }
+            const float4 ch = P.pix.cen_hi[pgi], cl = P.pix.cen_lo[pgi], ext = P.pix.ext[pgi];
+            const int kind = P.gkind[pgi];
+            const float sigma = P.gsig[pgi];
+            const bool gauss = (kind != DIRAC), par = (kind == PARAXIAL);
+            const int e0 = pgi * G + lane;
+            const int eidx[2] = {e0, e0 + 32};
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 xh[2], dx[2], pgd[2] = {z4, z4};
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                xh[r] = P.pix.hi[eidx[r]];
+                dx[r] = P.pix.off[eidx[r]];
+                if (gauss) pgd[r] = P.pgauss[eidx[r]];
+            }
+            const SmemGain sg{s_gain, lane};
+            double tot[2] = {0.0, 0.0};
+            for (int gs = g0; gs < g1; gs += BLK_GRAN) {
+                const int ns = min(BLK_GRAN, g1 - gs);
+                __syncthreads();
+                for (int t = threadIdx.x; t < ns * G; t += NTHREADS) {
+                    const int q = t / G, i = t % G;
+                    const int e = (gs + q) * G + i;
+                    s_off[q][i] = P.vis.off[e];
+                    s_lo[q][i] = P.vis.offlo[e];
+                    s_abs[q][i] = P.vis.hi[e];
+                    const double2 rr = R[e];
+                    s_r[q][i] = make_float2((float)rr.x, (float)rr.y);
+                    s_ant[q][i] = P.ant[e];
+                }
+                if (threadIdx.x < ns) {
+                    const int g = gs + threadIdx.x;
+                    s_cen[threadIdx.x][0] = P.vis.cen_hi[g];
+                    s_cen[threadIdx.x][1] = P.vis.cen_lo[g];
+                    s_cen[threadIdx.x][2] = P.vis.ext[g];
+                }
+                __syncthreads();
+                if (warp >= ns) continue;                    // this warp has no granule in this stage
+                const int q = warp;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = lane + 32 * h;
+                    float b = frac_dot3(ch, cl, s_off[q][k], s_lo[q][k]);
+                    if (gauss) {
+                        const float4 va = s_abs[q][k];
+                        const GaussConst gc = gauss_const(va.x, va.y, va.z, sigma);
+                        b = frac_turns(b + gc.cphase);
+                        const float2 rr = s_r[q][k];
+                        s_gw[q][k] = make_float4(gc.gam, gc.coef, gc.id * fmaf(gc.beta, rr.y, rr.x),
+                                                 gc.id * fmaf(-gc.beta, rr.x, rr.y));
+                    }
+                    s_B[q][k] = b;
+                }
+                __syncwarp();
+                const bool exact = dot3(ext, s_cen[q][2]) > D_MAX;
+                float C[2];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) C[r] = frac_dot3(xh[r], P.pix.lo[eidx[r]], s_cen[q][0], s_cen[q][1]);
+                float acc[2] = {0.f, 0.f};
+                if (!gauss) {
+                    if (exact) {
+                        const float4 dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
+                        adj_dirac_tile<true, true>(s_off[q], s_lo[q], s_r[q], s_ant[q], s_B[q], sg, C, dx, dxl, acc);
+                    } else {
+                        adj_dirac_tile<true, false>(s_off[q], s_lo[q], s_r[q], s_ant[q], s_B[q], sg, C, dx, dx, acc);
+                    }
+                } else {
+                    if (exact) {
+                        const float4 dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
+                        adj_gauss_tile<true, true>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[q], s_gw[q], sg, par, C,
+                                                   dx, dxl, pgd, acc);
+                    } else {
+                        adj_gauss_tile<true, false>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[q], s_gw[q], sg, par,
+                                                    C, dx, dx, pgd, acc);
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < 2; ++r) tot[r] += (double)acc[r];
+            }
+#pragma unroll
+            for (int r = 0; r < 2; ++r) s_red[warp][lane + 32 * r] = tot[r];
+            __syncthreads();
+            if (warp == 0) {
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    double t = 0.0;
+                    for (int w = 0; w < BLK_GRAN; ++w) t += s_red[w][lane + 32 * r];
+                    dst[og * G + lane + 32 * r] = t * P.pix.d[eidx[r]].w;
+                }
+            }
+        }
+        u += g1 - g0;
+    }
+}
+
 // ------------------------------------------------------------- launchers
 
 int fwd_smem_bytes(int n_ant, bool gains) { return gains ? G * n_ant * (int)sizeof(float2) : 0; }
+int adj_gains_smem_bytes(int n_ant) { return G * n_ant * (int)sizeof(float2); }
 
-cudaError_t launch_forward_mixed(bool gains, int n_ant, const DevProblem* probs, const Plan* plp, int C,
+template <class K>
+static int occ_of(K kernel, int dyn)
+{
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, NTHREADS, dyn);
+    return n < 1 ? 1 : n;
+}
+
+cudaError_t launch_forward_mixed(bool gains, int n_ant, int nst, const DevProblem* probs, const Plan* plp, int C,
                                  double2* partial, cudaStream_t st)
 {
     if (gains) {
         // the dynamic shared-memory limit was raised by occupancy_mixed()
         // when the batch was built (not here: this may run under capture)
-        const int sm = fwd_smem_bytes(n_ant, true);
-        fwd_mixed_kernel<true><<<C, NTHREADS, sm, st>>>(probs, plp, partial);
+        fwd_mixed_kernel<true, 1><<<C, NTHREADS, fwd_smem_bytes(n_ant, true), st>>>(probs, plp, partial);
+    } else if (nst <= 2) {
+        fwd_mixed_kernel<false, 2><<<C, NTHREADS, 0, st>>>(probs, plp, partial);
+    } else if (nst <= 4) {
+        fwd_mixed_kernel<false, 4><<<C, NTHREADS, 0, st>>>(probs, plp, partial);
     } else {
-        fwd_mixed_kernel<false><<<C, NTHREADS, 0, st>>>(probs, plp, partial);
+        fwd_mixed_kernel<false, 8><<<C, NTHREADS, 0, st>>>(probs, plp, partial);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_mixed(bool gains, const DevProblem* probs, const Plan* plp, int C,
+cudaError_t launch_adjoint_mixed(bool gains, int n_ant, int nst, const DevProblem* probs, const Plan* plp, int C,
                                  double* partial, cudaStream_t st)
 {
-    if (gains) adj_mixed_kernel<true><<<C, NTHREADS, 0, st>>>(probs, plp, partial);
-    else adj_mixed_kernel<false><<<C, NTHREADS, 0, st>>>(probs, plp, partial);
+    if (gains) adj_mixed_gains_kernel<<<C, NTHREADS, adj_gains_smem_bytes(n_ant), st>>>(probs, plp, partial);
+    else if (nst <= 2) adj_mixed_kernel<2><<<C, NTHREADS, 0, st>>>(probs, plp, partial);
+    else if (nst <= 4) adj_mixed_kernel<4><<<C, NTHREADS, 0, st>>>(probs, plp, partial);
+    else adj_mixed_kernel<8><<<C, NTHREADS, 0, st>>>(probs, plp, partial);
     return cudaGetLastError();
 }
 
-int occupancy_mixed(int op, bool gains, int n_ant)
+int occupancy_mixed(int op, bool gains, int n_ant, int nst)
 {
-    static int smem_limit = 0;   // only ever raised, so every earlier batch stays launchable
-    int n = 0;
+    static int fwd_smem_limit = 0, adj_smem_limit = 0;   // only ever raised
     if (op == 0) {
         if (gains) {
             const int sm = fwd_smem_bytes(n_ant, true);
-            if (sm > smem_limit) {
-                cudaFuncSetAttribute(fwd_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-                smem_limit = sm;
+            if (sm > fwd_smem_limit) {
+                cudaFuncSetAttribute(fwd_mixed_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                fwd_smem_limit = sm;
             }
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fwd_mixed_kernel<true>, NTHREADS, sm);
-        } else {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fwd_mixed_kernel<false>, NTHREADS, 0);
+            return occ_of(fwd_mixed_kernel<true, 1>, sm);
         }
-    } else {
-        if (gains) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adj_mixed_kernel<true>, NTHREADS, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adj_mixed_kernel<false>, NTHREADS, 0);
+        if (nst <= 2) return occ_of(fwd_mixed_kernel<false, 2>, 0);
+        if (nst <= 4) return occ_of(fwd_mixed_kernel<false, 4>, 0);
+        return occ_of(fwd_mixed_kernel<false, 8>, 0);
     }
-    return n < 1 ? 1 : n;
+    if (gains) {
+        const int sm = adj_gains_smem_bytes(n_ant);
+        if (sm > adj_smem_limit) {
+            cudaFuncSetAttribute(adj_mixed_gains_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            adj_smem_limit = sm;
+        }
+        return occ_of(adj_mixed_gains_kernel, sm);
+    }
+    if (nst <= 2) return occ_of(adj_mixed_kernel<2>, 0);
+    if (nst <= 4) return occ_of(adj_mixed_kernel<4>, 0);
+    return occ_of(adj_mixed_kernel<8>, 0);
 }
 
 }  // namespace sl1m

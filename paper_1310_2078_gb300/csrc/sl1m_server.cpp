@@ -55,7 +55,8 @@ struct Server {
     std::map<uint64_t, std::unique_ptr<Request>> reqs;
     uint64_t next_ticket = 1;
     size_t budget = 0, in_use = 0;
-    int max_slots = 64, ticks_per_round = 8, precision = SL1M_MIXED;
+    int max_slots = 64, ticks_per_round = 4, precision = SL1M_MIXED;
+    double max_pairs = 4e9;
     bool stop = false, running = false;
     long long finished = 0, max_active = 0, ticks = 0, rounds = 0;
     std::string err;
@@ -106,11 +107,17 @@ static void server_loop(Server* Sp)
             std::unique_lock<std::mutex> lk(S.mu);
             while (!S.stop && S.pending.empty() && S.active.empty()) S.cv_work.wait(lk);
             if (S.stop && S.pending.empty() && S.active.empty()) break;
+            double work = 0.0;
+            for (Request* r : S.active) work += r->prob->pairs();
             while (!S.pending.empty() && (int)(S.active.size() + admit.size()) < S.max_slots) {
                 Request* r = S.pending.front();
                 const size_t need = r->prob->estimate_bytes();
+                const bool first = S.active.empty() && admit.empty();
                 // admission by memory: wait for running solves to free theirs
-                if (S.in_use + need > S.budget && !(S.active.empty() && admit.empty())) break;
+                if (S.in_use + need > S.budget && !first) break;
+                // admission by work in flight: enough to fill the GPU, no more
+                if (work + r->prob->pairs() > S.max_pairs && !first) break;
+                work += r->prob->pairs();
                 S.pending.pop_front();
                 r->bytes = need;
                 S.in_use += need;
@@ -214,7 +221,8 @@ int sl1m_server_start(sl1m_ctx* ctx, const sl1m_server_opts* opts)
     S->budget = (opts && opts->mem_budget_bytes > 0) ? (size_t)opts->mem_budget_bytes : (size_t)(0.8 * free_b);
     S->max_slots = (opts && opts->max_slots > 0) ? opts->max_slots : 64;
     S->max_slots = std::min(S->max_slots, MAX_PROBS);
-    S->ticks_per_round = (opts && opts->ticks_per_round > 0) ? opts->ticks_per_round : 8;
+    S->ticks_per_round = (opts && opts->ticks_per_round > 0) ? opts->ticks_per_round : 4;
+    S->max_pairs = (opts && opts->max_pairs_per_tick > 0) ? opts->max_pairs_per_tick : 4e9;
     S->precision = opts ? opts->precision : SL1M_MIXED;
     if (S->precision != SL1M_MIXED && S->precision != SL1M_FP64) {
         delete S;

@@ -56,6 +56,16 @@ __global__ void fill_valid_kernel(double* __restrict__ dst, const int* __restric
         dst[i] = orig[i] >= 0 ? val : 0.0;
 }
 
+// r = W V in the library's visibility order (input of the dirty image).
+__global__ void weighted_vis_kernel(const double2* __restrict__ V, const d4* __restrict__ vd,
+                                    double2* __restrict__ r, int n_pad)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += gridDim.x * blockDim.x) {
+        const double w = vd[i].w;
+        r[i] = make_double2(w * V[i].x, w * V[i].y);
+    }
+}
+
 static int grid_for(int n) { return n <= 0 ? 1 : (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096; }
 
 cudaError_t launch_gather_real(const double* src, double* dst, const int* orig, int n_pad,
@@ -82,6 +92,12 @@ cudaError_t launch_scatter_cplx(const double2* src, double2* dst, const int* ori
     scatter_cplx_kernel<<<grid_for(n_pad), 256, 0, st>>>(src, dst, orig, n_pad);
     return cudaGetLastError();
 }
+cudaError_t launch_weighted_vis(const double2* V, const d4* vd, double2* r, int n_pad, cudaStream_t st)
+{
+    weighted_vis_kernel<<<grid_for(n_pad), 256, 0, st>>>(V, vd, r, n_pad);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fill_valid(double* dst, const int* orig, int n_pad, double val, cudaStream_t st)
 {
     fill_valid_kernel<<<grid_for(n_pad), 256, 0, st>>>(dst, orig, n_pad, val);

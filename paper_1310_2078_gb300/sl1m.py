@@ -34,7 +34,8 @@ EXPORTS = [
     "sl1m_profile_enable", "sl1m_profile_reset", "sl1m_profile_read", "sl1m_problem_bytes",
     "sl1m_counters", "sl1m_counters_reset", "sl1m_plan_preview", "sl1m_granule_order",
     "sl1m_server_start", "sl1m_server_submit", "sl1m_server_poll", "sl1m_server_wait",
-    "sl1m_server_stop", "sl1m_server_info", "sl1m_forward_noalloc",
+    "sl1m_server_stop", "sl1m_server_info", "sl1m_forward_noalloc", "sl1m_autotune",
+    "sl1m_dirty_image", "sl1m_solve_refine", "sl1m_get_solution",
 ]
 
 
@@ -47,7 +48,8 @@ class SolveOpts(C.Structure):
 
 class ServerOpts(C.Structure):
     _fields_ = [("mem_budget_bytes", C.c_int64), ("max_slots", C.c_int32),
-                ("ticks_per_round", C.c_int32), ("precision", C.c_int32)]
+                ("ticks_per_round", C.c_int32), ("precision", C.c_int32), ("reserved", C.c_int32),
+                ("max_pairs_per_tick", C.c_double)]
 
 
 class ServerInfo(C.Structure):
@@ -59,6 +61,10 @@ class ServerInfo(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class RefineOpts(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("refine_frac", C.c_double), ("keep_unrefined", C.c_int32)]
+
+
 class SolveStats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("E", C.c_double),
                 ("E_paper", C.c_double), ("resid2", C.c_double), ("l1", C.c_double),
@@ -67,6 +73,18 @@ class SolveStats(C.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class RefineStats(C.Structure):
+    _fields_ = [("levels_done", C.c_int32), ("n_pix", C.c_int64 * 17), ("iters", C.c_int32 * 17),
+                ("power_iters", C.c_int32 * 17), ("final_n_pix", C.c_int64),
+                ("total_pair_evals", C.c_double), ("last", SolveStats)]
+
+    def as_dict(self):
+        n = self.levels_done
+        return {"levels_done": n, "n_pix": list(self.n_pix)[:n], "iters": list(self.iters)[:n],
+                "power_iters": list(self.power_iters)[:n], "final_n_pix": self.final_n_pix,
+                "total_pair_evals": self.total_pair_evals, "last": self.last.as_dict()}
 
 
 _lib = None
@@ -106,6 +124,11 @@ def load():
             "sl1m_adjoint": ([vp, vp, vp, C.c_int], C.c_int),
             "sl1m_forward_dev": ([vp, vp, vp, C.c_int], C.c_int),
             "sl1m_forward_noalloc": ([vp, vp, vp, C.c_int], C.c_int),
+            "sl1m_autotune": ([vp, C.c_int, vp, vp], C.c_int),
+            "sl1m_dirty_image": ([vp, C.c_int, vp, C.POINTER(d)], C.c_int),
+            "sl1m_solve_refine": ([vp, C.POINTER(SolveOpts), C.POINTER(RefineOpts), d, C.POINTER(RefineStats)],
+                                  C.c_int),
+            "sl1m_get_solution": ([vp, C.POINTER(i64), vp, vp], C.c_int),
             "sl1m_adjoint_dev": ([vp, vp, vp, C.c_int], C.c_int),
             "sl1m_max_eig": ([vp, C.c_int, d, C.c_int, C.POINTER(d), C.POINTER(C.c_int)], C.c_int),
             "sl1m_solve": ([vp, C.POINTER(SolveOpts), vp, C.POINTER(SolveStats)], C.c_int),
@@ -116,8 +139,8 @@ def load():
             "sl1m_problem_bytes": ([vp, C.POINTER(i64)], C.c_int),
             "sl1m_counters": ([vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)], C.c_int),
             "sl1m_counters_reset": ([vp], C.c_int),
-            "sl1m_plan_preview": ([i32, vp, vp, i32, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32),
-                                   vp, vp, vp], C.c_int),
+            "sl1m_plan_preview": ([i32, vp, vp, i32, vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32),
+                                   vp, vp, vp, vp], C.c_int),
             "sl1m_granule_order": ([i64, vp, vp, C.POINTER(i64)], C.c_int),
             "sl1m_server_start": ([vp, C.POINTER(ServerOpts)], C.c_int),
             "sl1m_server_submit": ([vp, vp, C.POINTER(SolveOpts), C.POINTER(C.c_uint64)], C.c_int),
@@ -161,7 +184,7 @@ def _tptr(t):
     return t.data_ptr()
 
 
-def plan_preview(owned_blocks, streamed_granules, max_ctas):
+def plan_preview(owned_blocks, streamed_granules, max_ctas, unit_costs=None):
     """Host-only stream-K schedule (sl1m_plan_preview)."""
     lib = load()
     nb = np.ascontiguousarray(np.asarray(owned_blocks, np.int32))
@@ -170,13 +193,16 @@ def plan_preview(owned_blocks, streamed_granules, max_ctas):
     fc = np.zeros(max(1, nbt), np.int32)
     nc = np.zeros(max(1, nbt), np.int32)
     fs = np.zeros(max(1, nbt), np.int32)
+    cu = np.zeros(max(1, int(max_ctas)) + 1, np.int64)
+    uc = None if unit_costs is None else np.ascontiguousarray(np.asarray(unit_costs, np.float32))
     C_, U, S = C.c_int32(), C.c_int64(), C.c_int32()
-    st = lib.sl1m_plan_preview(len(nb), _ptr(nb), _ptr(ns), int(max_ctas), C.byref(C_), C.byref(U),
-                               C.byref(S), _ptr(fc), _ptr(nc), _ptr(fs))
+    st = lib.sl1m_plan_preview(len(nb), _ptr(nb), _ptr(ns), int(max_ctas), _ptr(uc), C.byref(C_), C.byref(U),
+                               C.byref(S), _ptr(fc), _ptr(nc), _ptr(fs), _ptr(cu))
     if st != OK:
         raise SL1MError(st, "sl1m_plan_preview failed")
     return {"n_ctas": C_.value, "n_units": U.value, "n_slots": S.value,
-            "first_cta": fc[:nbt], "n_ctas_blk": nc[:nbt], "first_slot": fs[:nbt]}
+            "first_cta": fc[:nbt], "n_ctas_blk": nc[:nbt], "first_slot": fs[:nbt],
+            "cta_first_unit": cu[:C_.value + 1]}
 
 
 def granule_order(xy):
@@ -240,8 +266,10 @@ class Context:
         self.check(self.lib.sl1m_counters_reset(self.h))
 
     # ---- continuous-batching server (sl1m_server_*)
-    def server_start(self, mem_budget_bytes=0, max_slots=0, ticks_per_round=0, precision=MIXED):
-        o = ServerOpts(int(mem_budget_bytes), int(max_slots), int(ticks_per_round), int(precision))
+    def server_start(self, mem_budget_bytes=0, max_slots=0, ticks_per_round=0, precision=MIXED,
+                     max_pairs_per_tick=0.0):
+        o = ServerOpts(int(mem_budget_bytes), int(max_slots), int(ticks_per_round), int(precision), 0,
+                       float(max_pairs_per_tick))
         self.check(self.lib.sl1m_server_start(self.h, C.byref(o)))
 
     def server_submit(self, problem, lam, L=0.0, max_iter=200, rel_tol=0.0, x0=None,
@@ -348,6 +376,13 @@ class Problem:
         """r_t: float64 CUDA tensor [n_vis, 2]; out_t: float64 CUDA tensor [n_pix]."""
         self.ctx.check(self.lib.sl1m_adjoint_dev(self.h, _tptr(r_t), _tptr(out_t), int(precision)))
 
+    def dirty_image(self, precision=MIXED):
+        """sl1m_dirty_image: (Re A^H W V, lambda_max)."""
+        img = np.zeros(self.n_pix)
+        lm = C.c_double()
+        self.ctx.check(self.lib.sl1m_dirty_image(self.h, int(precision), _ptr(img), C.byref(lm)))
+        return img, lm.value
+
     def max_eig(self, max_iter=50, tol=1e-6, precision=MIXED):
         L, it = C.c_double(), C.c_int()
         self.ctx.check(self.lib.sl1m_max_eig(self.h, int(max_iter), float(tol), int(precision),
@@ -363,6 +398,28 @@ class Problem:
         st = SolveStats()
         self.ctx.check(self.lib.sl1m_solve(self.h, C.byref(o), _ptr(img), C.byref(st)))
         return img, st.as_dict()
+
+    def autotune(self, precision=MIXED):
+        """sl1m_autotune: returns {"nst": [fwd, adj], "ctas_per_sm": [fwd, adj]}."""
+        nst = np.zeros(2, np.int32)
+        k = np.zeros(2, np.int32)
+        self.ctx.check(self.lib.sl1m_autotune(self.h, int(precision), _ptr(nst), _ptr(k)))
+        return {"nst": nst.tolist(), "ctas_per_sm": k.tolist()}
+
+    def solve_refine(self, lam, delta0, levels, refine_frac=0.01, keep_unrefined=True, L=0.0,
+                     max_iter=200, rel_tol=0.0, precision=MIXED):
+        """sl1m_solve_refine: returns (lm [n,2], image [n], stats)."""
+        o = SolveOpts(float(lam), float(L), float(rel_tol), int(max_iter), int(precision), 0, 0.0, None)
+        ro = RefineOpts(int(levels), float(refine_frac), int(bool(keep_unrefined)))
+        st = RefineStats()
+        self.ctx.check(self.lib.sl1m_solve_refine(self.h, C.byref(o), C.byref(ro), float(delta0), C.byref(st)))
+        n = C.c_int64()
+        self.ctx.check(self.lib.sl1m_get_solution(self.h, C.byref(n), None, None))
+        lm = np.zeros((n.value, 2))
+        img = np.zeros(n.value)
+        self.ctx.check(self.lib.sl1m_get_solution(self.h, C.byref(n), _ptr(lm), _ptr(img)))
+        self.n_pix = n.value
+        return lm, img, st.as_dict()
 
     def bytes(self):
         b = C.c_int64()

@@ -49,6 +49,48 @@ def test_stream_k_plan_covers_every_unit_once(sl1m, nb, ns, cmax):
     assert lo[0] == 0 and hi[-1] == U and all(hi[c] == lo[c + 1] for c in range(C - 1))
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_cost_weighted_plan_balances_cost(sl1m, seed):
+    """Units of unequal cost (clustered 3x tiles): every CTA gets total/C of
+    the cost up to one unit, blocks stay consistent with the CTA ranges."""
+    rng = np.random.default_rng(seed)
+    nb, ns, cmax = [7, 3], [200, 57], 40
+    U = 7 * 200 + 3 * 57
+    cost = np.ones(U, np.float32)
+    start = rng.integers(0, U - 300)
+    cost[start:start + 300] = 3.0                       # a clustered run of costly units
+    cost[rng.choice(U, 50)] = 1.6
+    pv = sl1m.plan_preview(nb, ns, cmax, cost)
+    cu = pv["cta_first_unit"]
+    C = pv["n_ctas"]
+    assert cu[0] == 0 and cu[-1] == U and np.all(np.diff(cu) >= 0)
+    per = np.array([cost[cu[c]:cu[c + 1]].sum() for c in range(C)])
+    assert per.max() <= cost.sum() / C + cost.max() + 1e-3
+    # a uniform split would be much worse on this input
+    uni = np.array([cost[(U * c) // C:(U * (c + 1)) // C].sum() for c in range(C)])
+    assert per.max() < uni.max()
+    # block tables agree with the CTA ranges
+    gb, u0 = 0, 0
+    for a, b in zip(nb, ns):
+        for blk in range(a):
+            s_, e_ = u0 + blk * b, u0 + (blk + 1) * b
+            ctas = [c for c in range(C) if cu[c] < e_ and cu[c + 1] > s_]
+            assert pv["first_cta"][gb] == ctas[0] and pv["n_ctas_blk"][gb] == len(ctas)
+            gb += 1
+        u0 += a * b
+
+
+def test_cost_weighted_plan_has_no_empty_cta(sl1m):
+    """Few units of very unequal cost: every CTA still gets a unit (a block's
+    partial slots are those of all CTAs between its first and its last)."""
+    cost = np.array([1, 9, 1, 1, 9, 9, 1, 1, 1, 9, 1, 1], np.float32)
+    pv = sl1m.plan_preview([3], [4], 12, cost)
+    cu = pv["cta_first_unit"]
+    assert pv["n_ctas"] == 12 and np.all(np.diff(cu) >= 1)
+    pv = sl1m.plan_preview([2, 1], [3, 4], 7, np.array([5, 1, 1, 1, 1, 1, 9, 1, 1, 1], np.float32))
+    assert np.all(np.diff(pv["cta_first_unit"]) >= 1)
+
+
 def test_plan_rejects_bad_arguments(sl1m):
     with pytest.raises(sl1m.SL1MError):
         sl1m.plan_preview([1], [-1], 4)
