@@ -14,6 +14,7 @@ ctypes.  Every function cites the passage of Hardy (2013) it follows:
 * :func:`adjoint`  -- Re(A^H r), the back-projection of Sect. 3
 * :func:`power`    -- L = largest eigenvalue of Re(A^H W A), Sect. 3.1
 * :func:`fista`    -- the FISTA box of Sect. 3 with Eq. threshp
+* :func:`mfista`   -- the monotone FISTA that Sect. 3 names (Beck & Teboulle 2009b)
 """
 from __future__ import annotations
 
@@ -80,8 +81,10 @@ def _load():
             lib.orc_power.argtypes = [P, C.c_int, C.c_double, d, C.POINTER(C.c_int)]
             lib.orc_fista.argtypes = [P, d, C.c_double, C.c_double, C.c_int,
                                       C.c_double, d, d, C.POINTER(Stats)]
+            lib.orc_mfista.argtypes = [P, d, C.c_double, C.c_double, C.c_int,
+                                       C.c_double, d, d, C.POINTER(Stats), d]
             for f in ("orc_entry", "orc_entry_kj", "orc_forward_rows",
-                      "orc_adjoint_cols", "orc_power", "orc_fista"):
+                      "orc_adjoint_cols", "orc_power", "orc_fista", "orc_mfista"):
                 getattr(lib, f).restype = C.c_int
             _lib = lib
     return _lib
@@ -211,3 +214,24 @@ def fista(P: Problem, vis, lam, L, max_iter, tol=0.0, x0=None):
     _check(_load().orc_fista(P.c, _dp(vv), float(lam), float(L), int(max_iter),
                              float(tol), _dp(x0), _dp(img), C.byref(st)), "fista")
     return img, st.as_dict()
+
+
+def mfista(P: Problem, vis, lam, L, max_iter, tol=0.0, x0=None, trace=False):
+    """(image, stats dict[, trace]): monotone FISTA (Beck & Teboulle 2009b),
+    the variant Sect. 3 names.  With ``trace`` the third value holds, per
+    step k, a dict of arrays y, z, x [iters, n_pix] and t, Fz, Fx [iters]."""
+    v = np.asarray(vis, dtype=np.complex128)
+    vv = np.ascontiguousarray(np.stack([v.real, v.imag], axis=-1))
+    img = np.zeros(P.n_pix)
+    st = Stats()
+    x0 = _f64(x0)
+    n = P.n_pix
+    tr = np.zeros((max(int(max_iter), 1), 3 * n + 3)) if trace else None
+    _check(_load().orc_mfista(P.c, _dp(vv), float(lam), float(L), int(max_iter),
+                              float(tol), _dp(x0), _dp(img), C.byref(st), _dp(tr)), "mfista")
+    d = st.as_dict()
+    if not trace:
+        return img, d
+    tr = tr[:d["iters"]]
+    return img, d, {"y": tr[:, :n], "z": tr[:, n:2 * n], "x": tr[:, 2 * n:3 * n],
+                    "t": tr[:, 3 * n], "Fz": tr[:, 3 * n + 1], "Fx": tr[:, 3 * n + 2]}

@@ -15,7 +15,8 @@
  *   - the step constant L, the largest eigenvalue of Re(A^H W A), by power
  *     iteration (Sect. 3.1 names such a routine but not its method);
  *   - FISTA with the positive soft threshold (Sect. 3, the algorithm box and
- *     Eq. threshp), with the relative-change-of-E stopping rule.
+ *     Eq. threshp), with the relative-change-of-E stopping rule;
+ *   - MFISTA, the monotone variant Sect. 3 names (Beck & Teboulle 2009b).
  *
  * Index convention: pixel j (n_pix of them), visibility k (n_vis of them).
  * The paper's M_jk (j = visibility, k = pixel) is A_kj here.
@@ -36,6 +37,8 @@
  *   R6  Gains: g_jk = G[j][a_k] * conj(G[j][b_k]).  Weights W_k >= 0 multiply
  *       the squared residual (W = 1 is the paper's case).
  *   R7  Threshold ties (x == d) map to 0, as Eq. threshp states.
+ *   R8  MFISTA keeps the proximal point z_k when F(z_k) == F(x_{k-1}), and
+ *       stops when the step proposed a relative change of F below tol.
  *
  * Summation order: forward sums pixels in index order j = 0..n_pix-1, adjoint
  * sums visibilities in index order k = 0..n_vis-1, with plain FP64 "+=".
@@ -386,5 +389,120 @@ int orc_fista(const orc_problem *P, const double *vis, double lambda, double L,
         }
     }
     free(Ik); free(Iprev); free(y); free(g); free(res);
+    return st;
+}
+
+/* MFISTA, the monotone FISTA of Beck & Teboulle (2009b), which Sect. 3 names
+ * as the alternative to FISTA that keeps the objective from rising.  With
+ * F(x) = 1/2 sum W|A x - V|^2 + lambda sum x over x >= 0 (reading R4) and the
+ * same proximal step as the FISTA box:
+ *   Step 0:  x_0 = y_1 = x0 (zero when x0 is NULL), t_1 = 1
+ *   Step k:  z_k = T^{lambda/L}( y_k - (1/L) Re A^H W (A y_k - V) )
+ *            t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2
+ *            x_k = z_k if F(z_k) <= F(x_{k-1}), else x_{k-1}
+ *            y_{k+1} = x_k + (t_k/t_{k+1}) (z_k - x_k)
+ *                          + ((t_k - 1)/t_{k+1}) (x_k - x_{k-1})
+ * (ties keep the new point z_k).  Stopping: when tol > 0, stop after step k
+ * once |F(z_k) - F(x_{k-1})| <= tol * F(x_{k-1}), i.e. the step proposed a
+ * relative change of the objective below tol (on an accepted step this is
+ * the FISTA rule on E(x_k)).  img_out receives the last x_k.
+ * trace (may be NULL) receives, for each step k = 1..iters, the row
+ *   [ y_k (n_pix) | z_k (n_pix) | x_k (n_pix) | t_k | F(z_k) | F(x_k) ]
+ * of 3 n_pix + 3 doubles; it must hold max_iter rows. */
+static int objective_of(const orc_problem *P, const double *x, const double *vis, double lambda,
+                        double *work, double *out)
+{
+    double r2;
+    int st = resid2_of(P, x, vis, work, &r2);
+    if (st) return st;
+    double l1 = 0.0;
+    for (long j = 0; j < P->n_pix; ++j) l1 += x[j];
+    *out = 0.5 * r2 + lambda * l1;
+    return ORC_OK;
+}
+
+int orc_mfista(const orc_problem *P, const double *vis, double lambda, double L,
+               int max_iter, double tol, const double *x0, double *img_out,
+               orc_stats *stats, double *trace)
+{
+    if (check_problem(P) || !vis || !img_out || !(L > 0.0) || !(lambda >= 0.0) || max_iter < 0)
+        return ORC_ERR_ARG;
+    long np = P->n_pix, nv = P->n_vis;
+    double *x = calloc(np, sizeof(double));      /* x_{k-1}, then x_k */
+    double *z = calloc(np, sizeof(double));
+    double *y = calloc(np, sizeof(double));
+    double *g = calloc(np, sizeof(double));
+    double *res = calloc(2 * nv + 2, sizeof(double));
+    if (!x || !z || !y || !g || !res) {
+        free(x); free(z); free(y); free(g); free(res);
+        return ORC_ERR_OOM;
+    }
+    if (x0) {
+        memcpy(x, x0, sizeof(double) * np);
+        memcpy(y, x0, sizeof(double) * np);
+    }
+    double t = 1.0, Fx = 0.0;
+    int st = objective_of(P, x, vis, lambda, res, &Fx);
+    int k = 0, converged = 0;
+    const long row = 3 * np + 3;
+    for (k = 1; k <= max_iter && st == ORC_OK; ++k) {
+        double *tr = trace ? trace + (long)(k - 1) * row : NULL;
+        if (tr) memcpy(tr, y, sizeof(double) * np);
+        /* z_k: the proximal gradient step at y_k */
+        st = orc_forward(P, y, res);
+        if (st) break;
+        for (long q = 0; q < nv; ++q) {
+            double wk = P->weights ? P->weights[q] : 1.0;
+            res[2 * q] = wk * (res[2 * q] - vis[2 * q]);
+            res[2 * q + 1] = wk * (res[2 * q + 1] - vis[2 * q + 1]);
+        }
+        st = orc_adjoint(P, res, g);
+        if (st) break;
+        for (long j = 0; j < np; ++j)
+            z[j] = thresh_pos(y[j] - g[j] / L, lambda / L);
+        double t_next = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        /* x_k: the better of z_k and x_{k-1} */
+        double Fz;
+        st = objective_of(P, z, vis, lambda, res, &Fz);
+        if (st) break;
+        const double Fx_prev = Fx;
+        const int take = Fz <= Fx;
+        /* y_{k+1}; x_k - x_{k-1} is z_k - x_{k-1} when z_k is taken, else 0 */
+        for (long j = 0; j < np; ++j) {
+            double xk = take ? z[j] : x[j];
+            y[j] = xk + (t / t_next) * (z[j] - xk) + ((t - 1.0) / t_next) * (xk - x[j]);
+            x[j] = xk;
+        }
+        if (take) Fx = Fz;
+        if (tr) {
+            memcpy(tr + np, z, sizeof(double) * np);
+            memcpy(tr + 2 * np, x, sizeof(double) * np);
+            tr[3 * np] = t;
+            tr[3 * np + 1] = Fz;
+            tr[3 * np + 2] = Fx;
+        }
+        t = t_next;
+        if (tol > 0.0 && fabs(Fz - Fx_prev) <= tol * Fx_prev) { converged = 1; break; }
+    }
+    int iters = (k > max_iter) ? max_iter : k;
+    if (st == ORC_OK) {
+        memcpy(img_out, x, sizeof(double) * np);
+        if (stats) {
+            double r2 = 0.0;
+            st = resid2_of(P, x, vis, res, &r2);
+            double l1 = 0.0;
+            long nnz = 0;
+            for (long j = 0; j < np; ++j) { l1 += x[j]; nnz += x[j] > 0.0; }
+            stats->iters = iters;
+            stats->converged = converged;
+            stats->resid2 = r2;
+            stats->l1 = l1;
+            stats->nnz = nnz;
+            stats->E = 0.5 * r2 + lambda * l1;
+            stats->E_paper = r2 + lambda * l1;
+            stats->t_final = t;
+        }
+    }
+    free(x); free(z); free(y); free(g); free(res);
     return st;
 }

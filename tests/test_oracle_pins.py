@@ -419,3 +419,123 @@ def test_stopping_rule_relative_change_of_E():
     img2, st2 = oracle.fista(P, V, 0.2, L, max_iter=st["iters"] - 1)
     assert abs(st["E"] - st2["E"]) <= 1e-6 * st2["E"] * (1 + 1e-9)
     assert st["E_paper"] == pytest.approx(st["resid2"] + 0.2 * st["l1"])
+
+
+# ---------------------------------------------------------------- MFISTA
+
+def _mfista_case(seed, lam=0.05):
+    """A small ill-conditioned problem on which FISTA's objective oscillates,
+    so that MFISTA rejects some proximal points."""
+    P, d = _problem(seed, 30, 6, kinds=(DIRAC, PAR), weights=True, uv_max=40, w_max=10,
+                    extent=0.2, sigma_max=0.02)
+    A = _dense(P)
+    W = d["weights"]
+    rng = np.random.default_rng(seed)
+    xt = np.abs(rng.normal(size=6)) * (rng.random(6) < 0.6)
+    V = A @ xt + 0.02 * (rng.normal(size=30) + 1j * rng.normal(size=30))
+    B, _ = _normal_eqs(A, W, V)
+    L = np.linalg.eigvalsh(B)[-1]
+    return P, A, W, V, L, lam
+
+
+def _F(A, W, V, lam, x):
+    return 0.5 * np.sum(W * np.abs(A @ x - V) ** 2) + lam * x.sum()
+
+
+@pytest.mark.parametrize("seed", [61, 64])
+def test_mfista_is_fista_until_the_first_rejection(seed):
+    """While every proximal point is accepted, MFISTA's y-update reduces to
+    FISTA's, so its iterates equal FISTA's bit for bit."""
+    P, A, W, V, L, lam = _mfista_case(seed)
+    _, st, tr = oracle.mfista(P, V, lam, L, 200, trace=True)
+    rej = np.flatnonzero(tr["Fz"] > np.r_[_F(A, W, V, lam, np.zeros(6)), tr["Fx"][:-1]])
+    assert len(rej) >= 1                        # the case does exercise a rejection
+    first = rej[0]                              # step first+1 is the first rejected one
+    assert first >= 2
+    for k in (1, first):
+        img, _ = oracle.fista(P, V, lam, L, max_iter=k)
+        assert np.array_equal(img, tr["x"][k - 1])
+
+
+@pytest.mark.parametrize("seed", [61, 64])
+def test_mfista_steps_follow_the_estimate_sequence(seed):
+    """Each step of the trace checked against forms other than the update the
+    oracle codes: F recomputed from the dense matrix; x_k the better of z_k and
+    x_{k-1}; z_k the KKT point of the proximal step at y_k; and y_{k+1} in the
+    estimate-sequence form of the convergence proof,
+        y_{k+1} = (1 - 1/t_{k+1}) x_k + u_k / t_{k+1},
+        u_k = x_{k-1} + t_k (z_k - x_{k-1})."""
+    P, A, W, V, L, lam = _mfista_case(seed)
+    _, st, tr = oracle.mfista(P, V, lam, L, 120, trace=True)
+    B, c = _normal_eqs(A, W, V)
+    x_prev = np.zeros(6)
+    Fx_prev = _F(A, W, V, lam, x_prev)
+    n_rej = 0
+    for k in range(len(tr["t"])):
+        y, z, x, t = tr["y"][k], tr["z"][k], tr["x"][k], tr["t"][k]
+        Fz = _F(A, W, V, lam, z)
+        assert abs(Fz - tr["Fz"][k]) <= 1e-12 * Fz
+        # z: for each j, either z_j > 0 and L (y - z)_j - grad_j = lam, or z_j = 0
+        # and L y_j - grad_j <= lam, with grad = B y - c at y
+        s = L * y - (B @ y - c)
+        on = z > 0
+        assert np.allclose(L * z[on], s[on] - lam, rtol=0, atol=1e-9 * (1 + np.abs(s).max()))
+        assert np.all(s[~on] <= lam + 1e-9 * (1 + np.abs(s).max()))
+        if Fz <= Fx_prev:
+            assert np.array_equal(x, z)
+        else:
+            n_rej += 1
+            assert np.array_equal(x, x_prev)
+        if k + 1 < len(tr["t"]):
+            tn = tr["t"][k + 1]
+            assert tn == pytest.approx((1 + math.sqrt(1 + 4 * t * t)) / 2, rel=1e-15)
+            u = x_prev + t * (z - x_prev)
+            assert np.allclose(tr["y"][k + 1], (1 - 1 / tn) * x + u / tn, rtol=0,
+                               atol=1e-12 * (1 + np.abs(u).max()))
+        x_prev, Fx_prev = x, min(Fz, Fx_prev)
+    assert n_rej >= 1
+
+
+@pytest.mark.parametrize("seed", [61, 62, 63, 64])
+def test_mfista_is_monotone_and_meets_the_rate_bound(seed):
+    """F(x_k) never rises, F(x_k) - F* <= 2 L ||x_0 - x*||^2 / (k+1)^2
+    (Beck & Teboulle 2009b), and the brute-force minimiser is reached."""
+    P, A, W, V, L, lam = _mfista_case(seed, lam=0.5)
+    xs, Fs = brute_force_l1(A, W, V, lam)
+    _, st, tr = oracle.mfista(P, V, lam, L, 300, trace=True)
+    Fx = np.array([_F(A, W, V, lam, x) for x in tr["x"]])
+    assert np.all(np.diff(Fx) <= 1e-14 * Fx[0])
+    k = np.arange(1, len(Fx) + 1)
+    assert np.all(Fx - Fs <= 2 * L * np.sum(xs ** 2) / (k + 1) ** 2 + 1e-9)
+    img, st = oracle.mfista(P, V, lam, L, max_iter=20000)
+    assert np.max(np.abs(img - xs)) < 1e-7 * max(1.0, xs.max())
+    assert abs(st["E"] - Fs) < 1e-10 * Fs
+
+
+def test_mfista_single_pixel_closed_form():
+    """N_p = 1 with L = ||a||_W^2: the first step reaches the minimiser and
+    every later proximal point equals it."""
+    P, d = _problem(51, 25, 1, weights=True)
+    a = _dense(P)[:, 0]
+    W = d["weights"]
+    rng = np.random.default_rng(2)
+    V = 3.0 * a + 0.1 * (rng.normal(size=25) + 1j * rng.normal(size=25))
+    L = np.sum(W * np.abs(a) ** 2)
+    for lam in (0.0, 1.0, 20.0, 1e4):
+        want = max(0.0, (np.real(np.vdot(a, W * V)) - lam) / L)
+        for k in (1, 5):
+            img, st = oracle.mfista(P, V, lam, L, max_iter=k)
+            assert abs(img[0] - want) < 1e-12 * max(1.0, want)
+
+
+def test_mfista_stopping_rule():
+    """With tol, MFISTA stops at the first step whose proposed objective
+    change |F(z_k) - F(x_{k-1})| is within tol of F(x_{k-1})."""
+    P, A, W, V, L, lam = _mfista_case(64, lam=0.2)
+    _, _, tr = oracle.mfista(P, V, lam, L, 3000, trace=True)
+    Fprev = np.r_[_F(A, W, V, lam, np.zeros(6)), tr["Fx"][:-1]]
+    hit = np.flatnonzero(np.abs(tr["Fz"] - Fprev) <= 1e-6 * Fprev)
+    assert len(hit) >= 1
+    img, st = oracle.mfista(P, V, lam, L, 3000, tol=1e-6)
+    assert st["converged"] == 1 and st["iters"] == hit[0] + 1
+    assert np.array_equal(img, tr["x"][hit[0]])
