@@ -21,6 +21,7 @@ import argparse
 import json
 import math
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -149,15 +150,21 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def ncu_traffic():
-    """dram bytes per launch of the dominant kernel from the committed ncu
-    summary (null when absent or stale)."""
-    p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+def ncu_traffic(kernel, nst, ctas, workload):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, or None when no summary matches this kernel, tile shape, grid and
+    workload (the counters belong to the kernel as it was captured)."""
+    p = os.path.join(ROOT, "profiles", "launch_list_wide_field_dirac_256x256_40320vis.md")
     try:
         with open(p) as f:
-            return json.load(f)
-    except (OSError, ValueError):
+            text = f.read()
+    except OSError:
         return None
+    for m in re.finditer(r"^traffic: kernel=(\S+) nst=(\d+) ctas=(\d+) workload=(\S+) "
+                         r"dram_bytes_per_launch=(\d+)$", text, re.M):
+        if (m.group(1), int(m.group(2)), int(m.group(3)), m.group(4)) == (kernel, nst, ctas, workload):
+            return int(m.group(5))
+    return None
 
 
 def cpu_baseline(w, budget_s: float = 12.0):
@@ -400,13 +407,16 @@ def main():
     achieved = pd["pairs"] / (pd["ms"] / 1e3) / 1e9 if pd["ms"] > 0 else 0.0
     kind = "gauss" if (w.kind is not None and np.any(w.kind != 0)) else "dirac"
     peak = N_SM * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / SFU_OPS_PER_PAIR[kind] / 1e9
-    traffic = ncu_traffic()
+    traffic = None
+    if tuned is not None:
+        op = 0 if dom.startswith("fwd") else 1
+        traffic = ncu_traffic(dom, tuned["nst"][op], tuned["ctas_per_sm"][op] * N_SM, w.name)
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
                 "unit": "Gpairs/s", "frac": achieved / peak,
                 "peak_basis": (f"SFU issue: {N_SM} SM x {MUFU_PER_SM_CLK} MUFU/clk x "
                                f"{SM_MAX_MHZ:.0f} MHz / {SFU_OPS_PER_PAIR[kind]} MUFU per pair"),
                 "launches": pd["launches"], "avg_launch_ms": pd["ms"] / max(1, pd["launches"]),
-                "traffic": (traffic or {}).get("dram_bytes_per_launch")}
+                "traffic": traffic}
     fin_ms = prof["fwd_finish"]["ms"] + prof["adj_finish"]["ms"]
     fin_bytes = prof["fwd_finish"]["bytes"] + prof["adj_finish"]["bytes"]
     vec = {"kernels": "fwd_finish+adj_finish (residual, threshold, momentum)",
