@@ -53,6 +53,10 @@ extern "C" {
  * Eq. gaus has unit integral, so x_j is the pixel's total flux; and the
  * wide-field residual phase is w (n - 1 + (l^2+m^2)/2), the form whose
  * Taylor expansion is Eq. taylorexp.) */
+/* Solvers (sl1m_solve_opts.algorithm). */
+#define SL1M_FISTA 0          /* the algorithm box of Sect. 3                  */
+#define SL1M_MFISTA 1         /* its monotone variant, Beck & Teboulle (2009b) */
+
 #define SL1M_DIRAC 0
 #define SL1M_GAUSS_PARAXIAL 1
 #define SL1M_GAUSS_WIDE 2
@@ -161,7 +165,9 @@ int sl1m_max_eig(sl1m_problem* prob, int max_iter, double tol, int precision,
  * when |E_k - E_{k-1}| <= rel_tol * E_{k-1} (Sect. 3; 0 = run max_iter
  * steps), where E = 1/2 sum W |A I - V|^2 + lambda sum I is the objective the
  * algorithm box minimises.  x0: starting image [n_pix] (host) or NULL (zero,
- * the box's Step 0). */
+ * the box's Step 0).  algorithm: SL1M_FISTA (default, zero) or SL1M_MFISTA;
+ * for MFISTA, rel_tol applies to the objective change a step proposes,
+ * |E(z_k) - E(x_{k-1})| <= rel_tol * E(x_{k-1}). */
 typedef struct {
     double lambda;
     double L;
@@ -171,6 +177,7 @@ typedef struct {
     int32_t power_max_iter;   /* 0 = 50   */
     double power_tol;         /* 0 = 1e-6 */
     const double* x0;
+    int32_t algorithm;        /* SL1M_FISTA (0) or SL1M_MFISTA */
 } sl1m_solve_opts;
 
 typedef struct {
@@ -191,6 +198,14 @@ typedef struct {
  *   t_{k+1} = (1 + sqrt(1 + 4 t_k^2))/2,
  *   y_{k+1} = I_k + ((t_k - 1)/t_{k+1}) (I_k - I_{k-1}).
  * img_out [n_pix] (host) receives the last I_k; stats may be NULL.
+ * With algorithm = SL1M_MFISTA, the monotone variant that Sect. 3 names
+ * (Beck & Teboulle 2009b):
+ *   z_k = T^{lambda/L}(y_k - Re A^H W (A y_k - V)/L),
+ *   x_k = z_k if E(z_k) <= E(x_{k-1}), else x_{k-1},
+ *   y_{k+1} = x_k + (t_k/t_{k+1})(z_k - x_k) + ((t_k - 1)/t_{k+1})(x_k - x_{k-1});
+ * E(z_k) comes from the forward product the stopping test already needs and
+ * A y_{k+1} follows by linearity, so a step costs one forward and one
+ * adjoint, as a FISTA step does.  img_out receives x_k, and E never rises.
  * Synchronous.  SL1M_ERR_NONFINITE if a non-finite value appeared. */
 int sl1m_solve(sl1m_problem* prob, const sl1m_solve_opts* opts, double* img_out,
                sl1m_solve_stats* stats);

@@ -72,7 +72,8 @@ struct Side {
 //   PINIT  forward of x = 1/sqrt(n) -> r = W A x
 //   POWER  power-iteration step: z = B x_unit, then r = W A z; mu = ||z||
 //   SINIT  forward of I_0 -> A I_0, r = W (A I_0 - V), E_0
-//   SOLVE  one FISTA step (Sect. 3 algorithm box)
+//   SOLVE  one FISTA step (Sect. 3 algorithm box), or one MFISTA step
+//          (Beck & Teboulle 2009b), which a sixth kernel finishes (mix)
 //   DONE   finished (converged, max_iter reached, or non-finite)
 enum Phase : int { PH_IDLE = 0, PH_PINIT = 1, PH_POWER = 2, PH_SINIT = 3, PH_SOLVE = 4, PH_DONE = 5 };
 
@@ -90,6 +91,11 @@ struct SolveState {
     int converged;
     int nonfinite;       // 1: a non-finite value was met
     int power_only;      // 1: stop after the power iteration (L only)
+    // MFISTA (algo = 1): I[0] = x_k, I[1] = z_k, AI[0] = A x_k, AI[1] = A z_k
+    int algo;            // 0 FISTA, 1 MFISTA
+    int take;            // last step kept z_k (F(z_k) <= F(x_{k-1}))
+    int mix_pending;     // the mix kernel of this tick finishes the last step
+    double cmix;         // y_{k+1} = x_{k-1} + cmix (z_k - x_{k-1})
     // power iteration
     double mu, mu_prev, inv_mu;
     int pit, pmax;
@@ -141,7 +147,7 @@ __device__ __forceinline__ bool fwd_role(const DevProblem& P, const double*& X)
     const int ph = P.st->phase;
     if (ph == PH_PINIT || ph == PH_POWER) { X = P.b.xv; return true; }
     if (ph == PH_SINIT) { X = P.b.I[0]; return true; }
-    if (ph == PH_SOLVE) { X = P.b.I[(P.st->k + 1) & 1]; return true; }
+    if (ph == PH_SOLVE) { X = P.b.I[P.st->algo ? 1 : (P.st->k + 1) & 1]; return true; }
     return false;
 }
 

@@ -684,6 +684,10 @@ int sl1m_problem::init_solve(const sl1m_solve_opts* o, double L, bool power_only
     s0.pmax = (o && o->power_max_iter > 0) ? o->power_max_iter : 50;
     s0.ptol = (o && o->power_tol > 0) ? o->power_tol : 1e-6;
     s0.power_only = power_only ? 1 : 0;
+    s0.algo = (o && o->algorithm == SL1M_MFISTA && !power_only) ? 1 : 0;
+    algo = s0.algo;
+    if (o && o->x0)
+        for (int64_t j = 0; j < n_pix; ++j) s0.nnz += o->x0[j] > 0.0;
     s0.phase = (L > 0.0 && !power_only) ? PH_SINIT : PH_PINIT;
     CK(cudaMemcpyAsync(D.st.p, &s0, sizeof s0, cudaMemcpyHostToDevice, st));
     // the host struct is a temporary: finish the copy before returning
@@ -704,7 +708,7 @@ int sl1m_problem::fetch_image(double* host_out, cudaStream_t st)
     SolveState s;
     RET(read_state(s, st));
     ProblemDev& D = *dev;
-    double* Ik = (s.k & 1) ? D.I1.p : D.I0.p;
+    double* Ik = (!s.algo && (s.k & 1)) ? D.I1.p : D.I0.p;   // MFISTA: x_k lives in I[0]
     CK(D.img_user.reserve(n_pix, st));
     CKL(launch_scatter_real(Ik, D.img_user.p, hp.pix.orig, hp.pix.n_pad, st));
     CK(cudaMemcpyAsync(host_out, D.img_user.p, sizeof(double) * n_pix, cudaMemcpyDeviceToHost, st));
@@ -878,6 +882,17 @@ static int enqueue_tick(sl1m_ctx* ctx, Batch& B)
     for (int c = 0; c < 2; ++c) RET(launch_op_class(ctx, B, 1, c));
     for (int c = 0; c < 2; ++c) RET(launch_op_class(ctx, B, 0, c));
     CKL(launch_scalars(B.desc.p, B.n_probs_dev.p, B.sc_grid, ctx->stream));
+    if (B.has_mfista) {
+        ProfTok tk;
+        prof_begin(ctx, 6, tk);
+        for (int c = 0; c < 2; ++c) {
+            if (!B.has_class[c]) continue;
+            const int nb = B.plan[0][c].pl.n_blocks + B.plan[1][c].pl.n_blocks;
+            CKL(launch_mfista_mix(B.desc.p, B.plan[0][c].dpl.p, B.plan[1][c].dpl.p,
+                                  std::min(B.fin_grid, std::max(1, nb)), ctx->stream));
+        }
+        prof_end(ctx, tk, 0.0, 0.0);
+    }
     return SL1M_OK;
 }
 
@@ -885,6 +900,13 @@ static int enqueue_tick(sl1m_ctx* ctx, Batch& B)
 // kernel) or graphs are off.
 int batch_ticks(sl1m_ctx* ctx, Batch& B, int n)
 {
+    bool hm = false;
+    if (B.solver)
+        for (const sl1m_problem* p : B.probs) hm = hm || p->algo == 1;
+    if (hm != B.has_mfista) {
+        B.has_mfista = hm;
+        B.graph_ok = false;
+    }
     if (!ctx->use_graphs || ctx->prof) {
         for (int i = 0; i < n; ++i) RET(enqueue_tick(ctx, B));
         return SL1M_OK;
@@ -1390,8 +1412,9 @@ int sl1m_autotune(sl1m_problem* prob, int precision, int32_t* nst_out, int32_t* 
         const std::vector<int> ns = {op == 0 ? d.pix.n_gran : d.vis.n_gran};
         const std::vector<const UnitCost*> uc = {&prob->unit_cost(precision, op)};
         const long long units = (long long)nb[0] * ns[0];
-        const std::vector<int> cands = (precision == SL1M_MIXED && !gains) ? std::vector<int>{2, 4, 8}
-                                                                           : std::vector<int>{NST_DEFAULT};
+        // 0 = warp-decoupled forward (warp-private staging, no CTA barrier)
+        std::vector<int> cands = {NST_DEFAULT};
+        if (precision == SL1M_MIXED && !gains) cands = op == 0 ? std::vector<int>{0, 2, 4, 8} : std::vector<int>{2, 4, 8};
         float best = 1e30f;
         int bnst = NST_DEFAULT, bk = 0;
         for (int nst : cands) {

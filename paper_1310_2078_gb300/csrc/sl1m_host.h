@@ -122,6 +122,7 @@ struct Batch {
     int fin_grid = 1, sc_grid = 1;
     double pairs_class[2] = {0, 0};
     double fin_bytes[2] = {0, 0};   // [forward finish, adjoint finish] per tick
+    bool has_mfista = false;         // a tick ends with the MFISTA mix kernel
     // captured tick
     cudaGraphExec_t gexec = nullptr;
     bool graph_ok = false;
@@ -180,6 +181,7 @@ struct sl1m_problem {
     sl1m::SolveBufs hbufs{};
     std::vector<int> vis_orig, pix_orig;
     std::vector<double> last_img;             // image of the last refinement (caller's order)
+    int algo = 0;                              // solver of the last init_solve (0 FISTA, 1 MFISTA)
     std::vector<float4> gext_vis, gext_pix;   // granule extents (host copies)
     std::vector<int> gkind_pix;               // pixel granule kinds
     UnitCost ucost[2][2];                      // [precision][0 forward / 1 adjoint]

@@ -9,7 +9,8 @@ enum FinishMode : int { FIN_OP = 0, FIN_POWER = 1, FIN_SOLVE = 2, FIN_INIT = 3 }
 // operator kernels (sl1m_mixed.cu, sl1m_fp64.cu); precision 0 = FP64, 1 = mixed.
 // plp: device-resident plan; C: its grid size (known on the host).
 // nst: streamed granules per shared-memory stage of the mixed no-gains
-// kernels (2, 4 or 8; the tile shape the autotuner picks).
+// kernels (2, 4 or 8; the tile shape the autotuner picks); for the forward,
+// 0 selects the warp-decoupled kernel (each warp stages for itself).
 constexpr int NST_DEFAULT = 4;
 cudaError_t launch_forward(int precision, bool gains, int n_ant, const DevProblem* probs,
                            const Plan* plp, int C, double2* partial, cudaStream_t st, int nst = NST_DEFAULT);
@@ -33,6 +34,8 @@ cudaError_t launch_weighted_vis(const double2* V, const d4* vd, double2* r, int 
 cudaError_t launch_fwd_finish(const DevProblem* probs, const Plan* plp, int grid, const double2* partial,
                               cudaStream_t st);
 cudaError_t launch_adj_finish(const DevProblem* probs, const Plan* plp, int grid, const double* partial,
+                              cudaStream_t st);
+cudaError_t launch_mfista_mix(const DevProblem* probs, const Plan* fplp, const Plan* aplp, int grid,
                               cudaStream_t st);
 cudaError_t launch_scalars(const DevProblem* probs, const int* n_probs, int grid, cudaStream_t st);
 cudaError_t launch_phases(const DevProblem* probs, const int* n_probs, int grid, int* out, cudaStream_t st);

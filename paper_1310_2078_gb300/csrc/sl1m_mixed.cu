@@ -271,6 +271,135 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
     }
 }
 
+// Forward, warp-decoupled variant (no gains): every warp stages the streamed
+// pixel granules into its own slice of shared memory and synchronises only
+// with itself, so a tile that takes the exact phase path delays its own warp
+// and no CTA barrier couples the 8 warps.  Each warp re-reads the granule
+// data the other warps read (from L1/L2, ~0.4 B per pair).  An autotuner
+// candidate beside the CTA-staged kernel.
+constexpr int NSW = 2;   // granules per warp stage
+
+__global__ void __launch_bounds__(NTHREADS, 2)
+fwd_mixed_wd_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ plp,
+                    double2* __restrict__ partial)
+{
+    __shared__ float4 s_off[BLK_GRAN][NSW][G];
+    __shared__ float4 s_lo[BLK_GRAN][NSW][G];
+    __shared__ float4 s_pg[BLK_GRAN][NSW][G];
+    __shared__ float s_B[BLK_GRAN][NSW][G];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Plan pl = *plp;
+    const long long c = blockIdx.x;
+    long long u, u_end;
+    cta_range(pl, c, u, u_end);
+
+    while (u < u_end) {
+        const int p = find_prob(pl, u);
+        const DevProblem& P = probs[p];
+        const long long loc = u - pl.prob_u0[p];
+        const double* X;
+        if (!fwd_role(P, X)) {
+            u = min(u_end, pl.prob_u0[p + 1]);
+            continue;
+        }
+        const int upb = P.pix.n_gran;
+        const int blk = (int)(loc / upb);
+        const int g0 = (int)(loc % upb);
+        const int g1 = (int)min((long long)upb, (long long)g0 + (u_end - u));
+        u += g1 - g0;
+        const int vg = blk * BLK_GRAN + warp;
+        if (vg >= P.vis.n_gran) continue;               // this warp owns nothing in this block
+        const int e0 = vg * G + lane;
+        const float4 ch = P.vis.cen_hi[vg], cl = P.vis.cen_lo[vg], ext = P.vis.ext[vg];
+        float4 xh[2], dx[2];
+        const int2 ant[2] = {make_int2(0, 0), make_int2(0, 0)};
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            xh[r] = P.vis.hi[e0 + 32 * r];
+            dx[r] = P.vis.off[e0 + 32 * r];
+        }
+        double tr[2] = {0.0, 0.0}, ti[2] = {0.0, 0.0};
+        for (int gs = g0; gs < g1; gs += NSW) {
+            const int ns = min(NSW, g1 - gs);
+            __syncwarp();                               // this warp's previous stage consumed
+            for (int q = 0; q < ns; ++q) {
+                const int g = gs + q;
+                const bool gauss = P.gkind[g] != DIRAC;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int i = lane + 32 * h;
+                    const int e = g * G + i;
+                    float4 o = P.pix.off[e];
+                    o.w = (float)(X[e] * P.pix.d[e].w);
+                    s_off[warp][q][i] = o;
+                    const float4 lo = P.pix.offlo[e];
+                    s_lo[warp][q][i] = lo;
+                    if (gauss) s_pg[warp][q][i] = P.pgauss[e];
+                    s_B[warp][q][i] = frac_dot3(ch, cl, o, lo);
+                }
+            }
+            __syncwarp();
+            for (int q = 0; q < ns; ++q) {
+                const int g = gs + q;
+                const int kind = P.gkind[g];
+                const float4 yc_h = P.pix.cen_hi[g], yc_l = P.pix.cen_lo[g];
+                const bool exact = dot3(ext, P.pix.ext[g]) > D_MAX;
+                float C[2];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) C[r] = frac_dot3(xh[r], P.vis.lo[e0 + 32 * r], yc_h, yc_l);
+                float sr[2] = {0.f, 0.f}, si[2] = {0.f, 0.f};
+                if (kind == DIRAC) {
+                    if (exact) {
+                        const float4 dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
+                        fwd_dirac_tile<false, true>(s_off[warp][q], s_lo[warp][q], s_B[warp][q], nullptr, 0, dx, dxl,
+                                                    ant, sr, si);
+                    } else {
+                        fwd_dirac_tile<false, false>(s_off[warp][q], s_lo[warp][q], s_B[warp][q], nullptr, 0, dx, dx,
+                                                     ant, sr, si);
+                    }
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        float sn, cs;
+                        __sincosf(C[r] * TWO_PI_F, &sn, &cs);
+                        tr[r] += (double)fmaf(cs, sr[r], sn * si[r]);
+                        ti[r] += (double)fmaf(cs, si[r], -sn * sr[r]);
+                    }
+                } else {
+                    const bool par = (kind == PARAXIAL);
+                    GaussConst gc[2];
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        gc[r] = gauss_const(xh[r].x, xh[r].y, xh[r].z, P.gsig[g]);
+                        C[r] = frac_turns(C[r] + gc[r].cphase);
+                    }
+                    if (exact) {
+                        const float4 dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
+                        fwd_gauss_tile<false, true>(s_off[warp][q], s_lo[warp][q], s_pg[warp][q], s_B[warp][q],
+                                                    nullptr, 0, par, xh, dx, dxl, gc, ant, sr, si);
+                    } else {
+                        fwd_gauss_tile<false, false>(s_off[warp][q], s_lo[warp][q], s_pg[warp][q], s_B[warp][q],
+                                                     nullptr, 0, par, xh, dx, dx, gc, ant, sr, si);
+                    }
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        const float ar = gc[r].id * fmaf(-gc[r].beta, si[r], sr[r]);
+                        const float ai = gc[r].id * fmaf(gc[r].beta, sr[r], si[r]);
+                        float sn, cs;
+                        __sincosf(C[r] * TWO_PI_F, &sn, &cs);
+                        tr[r] += (double)fmaf(cs, ar, sn * ai);
+                        ti[r] += (double)fmaf(cs, ai, -sn * ar);
+                    }
+                }
+            }
+        }
+        const int gb = pl.prob_b0[p] + blk;
+        double2* dst = partial + (size_t)slot_of(pl, gb) * BLK + warp * G + lane;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) dst[32 * r] = make_double2(tr[r], ti[r]);
+    }
+}
+
 // ----------------------------------------------------------- adjoint tiles
 
 // Gain of owned pixel r (0/1 of this lane) at antenna a.
@@ -674,6 +803,8 @@ cudaError_t launch_forward_mixed(bool gains, int n_ant, int nst, const DevProble
         // the dynamic shared-memory limit was raised by occupancy_mixed()
         // when the batch was built (not here: this may run under capture)
         fwd_mixed_kernel<true, 1><<<C, NTHREADS, fwd_smem_bytes(n_ant, true), st>>>(probs, plp, partial);
+    } else if (nst == 0) {
+        fwd_mixed_wd_kernel<<<C, NTHREADS, 0, st>>>(probs, plp, partial);
     } else if (nst <= 2) {
         fwd_mixed_kernel<false, 2><<<C, NTHREADS, 0, st>>>(probs, plp, partial);
     } else if (nst <= 4) {
@@ -706,6 +837,7 @@ int occupancy_mixed(int op, bool gains, int n_ant, int nst)
             }
             return occ_of(fwd_mixed_kernel<true, 1>, sm);
         }
+        if (nst == 0) return occ_of(fwd_mixed_wd_kernel, 0);
         if (nst <= 2) return occ_of(fwd_mixed_kernel<false, 2>, 0);
         if (nst <= 4) return occ_of(fwd_mixed_kernel<false, 4>, 0);
         return occ_of(fwd_mixed_kernel<false, 8>, 0);

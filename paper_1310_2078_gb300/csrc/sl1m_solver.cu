@@ -184,6 +184,7 @@ __device__ __forceinline__ int adj_finish_mode(const DevProblem& P)
 //   FIN_SOLVE : AI_k = A I_k, block sum W|A I_k - V|^2,
 //               A y_{k+1} = AI_k + beta_k (AI_k - AI_{k-1})  (linearity),
 //               r = W (A y_{k+1} - V)
+//               (MFISTA: A z_k and its block sum only)
 __global__ void __launch_bounds__(256)
 fwd_finish_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ plp,
                   const double2* __restrict__ partial)
@@ -199,12 +200,13 @@ fwd_finish_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__
         const int blk = gb - pl.prob_b0[p];
         const int poff = pl.blk_poff[gb], ncon = pl.blk_ncon[gb];
         double beta = 0.0;
-        int par = 0;
+        int par = 0, mf = 0;
         if (mode == FIN_SOLVE) {
             const SolveState& S = *P.st;
             double tn;
             fista_beta(S.t, tn, beta);
             par = (S.k + 1) & 1;
+            mf = S.algo;
         }
         double bn = 0.0;
         int bad = 0;
@@ -235,6 +237,8 @@ fwd_finish_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__
             if (mode == FIN_INIT) {
                 B.AI[0][e] = s;
                 B.r[e] = make_double2(W * dr, W * di);
+            } else if (mf) {
+                B.AI[1][e] = s;                 // A z_k; r is formed by the mix kernel
             } else {
                 const double2 old = B.AI[par ^ 1][e];
                 B.AI[par][e] = s;
@@ -259,6 +263,7 @@ fwd_finish_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__
 //   FIN_SOLVE : I_k = T^{lambda/L}(y_k - g/L)                 (Eq. threshp)
 //               y_{k+1} = I_k + beta_k (I_k - I_{k-1})        (FISTA box)
 //               block sums of I_k and of nnz
+//               (MFISTA: z_k = T^{lambda/L}(y_k - g/L) and its sums only)
 __global__ void __launch_bounds__(256)
 adj_finish_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ plp,
                   const double* __restrict__ partial)
@@ -274,7 +279,7 @@ adj_finish_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__
         const int blk = gb - pl.prob_b0[p];
         const int poff = pl.blk_poff[gb], ncon = pl.blk_ncon[gb];
         double inv_L = 0.0, thr = 0.0, beta = 0.0, scale = 1.0;
-        int par = 0;
+        int par = 0, mf = 0;
         if (mode == FIN_SOLVE) {
             const SolveState& S = *P.st;
             double tn;
@@ -282,6 +287,7 @@ adj_finish_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__
             inv_L = 1.0 / S.L;
             thr = S.lambda / S.L;
             par = (S.k + 1) & 1;
+            mf = S.algo;
         } else if (mode == FIN_POWER) {
             scale = P.st->inv_mu;
         }
@@ -309,9 +315,13 @@ adj_finish_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__
             const double v = B.y[e] - s * inv_L;
             double In = v > thr ? v - thr : 0.0;
             if (P.pix.orig[e] < 0) In = 0.0;
-            const double Io = B.I[par ^ 1][e];
-            B.I[par][e] = In;
-            B.y[e] = In + beta * (In - Io);
+            if (mf) {
+                B.I[1][e] = In;                 // z_k; y is formed by the mix kernel
+            } else {
+                const double Io = B.I[par ^ 1][e];
+                B.I[par][e] = In;
+                B.y[e] = In + beta * (In - Io);
+            }
             acc += In;
             cnt += In > 0.0;
         }
@@ -360,6 +370,8 @@ __global__ void scalars_kernel(const DevProblem* __restrict__ probs, const int* 
         const SolveBufs& B = P.b;
         const int nvb = P.vis.n_blk, npb = P.pix.n_blk;
         const int ph = S.phase;
+        // the mix kernel of the previous tick has run (stream order)
+        if (threadIdx.x == 0) S.mix_pending = 0;
         if (ph == PH_PINIT) {
             if (threadIdx.x == 0) S.phase = PH_POWER;
         } else if (ph == PH_POWER) {
@@ -401,7 +413,41 @@ __global__ void scalars_kernel(const DevProblem* __restrict__ probs, const int* 
             const double l1 = warp_sum_fixed(B.blk_l1, npb);
             const long long nnz = warp_sum_fixed_i(B.blk_nnz, npb);
             const long long bad = warp_sum_fixed_i(B.blk_badv, nvb) + warp_sum_fixed_i(B.blk_badp, npb);
-            if (threadIdx.x == 0) {
+            if (threadIdx.x == 0 && S.algo) {
+                // MFISTA: keep the better of z_k and x_{k-1}; then
+                // y_{k+1} = x_k + (t_k/t_{k+1})(z_k - x_k) + ((t_k-1)/t_{k+1})(x_k - x_{k-1})
+                //         = x_{k-1} + c (z_k - x_{k-1}), c = 1 + (t_k-1)/t_{k+1} when z_k
+                // is kept, t_k/t_{k+1} when it is not (formed by the mix kernel).
+                double tn, beta;
+                fista_beta(S.t, tn, beta);
+                const double Fz = 0.5 * r2 + S.lambda * l1;
+                const double Fx = S.E_prev;
+                const int take = Fz <= Fx;
+                S.take = take;
+                S.cmix = take ? 1.0 + beta : S.t / tn;
+                S.mix_pending = 1;
+                S.k += 1;
+                S.t = tn;
+                S.beta = beta;
+                if (take) {
+                    S.resid2 = r2;
+                    S.l1 = l1;
+                    S.nnz = nnz;
+                    S.E = Fz;
+                }
+                bool done = false;
+                if (bad || !isfinite(Fz)) {
+                    S.nonfinite = 1;
+                    done = true;
+                }
+                if (S.tol > 0.0 && fabs(Fz - Fx) <= S.tol * Fx) {
+                    S.converged = 1;
+                    done = true;
+                }
+                if (S.k >= S.max_iter) done = true;
+                S.E_prev = S.E;
+                if (done) S.phase = PH_DONE;
+            } else if (threadIdx.x == 0) {
                 double tn, beta;
                 fista_beta(S.t, tn, beta);
                 const double E = 0.5 * r2 + S.lambda * l1;
@@ -429,6 +475,48 @@ __global__ void scalars_kernel(const DevProblem* __restrict__ probs, const int* 
     }
 }
 
+// ------------------------------------------------------------ MFISTA mix
+// Finishes an MFISTA step once the scalars kernel has compared F(z_k) with
+// F(x_{k-1}): grid-stride over the visibility blocks of the forward plan and
+// then the pixel blocks of the adjoint plan,
+//   visibilities: A y_{k+1} = A x_{k-1} + c (A z_k - A x_{k-1})   (linearity)
+//                 r = W (A y_{k+1} - V);  A x_k = A z_k if z_k was kept
+//   pixels:       y_{k+1} = x_{k-1} + c (z_k - x_{k-1});  x_k = z_k if kept
+__global__ void __launch_bounds__(256)
+mfista_mix_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ fplp,
+                  const Plan* __restrict__ aplp)
+{
+    const Plan fp = *fplp, ap = *aplp;
+    for (int gb = blockIdx.x; gb < fp.n_blocks + ap.n_blocks; gb += gridDim.x) {
+        const bool vis = gb < fp.n_blocks;
+        const Plan& pl = vis ? fp : ap;
+        const int g = vis ? gb : gb - fp.n_blocks;
+        const int p = find_blk_prob(pl, g);
+        const DevProblem& P = probs[p];
+        if (!P.st || !P.st->algo || !P.st->mix_pending) continue;
+        const double c = P.st->cmix;
+        const int take = P.st->take;
+        const int blk = g - pl.prob_b0[p];
+        const SolveBufs& B = P.b;
+        for (int h = 0; h < 2; ++h) {
+            const int e = blk * BLK + threadIdx.x + 256 * h;
+            if (vis) {
+                if (e >= P.vis.n_pad) continue;
+                const double2 ax = B.AI[0][e], az = B.AI[1][e], V = P.V[e];
+                const double W = P.vis.d[e].w;
+                const double ayr = ax.x + c * (az.x - ax.x), ayi = ax.y + c * (az.y - ax.y);
+                B.r[e] = make_double2(W * (ayr - V.x), W * (ayi - V.y));
+                if (take) B.AI[0][e] = az;
+            } else {
+                if (e >= P.pix.n_pad) continue;
+                const double x = B.I[0][e], z = B.I[1][e];
+                B.y[e] = x + c * (z - x);
+                if (take) B.I[0][e] = z;
+            }
+        }
+    }
+}
+
 // Phase of every problem of a batch, for the host (one int per problem).
 __global__ void phases_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ n_probs,
                               int* __restrict__ out)
@@ -449,6 +537,13 @@ cudaError_t launch_adj_finish(const DevProblem* probs, const Plan* plp, int grid
                               cudaStream_t st)
 {
     adj_finish_kernel<<<grid, 256, 0, st>>>(probs, plp, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mfista_mix(const DevProblem* probs, const Plan* fplp, const Plan* aplp, int grid,
+                              cudaStream_t st)
+{
+    mfista_mix_kernel<<<grid, 256, 0, st>>>(probs, fplp, aplp);
     return cudaGetLastError();
 }
 

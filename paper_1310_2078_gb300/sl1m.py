@@ -22,6 +22,8 @@ LIB_PATH = os.path.join(HERE, "libsl1m.so")
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_BUSY, ERR_STATE = range(8)
 FP64, MIXED = 0, 1
+FISTA, MFISTA = 0, 1
+_ALGOS = {"fista": FISTA, "mfista": MFISTA, FISTA: FISTA, MFISTA: MFISTA}
 DIRAC, GAUSS_PARAXIAL, GAUSS_WIDE = 0, 1, 2
 KERNEL_IDS = {"fwd_fp64": 0, "adj_fp64": 1, "fwd_mixed": 2, "adj_mixed": 3,
               "fwd_finish": 4, "adj_finish": 5, "other": 6}
@@ -43,7 +45,7 @@ class SolveOpts(C.Structure):
     _fields_ = [("lambda_", C.c_double), ("L", C.c_double), ("rel_tol", C.c_double),
                 ("max_iter", C.c_int32), ("precision", C.c_int32),
                 ("power_max_iter", C.c_int32), ("power_tol", C.c_double),
-                ("x0", C.c_void_p)]
+                ("x0", C.c_void_p), ("algorithm", C.c_int32)]
 
 
 class ServerOpts(C.Structure):
@@ -273,10 +275,10 @@ class Context:
         self.check(self.lib.sl1m_server_start(self.h, C.byref(o)))
 
     def server_submit(self, problem, lam, L=0.0, max_iter=200, rel_tol=0.0, x0=None,
-                      power_max_iter=0, power_tol=0.0):
+                      power_max_iter=0, power_tol=0.0, algorithm="fista"):
         x0a = _f64(x0)
         o = SolveOpts(float(lam), float(L), float(rel_tol), int(max_iter), MIXED,
-                      int(power_max_iter), float(power_tol), _ptr(x0a))
+                      int(power_max_iter), float(power_tol), _ptr(x0a), _ALGOS[algorithm])
         t = C.c_uint64()
         self.check(self.lib.sl1m_server_submit(self.h, problem.h, C.byref(o), C.byref(t)))
         return t.value
@@ -390,10 +392,10 @@ class Problem:
         return L.value, it.value
 
     def solve(self, lam, L=0.0, max_iter=200, rel_tol=0.0, precision=MIXED, x0=None,
-              power_max_iter=0, power_tol=0.0):
+              power_max_iter=0, power_tol=0.0, algorithm="fista"):
         x0a = _f64(x0)
         o = SolveOpts(float(lam), float(L), float(rel_tol), int(max_iter), int(precision),
-                      int(power_max_iter), float(power_tol), _ptr(x0a))
+                      int(power_max_iter), float(power_tol), _ptr(x0a), _ALGOS[algorithm])
         img = np.zeros(self.n_pix)
         st = SolveStats()
         self.ctx.check(self.lib.sl1m_solve(self.h, C.byref(o), _ptr(img), C.byref(st)))
@@ -409,7 +411,8 @@ class Problem:
     def solve_refine(self, lam, delta0, levels, refine_frac=0.01, keep_unrefined=True, L=0.0,
                      max_iter=200, rel_tol=0.0, precision=MIXED):
         """sl1m_solve_refine: returns (lm [n,2], image [n], stats)."""
-        o = SolveOpts(float(lam), float(L), float(rel_tol), int(max_iter), int(precision), 0, 0.0, None)
+        o = SolveOpts(float(lam), float(L), float(rel_tol), int(max_iter), int(precision), 0, 0.0, None,
+                      FISTA)
         ro = RefineOpts(int(levels), float(refine_frac), int(bool(keep_unrefined)))
         st = RefineStats()
         self.ctx.check(self.lib.sl1m_solve_refine(self.h, C.byref(o), C.byref(ro), float(delta0), C.byref(st)))
