@@ -167,14 +167,24 @@ def ncu_traffic(kernel, nst, ctas, workload):
     return None
 
 
-def cpu_baseline(w, budget_s: float = 12.0):
-    """The FP64 oracle as it stands, single-threaded, on a bounded sample of
-    the same workload: forward rows and adjoint columns; pairs/s."""
-    import oracle
-    O = oracle.Problem(w.uvw, w.lm, w.sigma, w.kind, w.weights, w.ant_pair, w.gains)
+def baseline_inputs(w):
+    """The seeded x [n_pix] and r [n_vis] the CPU-baseline sample runs on."""
     rng = np.random.default_rng(0)
     x = np.abs(rng.normal(size=w.n_pix))
     r = rng.normal(size=w.n_vis) + 1j * rng.normal(size=w.n_vis)
+    return x, r
+
+
+def cpu_baseline(w, gpu_fwd=None, gpu_adj=None, budget_s: float = 12.0):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample of
+    the same workload: forward rows and adjoint columns; pairs/s.  Given the
+    library's forward A x and adjoint Re A^H r of the same inputs, the sampled
+    oracle outputs also give their error (max |diff| / max |oracle| over the
+    sample)."""
+    import oracle
+    O = oracle.Problem(w.uvw, w.lm, w.sigma, w.kind, w.weights, w.ant_pair, w.gains)
+    rng = np.random.default_rng(0)
+    x, r = baseline_inputs(w)
     # calibrate: 8 rows
     t0 = time.perf_counter()
     oracle.forward(O, x, rows=np.arange(8))
@@ -184,13 +194,19 @@ def cpu_baseline(w, budget_s: float = 12.0):
     rows = rng.choice(w.n_vis, min(n_rows, w.n_vis), replace=False)
     cols = rng.choice(w.n_pix, min(n_cols, w.n_pix), replace=False)
     t0 = time.perf_counter()
-    oracle.forward(O, x, rows=rows)
-    oracle.adjoint(O, r, cols=cols)
+    fo = oracle.forward(O, x, rows=rows)
+    ao = oracle.adjoint(O, r, cols=cols)
     dt = time.perf_counter() - t0
     pairs = len(rows) * w.n_pix + len(cols) * w.n_vis
-    return {"value": pairs / dt, "unit": "pairs/s", "cores": 1, "kind": "oracle",
-            "sample": f"{len(rows)} forward rows x {w.n_pix} px + {len(cols)} adjoint "
-                      f"columns x {w.n_vis} vis of {w.name}, FP64, single thread, {dt:.1f} s"}
+    out = {"value": pairs / dt, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+           "sample": f"{len(rows)} forward rows x {w.n_pix} px + {len(cols)} adjoint "
+                     f"columns x {w.n_vis} vis of {w.name}, FP64, single thread, {dt:.1f} s"}
+    if gpu_fwd is not None and gpu_adj is not None:
+        out["gpu_error_vs_oracle"] = {
+            "forward": float(np.max(np.abs(gpu_fwd[rows] - fo)) / np.max(np.abs(fo))),
+            "adjoint": float(np.max(np.abs(gpu_adj[cols] - ao)) / np.max(np.abs(ao))),
+            "measure": "max |gpu - oracle| / max |oracle| over the sampled rows / columns"}
+    return out
 
 
 def run_reference(args):
@@ -281,7 +297,10 @@ def run_serve(args):
     pairs = sum((2 * st["power_iters"] + 2 * st["iters"] + 2) * float(w.n_vis) * w.n_pix
                 for (_, st), w in zip(results, reqs))
     # FP64 plain single-solve path on the smallest requests (serial, same iterations)
-    order = np.argsort([w.pairs for w in reqs])[:args.fp64_sample]
+    # FP64 sample: requests spread over the lower half of the work distribution
+    by_work = np.argsort([w.pairs for w in reqs])
+    ranks = np.unique(np.linspace(0, len(reqs) // 2, max(1, args.fp64_sample)).astype(int))
+    order = by_work[ranks]
     cmp = []
     for i in order:
         P, V = probs[i]
@@ -297,6 +316,15 @@ def run_serve(args):
                     "E_rel_diff": abs(stm["E"] - st64["E"]) / st64["E"],
                     "img_err_of_peak": float(np.max(np.abs(imgm - img64)) / max(img64.max(), 1e-300))})
     fp64_solves_per_s = len(cmp) / sum(c["fp64_s"] for c in cmp) if cmp else None
+    # the FP64 plain path solving every request serially: its pair rate on the
+    # sample (same iterations, L given) applied to the whole stream's pairs
+    fp64_pairs = sum((2 * c["iters"] + 2) * float(c["n_vis"]) * c["n_pix"] for c in cmp)
+    fp64_rate = fp64_pairs / sum(c["fp64_s"] for c in cmp) if cmp else None
+    fp64_serial = ({"pairs_per_s": fp64_rate, "est_wall_s": pairs / fp64_rate,
+                    "est_solves_per_s": args.requests / (pairs / fp64_rate),
+                    "method": "FP64 single solves, pair rate measured on the sample, "
+                              "applied to all requests' pairs (serial, no overlap)"}
+                   if fp64_rate else None)
     out = {"metric": "solves/s (continuous batching, mixed precision)", "value": args.requests / T,
            "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32+f64",
            "data": "synthetic",
@@ -310,7 +338,8 @@ def run_serve(args):
            "pairs_per_s": pairs / T, "wall_s": T,
            "iters_mean": float(np.mean([st["iters"] for _, st in results])),
            "server": info, "clocks": clk, "gpu_launches": ctx.counters()["launches"],
-           "fp64_plain_single_solve": {"sample": cmp, "solves_per_s_on_sample": fp64_solves_per_s}}
+           "fp64_plain_single_solve": {"sample": cmp, "solves_per_s_on_sample": fp64_solves_per_s,
+                                       "serial_whole_stream": fp64_serial}}
     print(json.dumps(out))
     ctx.close()
 
@@ -428,7 +457,8 @@ def main():
         e2e = run_e2e(ctx, w, V, lam, prec, args, sl1m, stream)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = cpu_baseline(w)
+        xb, rb = baseline_inputs(w)
+        cpu = cpu_baseline(w, P.forward(xb, prec), P.adjoint(rb, prec))
     if rank == 0:
         out = {"metric": "pixel-visibility pairs/s (fwd+adj)", "value": value, "unit": "pairs/s",
                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,

@@ -5,7 +5,20 @@
 namespace sl1m {
 
 #define TWO_PI_F 6.283185307179586f
+#define INV_TWO_PI_F 0.15915494309189535f
 #define LOG2E_F 1.4426950408889634f
+
+// {u, v, w, 2 pi w}: a visibility's coordinates with w also in radians.
+__device__ __forceinline__ float4 to_w2pi(const float4 a)
+{
+    return make_float4(a.x, a.y, a.z, a.z * TWO_PI_F);
+}
+
+// The x, y, z of an offset in radians per turn (w unchanged).
+__device__ __forceinline__ float4 to_rad(const float4 a)
+{
+    return make_float4(a.x * TWO_PI_F, a.y * TWO_PI_F, a.z * TWO_PI_F, a.w);
+}
 
 // x - rint(x) for |x| < 2^22, exact: adding and removing 1.5 * 2^23 rounds x
 // to the nearest integer (ties to even) on the FP32 add pipe.
@@ -65,8 +78,8 @@ __device__ __forceinline__ int slot_of(const Plan& pl, int gblk)
 
 // Constants of one (visibility, Gaussian scale) pair, Eq. samlm4 in split form.
 struct GaussConst {
-    float beta, id, gam, coef;   // beta = w s^2, id = 1/(1+beta^2), gam = beta^2 id,
-                                 // coef = -pi s^2 id log2(e)
+    float beta, id, gamr, coef;  // beta = w s^2, id = 1/(1+beta^2), gamr = 2 pi beta^2 id
+                                 // (radians per turn of t), coef = -pi s^2 id log2(e)
     float cphase;                // id beta s^2 (u^2+v^2)/2, turns
 };
 
@@ -76,7 +89,7 @@ __device__ __forceinline__ GaussConst gauss_const(float u, float v, float w, flo
     const float s2 = sigma * sigma;
     g.beta = w * s2;
     g.id = 1.0f / fmaf(g.beta, g.beta, 1.0f);
-    g.gam = g.beta * g.beta * g.id;
+    g.gamr = g.beta * g.beta * g.id * TWO_PI_F;
     g.coef = -3.14159265358979f * s2 * g.id * LOG2E_F;
     g.cphase = 0.5f * g.id * g.beta * s2 * fmaf(u, u, v * v);
     return g;

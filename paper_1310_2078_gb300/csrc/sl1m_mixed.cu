@@ -18,8 +18,12 @@
 // exactly.  C (per owned element and streamed granule) and B (per owned
 // granule and streamed element) are reduced to fractional turns by an FP32
 // TwoProduct; D is one FP32 fma chain when the tile's offset extents bound
-// |D| <= D_MAX turns, else it is reduced exactly too.  sincos / exp2 run on
-// the SFU in FP32; each granule's FP32 sum is added into FP64 accumulators.
+// |D| <= D_MAX turns, else it is reduced exactly too.  On the first (common)
+// path B and the owned offsets are held in radians (pre-multiplied by 2 pi),
+// so B + D, at most 2 pi (1 + D_MAX) in size, goes to the SFU's sincos with
+// no reduction step of its own; on the exact path the fractional turns are
+// reduced exactly and then scaled.  sincos / exp2 run on the SFU in FP32;
+// each granule's FP32 sum is added into FP64 accumulators.
 //
 // Work split: a CTA owns BLK_GRAN granules of one side (one per warp, 2
 // elements per lane) and streams granules of the other side through shared
@@ -45,16 +49,15 @@ __device__ __forceinline__ void fwd_dirac_tile(const float4* __restrict__ s_off,
 #pragma unroll 4
     for (int j = 0; j < G; ++j) {
         const float4 o = s_off[j];             // {dl, dm, dn, a = x/n}
-        const float b = sB[j];
+        const float b = sB[j];                 // B_j in radians
         const float4 ol = EXACT ? s_lo[j] : o;
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
-            float ph;
-            if (EXACT) ph = b + frac_dot3(dx[r], dxl[r], o, ol);
-            else ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, b)));
-            ph = frac_turns(ph);
+            float ph;                          // radians
+            if (EXACT) ph = frac_turns(fmaf(b, INV_TWO_PI_F, frac_dot3(dx[r], dxl[r], o, ol))) * TWO_PI_F;
+            else ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, b)));   // dx in radians
             float sn, cs;
-            __sincosf(ph * TWO_PI_F, &sn, &cs);
+            __sincosf(ph, &sn, &cs);
             if (GAINS) {
                 const float2 ga = s_gain[j * n_ant + ant[r].x];
                 const float2 gb = s_gain[j * n_ant + ant[r].y];
@@ -89,15 +92,20 @@ __device__ __forceinline__ void fwd_gauss_tile(const float4* __restrict__ s_off,
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             const float uf = xh[r].x, vf = xh[r].y, wf = xh[r].z;
-            float ph;
-            if (EXACT) ph = b + frac_dot3(dx[r], dxl[r], o, ol);
-            else ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, b)));
             const float t = fmaf(uf, pg.x, fmaf(vf, pg.y, -wf * pg.z));
-            ph = fmaf(-gc[r].gam, t, ph);
-            if (par) ph = fmaf(-wf, pg.w, ph);
-            ph = frac_turns(ph);
+            float ph;                          // radians
+            if (EXACT) {
+                ph = fmaf(b, INV_TWO_PI_F, frac_dot3(dx[r], dxl[r], o, ol));
+                ph = fmaf(-gc[r].gamr * INV_TWO_PI_F, t, ph);
+                if (par) ph = fmaf(-wf, pg.w, ph);
+                ph = frac_turns(ph) * TWO_PI_F;
+            } else {
+                ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, b)));
+                ph = fmaf(-gc[r].gamr, t, ph);
+                if (par) ph = fmaf(-wf * TWO_PI_F, pg.w, ph);
+            }
             float sn, cs;
-            __sincosf(ph * TWO_PI_F, &sn, &cs);
+            __sincosf(ph, &sn, &cs);
             const float e1 = fmaf(-wf, pg.x, uf), e2 = fmaf(-wf, pg.y, vf);
             const float amp = o.w * ex2_approx(gc[r].coef * fmaf(e1, e1, e2 * e2));
             if (GAINS) {
@@ -126,7 +134,7 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
     __shared__ float4 s_off[NST][G];       // {dl, dm, dn, a = x/n}
     __shared__ float4 s_lo[NST][G];        // offset residuals
     __shared__ float4 s_pg[NST][G];        // {l, m, r^2/2, nu}
-    __shared__ float s_B[BLK_GRAN][NST][G];
+    __shared__ float s_B[BLK_GRAN][NST][G];   // B_j in radians
     __shared__ float4 s_cen[NST][3];       // centre hi, lo, extent
     __shared__ int s_kind[NST];
     __shared__ float s_sig[NST];
@@ -167,7 +175,7 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 xh[r] = P.vis.hi[e0 + 32 * r];
-                dx[r] = P.vis.off[e0 + 32 * r];
+                dx[r] = to_rad(P.vis.off[e0 + 32 * r]);
                 if (GAINS) ant[r] = P.ant[e0 + 32 * r];
             }
         }
@@ -204,7 +212,7 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int j = lane + 32 * h;
-                    s_B[warp][q][j] = frac_dot3(ch, cl, s_off[q][j], s_lo[q][j]);
+                    s_B[warp][q][j] = frac_dot3(ch, cl, s_off[q][j], s_lo[q][j]) * TWO_PI_F;
                 }
             }
             __syncwarp();
@@ -218,8 +226,8 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                 float sr[2] = {0.f, 0.f}, si[2] = {0.f, 0.f};
                 if (kind == DIRAC) {
                     if (exact) {
-                        const float4 dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
-                        fwd_dirac_tile<GAINS, true>(s_off[q], s_lo[q], s_B[warp][q], s_gain, n_ant, dx, dxl, ant,
+                        const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]}, dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
+                        fwd_dirac_tile<GAINS, true>(s_off[q], s_lo[q], s_B[warp][q], s_gain, n_ant, dxt, dxl, ant,
                                                     sr, si);
                     } else {
                         fwd_dirac_tile<GAINS, false>(s_off[q], s_lo[q], s_B[warp][q], s_gain, n_ant, dx, dx, ant,
@@ -241,9 +249,9 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                         C[r] = frac_turns(C[r] + gc[r].cphase);
                     }
                     if (exact) {
-                        const float4 dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
+                        const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]}, dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
                         fwd_gauss_tile<GAINS, true>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], s_gain, n_ant, par, xh,
-                                                    dx, dxl, gc, ant, sr, si);
+                                                    dxt, dxl, gc, ant, sr, si);
                     } else {
                         fwd_gauss_tile<GAINS, false>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], s_gain, n_ant, par,
                                                      xh, dx, dx, gc, ant, sr, si);
@@ -317,7 +325,7 @@ fwd_mixed_wd_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             xh[r] = P.vis.hi[e0 + 32 * r];
-            dx[r] = P.vis.off[e0 + 32 * r];
+            dx[r] = to_rad(P.vis.off[e0 + 32 * r]);
         }
         double tr[2] = {0.0, 0.0}, ti[2] = {0.0, 0.0};
         for (int gs = g0; gs < g1; gs += NSW) {
@@ -336,7 +344,7 @@ fwd_mixed_wd_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict
                     const float4 lo = P.pix.offlo[e];
                     s_lo[warp][q][i] = lo;
                     if (gauss) s_pg[warp][q][i] = P.pgauss[e];
-                    s_B[warp][q][i] = frac_dot3(ch, cl, o, lo);
+                    s_B[warp][q][i] = frac_dot3(ch, cl, o, lo) * TWO_PI_F;
                 }
             }
             __syncwarp();
@@ -351,8 +359,8 @@ fwd_mixed_wd_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict
                 float sr[2] = {0.f, 0.f}, si[2] = {0.f, 0.f};
                 if (kind == DIRAC) {
                     if (exact) {
-                        const float4 dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
-                        fwd_dirac_tile<false, true>(s_off[warp][q], s_lo[warp][q], s_B[warp][q], nullptr, 0, dx, dxl,
+                        const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]}, dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
+                        fwd_dirac_tile<false, true>(s_off[warp][q], s_lo[warp][q], s_B[warp][q], nullptr, 0, dxt, dxl,
                                                     ant, sr, si);
                     } else {
                         fwd_dirac_tile<false, false>(s_off[warp][q], s_lo[warp][q], s_B[warp][q], nullptr, 0, dx, dx,
@@ -374,9 +382,9 @@ fwd_mixed_wd_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict
                         C[r] = frac_turns(C[r] + gc[r].cphase);
                     }
                     if (exact) {
-                        const float4 dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
+                        const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]}, dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
                         fwd_gauss_tile<false, true>(s_off[warp][q], s_lo[warp][q], s_pg[warp][q], s_B[warp][q],
-                                                    nullptr, 0, par, xh, dx, dxl, gc, ant, sr, si);
+                                                    nullptr, 0, par, xh, dxt, dxl, gc, ant, sr, si);
                     } else {
                         fwd_gauss_tile<false, false>(s_off[warp][q], s_lo[warp][q], s_pg[warp][q], s_B[warp][q],
                                                      nullptr, 0, par, xh, dx, dx, gc, ant, sr, si);
@@ -431,12 +439,11 @@ __device__ __forceinline__ void adj_dirac_tile(const float4* __restrict__ s_off,
         const float4 ol = EXACT ? s_lo[k] : o;
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
-            float ph;
-            if (EXACT) ph = (C[r] + b) + frac_dot3(dx[r], dxl[r], o, ol);
+            float ph;                                  // radians; C and dx in radians unless EXACT
+            if (EXACT) ph = frac_turns((C[r] + b * INV_TWO_PI_F) + frac_dot3(dx[r], dxl[r], o, ol)) * TWO_PI_F;
             else ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, C[r] + b)));
-            ph = frac_turns(ph);
             float sn, cs;
-            __sincosf(ph * TWO_PI_F, &sn, &cs);           // exp(+2 pi i ph) = cs + i sn
+            __sincosf(ph, &sn, &cs);                      // exp(+i ph) = cs + i sn
             if (GAINS) {
                 const int2 ab = s_ant[k];
                 const float2 ga = gain(ab.x, r);
@@ -467,21 +474,26 @@ __device__ __forceinline__ void adj_gauss_tile(const float4* __restrict__ s_off,
 #pragma unroll 2
     for (int k = 0; k < G; ++k) {
         const float4 o = s_off[k];
-        const float4 va = s_abs[k];            // {u, v, w, -}
-        const float4 gw = s_gw[k];             // {gam, coef, r're, r'im}
+        const float4 va = s_abs[k];            // {u, v, w, 2 pi w}
+        const float4 gw = s_gw[k];             // {gamr, coef, r're, r'im}
         const float b = sB[k];
         const float4 ol = EXACT ? s_lo[k] : o;
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
-            float ph;
-            if (EXACT) ph = (C[r] + b) + frac_dot3(dx[r], dxl[r], o, ol);
-            else ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, C[r] + b)));
             const float t = fmaf(va.x, pgd[r].x, fmaf(va.y, pgd[r].y, -va.z * pgd[r].z));
-            ph = fmaf(-gw.x, t, ph);
-            if (par) ph = fmaf(-va.z, pgd[r].w, ph);
-            ph = frac_turns(ph);
+            float ph;                                  // radians; C and dx in radians unless EXACT
+            if (EXACT) {
+                ph = (C[r] + b * INV_TWO_PI_F) + frac_dot3(dx[r], dxl[r], o, ol);
+                ph = fmaf(-gw.x * INV_TWO_PI_F, t, ph);
+                if (par) ph = fmaf(-va.z, pgd[r].w, ph);
+                ph = frac_turns(ph) * TWO_PI_F;
+            } else {
+                ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, C[r] + b)));
+                ph = fmaf(-gw.x, t, ph);
+                if (par) ph = fmaf(-va.w, pgd[r].w, ph);   // va.w = 2 pi w
+            }
             float sn, cs;
-            __sincosf(ph * TWO_PI_F, &sn, &cs);
+            __sincosf(ph, &sn, &cs);
             const float e1 = fmaf(-va.z, pgd[r].x, va.x), e2 = fmaf(-va.z, pgd[r].y, va.y);
             const float amp = ex2_approx(gw.y * fmaf(e1, e1, e2 * e2));
             const float zr = fmaf(cs, gw.z, -sn * gw.w);
@@ -508,11 +520,11 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
 {
     __shared__ float4 s_off[NSA][G];            // {du, dv, dw, W}
     __shared__ float4 s_lo[NSA][G];
-    __shared__ float4 s_abs[NSA][G];            // {u, v, w, 0} (Gaussian owners)
+    __shared__ float4 s_abs[NSA][G];            // {u, v, w, 2 pi w} (Gaussian owners)
     __shared__ float2 s_r[NSA][G];
     __shared__ int2 s_ant[NSA][G];      // unused without gains
     __shared__ float s_B[BLK_GRAN][NSA][G];
-    __shared__ float4 s_gw[BLK_GRAN][NSA][G];   // Gaussian owners: {gam, coef, r're, r'im}
+    __shared__ float4 s_gw[BLK_GRAN][NSA][G];   // Gaussian owners: {gamr, coef, r're, r'im}
     __shared__ float4 s_cen[NSA][3];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -553,7 +565,7 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 xh[r] = P.pix.hi[eidx[r]];
-                dx[r] = P.pix.off[eidx[r]];
+                dx[r] = to_rad(P.pix.off[eidx[r]]);
                 if (kind != DIRAC) pgd[r] = P.pgauss[eidx[r]];
             }
         }
@@ -569,7 +581,7 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                 const int e = (gs + q) * G + i;
                 s_off[q][i] = P.vis.off[e];
                 s_lo[q][i] = P.vis.offlo[e];
-                s_abs[q][i] = P.vis.hi[e];
+                s_abs[q][i] = to_w2pi(P.vis.hi[e]);
                 const double2 rr = R[e];
                 s_r[q][i] = make_float2((float)rr.x, (float)rr.y);
             }
@@ -591,10 +603,10 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                         b = frac_turns(b + gc.cphase);
                         const float2 rr = s_r[q][k];
                         // r' = id (1 - i beta) r
-                        s_gw[warp][q][k] = make_float4(gc.gam, gc.coef, gc.id * fmaf(gc.beta, rr.y, rr.x),
+                        s_gw[warp][q][k] = make_float4(gc.gamr, gc.coef, gc.id * fmaf(gc.beta, rr.y, rr.x),
                                                        gc.id * fmaf(-gc.beta, rr.x, rr.y));
                     }
-                    s_B[warp][q][k] = b;
+                    s_B[warp][q][k] = b * TWO_PI_F;           // radians
                 }
             }
             __syncwarp();
@@ -604,25 +616,28 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                 float C[2];
 #pragma unroll
                 for (int r = 0; r < 2; ++r) C[r] = frac_dot3(xh[r], P.pix.lo[eidx[r]], yc_h, yc_l);
+                const float Cr[2] = {C[0] * TWO_PI_F, C[1] * TWO_PI_F};
                 float acc[2] = {0.f, 0.f};
                 const NoGain ng;
                 if (!gauss) {
                     if (exact) {
-                        const float4 dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
-                        adj_dirac_tile<false, true>(s_off[q], s_lo[q], s_r[q], s_ant[q], s_B[warp][q], ng, C, dx,
+                        const float4 dxt[2] = {P.pix.off[eidx[0]], P.pix.off[eidx[1]]},
+                                 dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
+                        adj_dirac_tile<false, true>(s_off[q], s_lo[q], s_r[q], s_ant[q], s_B[warp][q], ng, C, dxt,
                                                     dxl, acc);
                     } else {
-                        adj_dirac_tile<false, false>(s_off[q], s_lo[q], s_r[q], s_ant[q], s_B[warp][q], ng, C, dx,
+                        adj_dirac_tile<false, false>(s_off[q], s_lo[q], s_r[q], s_ant[q], s_B[warp][q], ng, Cr, dx,
                                                      dx, acc);
                     }
                 } else {
                     if (exact) {
-                        const float4 dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
+                        const float4 dxt[2] = {P.pix.off[eidx[0]], P.pix.off[eidx[1]]},
+                                 dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
                         adj_gauss_tile<false, true>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[warp][q],
-                                                    s_gw[warp][q], ng, par, C, dx, dxl, pgd, acc);
+                                                    s_gw[warp][q], ng, par, C, dxt, dxl, pgd, acc);
                     } else {
                         adj_gauss_tile<false, false>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[warp][q],
-                                                     s_gw[warp][q], ng, par, C, dx, dx, pgd, acc);
+                                                     s_gw[warp][q], ng, par, Cr, dx, dx, pgd, acc);
                     }
                 }
 #pragma unroll
@@ -700,7 +715,7 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 xh[r] = P.pix.hi[eidx[r]];
-                dx[r] = P.pix.off[eidx[r]];
+                dx[r] = to_rad(P.pix.off[eidx[r]]);
                 if (gauss) pgd[r] = P.pgauss[eidx[r]];
             }
             const SmemGain sg{s_gain, lane};
@@ -713,7 +728,7 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
                     const int e = (gs + q) * G + i;
                     s_off[q][i] = P.vis.off[e];
                     s_lo[q][i] = P.vis.offlo[e];
-                    s_abs[q][i] = P.vis.hi[e];
+                    s_abs[q][i] = to_w2pi(P.vis.hi[e]);
                     const double2 rr = R[e];
                     s_r[q][i] = make_float2((float)rr.x, (float)rr.y);
                     s_ant[q][i] = P.ant[e];
@@ -736,32 +751,35 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
                         const GaussConst gc = gauss_const(va.x, va.y, va.z, sigma);
                         b = frac_turns(b + gc.cphase);
                         const float2 rr = s_r[q][k];
-                        s_gw[q][k] = make_float4(gc.gam, gc.coef, gc.id * fmaf(gc.beta, rr.y, rr.x),
+                        s_gw[q][k] = make_float4(gc.gamr, gc.coef, gc.id * fmaf(gc.beta, rr.y, rr.x),
                                                  gc.id * fmaf(-gc.beta, rr.x, rr.y));
                     }
-                    s_B[q][k] = b;
+                    s_B[q][k] = b * TWO_PI_F;                 // radians
                 }
                 __syncwarp();
                 const bool exact = dot3(ext, s_cen[q][2]) > D_MAX;
                 float C[2];
 #pragma unroll
                 for (int r = 0; r < 2; ++r) C[r] = frac_dot3(xh[r], P.pix.lo[eidx[r]], s_cen[q][0], s_cen[q][1]);
+                const float Cr[2] = {C[0] * TWO_PI_F, C[1] * TWO_PI_F};
                 float acc[2] = {0.f, 0.f};
                 if (!gauss) {
                     if (exact) {
-                        const float4 dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
-                        adj_dirac_tile<true, true>(s_off[q], s_lo[q], s_r[q], s_ant[q], s_B[q], sg, C, dx, dxl, acc);
+                        const float4 dxt[2] = {P.pix.off[eidx[0]], P.pix.off[eidx[1]]},
+                                 dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
+                        adj_dirac_tile<true, true>(s_off[q], s_lo[q], s_r[q], s_ant[q], s_B[q], sg, C, dxt, dxl, acc);
                     } else {
-                        adj_dirac_tile<true, false>(s_off[q], s_lo[q], s_r[q], s_ant[q], s_B[q], sg, C, dx, dx, acc);
+                        adj_dirac_tile<true, false>(s_off[q], s_lo[q], s_r[q], s_ant[q], s_B[q], sg, Cr, dx, dx, acc);
                     }
                 } else {
                     if (exact) {
-                        const float4 dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
+                        const float4 dxt[2] = {P.pix.off[eidx[0]], P.pix.off[eidx[1]]},
+                                 dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
                         adj_gauss_tile<true, true>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[q], s_gw[q], sg, par, C,
-                                                   dx, dxl, pgd, acc);
+                                                   dxt, dxl, pgd, acc);
                     } else {
                         adj_gauss_tile<true, false>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[q], s_gw[q], sg, par,
-                                                    C, dx, dx, pgd, acc);
+                                                    Cr, dx, dx, pgd, acc);
                     }
                 }
 #pragma unroll
