@@ -111,7 +111,11 @@ int sl1m_set_pixels(sl1m_problem* prob, int64_t n_pix, const double* lm,
 int sl1m_set_gains(sl1m_problem* prob, int32_t n_ant, const double* G);
 
 /* Forward operator, Eq. sme: vis_out_k = sum_j A_kj x_j.
- * x [n_pix] (host), vis_out [n_vis][2] (host).  Synchronous. */
+ * x [n_pix] (host), vis_out [n_vis][2] (host).  Synchronous.
+ * This and every later operator or solve call lay the problem out first and
+ * return SL1M_ERR_ARG when max|u|*max|l|, max|v|*max|m| or max|w|*max|n-1|
+ * reaches 2^21 turns (about 2e6 wavelengths at |l| = 1): the mixed kernels
+ * split the phase exactly only below that. */
 int sl1m_forward(sl1m_problem* prob, const double* x, double* vis_out, int precision);
 
 /* Adjoint (back-projection of Sect. 3): img_out_j = sum_k Re(conj(A_kj) r_k).
@@ -264,14 +268,25 @@ typedef struct {
 int sl1m_server_info(sl1m_ctx* ctx, sl1m_server_info_t* info);
 
 /* Autotuner of the operator kernels' tile shape: for the forward and the
- * adjoint of this problem it times every candidate -- streamed granules per
- * shared-memory stage (2, 4 or 8; the mixed no-gains kernels) times the
- * persistent grid (1 .. occupancy CTAs per SM) -- with CUDA events and keeps
- * the fastest in the context, keyed by (precision, operator, gains, Gaussian
- * pixels, log2 of the work units).  Later launches of problems with the same
- * key -- single solves and server batches -- use it.  nst_out and
- * ctas_per_sm_out ([2]: forward, adjoint) may be NULL.  Synchronous. */
-int sl1m_autotune(sl1m_problem* prob, int precision, int32_t* nst_out, int32_t* ctas_per_sm_out);
+ * adjoint of this problem it times, with CUDA events, every (streamed
+ * granules per shared-memory stage: 2, 4 or 8, or 0 = the warp-decoupled
+ * forward) x (persistent grid: 1 .. occupancy CTAs per SM) of the mixed
+ * no-gains kernels, then at the fastest of those the share npoly (1 or 2 of
+ * every 8 pairs) whose sincos runs on the FMA pipe instead of the SFU; with
+ * gains or in FP64 only the grid is tuned.  The choice is kept in the context,
+ * keyed by (precision, operator, gains, Gaussian pixels, log2 of the work
+ * units); later launches of problems with the same key -- single solves and
+ * server batches -- use it.  nst_out, ctas_per_sm_out and npoly_out ([2]:
+ * forward, adjoint) may be NULL.  Synchronous. */
+int sl1m_autotune(sl1m_problem* prob, int precision, int32_t* nst_out, int32_t* ctas_per_sm_out,
+                  int32_t* npoly_out);
+
+/* Set the tile shape the autotuner would choose, for this problem's key
+ * (op 0 forward, 1 adjoint): nst 2, 4 or 8 (0: warp-decoupled forward),
+ * ctas_per_sm from 1 to the kernel's occupancy, npoly 0, 1 or 2.  With gains
+ * or in FP64 only ctas_per_sm may differ from the defaults (nst 4, npoly 0).
+ * SL1M_ERR_ARG for a shape that does not exist or does not fit. */
+int sl1m_set_tile_shape(sl1m_problem* prob, int precision, int op, int nst, int ctas_per_sm, int npoly);
 
 /* ---- Adaptive quadtree refinement (Sect. 4.4) ---------------------------
  * The pixels set on the problem (Dirac, a regular grid of spacing delta0, no

@@ -1,6 +1,7 @@
 // sl1m_devfn.cuh -- device helpers shared by the operator kernels (internal).
 #pragma once
 #include "sl1m_dev.h"
+#include "sl1m_sincos_poly.h"
 
 namespace sl1m {
 
@@ -8,10 +9,17 @@ namespace sl1m {
 #define INV_TWO_PI_F 0.15915494309189535f
 #define LOG2E_F 1.4426950408889634f
 
-// {u, v, w, 2 pi w}: a visibility's coordinates with w also in radians.
-__device__ __forceinline__ float4 to_w2pi(const float4 a)
+// {u, v, -2 w, u^2 + v^2}: a streamed visibility as the adjoint's Gaussian
+// terms use it (t = u l + v m + (-2 w) r^2/4, |(u,v) - w (l,m)|^2 = u^2 + v^2 + (-2 w) t).
+__device__ __forceinline__ float4 vis_for_gauss(const float4 a)
 {
-    return make_float4(a.x, a.y, a.z, a.z * TWO_PI_F);
+    return make_float4(a.x, a.y, -2.0f * a.z, fmaf(a.x, a.x, a.y * a.y));
+}
+
+// {l, m, r^2/4, pi nu}: an owned Gaussian pixel as the adjoint uses it.
+__device__ __forceinline__ float4 pix_for_gauss(const float4 a)
+{
+    return make_float4(a.x, a.y, 0.5f * a.z, 3.14159265358979f * a.w);
 }
 
 // The x, y, z of an offset in radians per turn (w unchanged).
@@ -30,11 +38,13 @@ __device__ __forceinline__ float frac_turns(float x)
 
 // frac(a*b) in turns for a = ah + al, b = bh + bl: p + e == ah*bh exactly
 // (TwoProduct with one fma), p - rint(p) is exact, the cross terms are small.
+// The rounding is frac_turns' FP32-add trick, exact for |p| <= 2^22; the
+// host refuses problems whose coordinate products could reach 2^21.
 __device__ __forceinline__ float tp_frac(float ah, float al, float bh, float bl)
 {
     const float p = __fmul_rn(ah, bh);
     const float e = __fmaf_rn(ah, bh, -p);
-    const float f = __fsub_rn(p, rintf(p));   // |p| may exceed 2^22: exact rint
+    const float f = frac_turns(p);
     const float lo = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, e));
     return __fadd_rn(f, lo);
 }
@@ -46,6 +56,22 @@ __device__ __forceinline__ float frac_dot3(const float4 ah, const float4 al,
     float s = __fadd_rn(tp_frac(ah.x, al.x, bh.x, bl.x), tp_frac(ah.y, al.y, bh.y, bl.y));
     s = __fadd_rn(s, tp_frac(ah.z, al.z, bh.z, bl.z));
     return frac_turns(s);
+}
+
+// sin and cos of ph (radians, |ph| < 2^22 turns) on the FMA pipe, for a share
+// of the pairs so that the SFU is not the only pipe doing sincos: ph is reduced
+// to turns f in [-1/2, 1/2]; h = sqrt(2) sin(pi f) and q = sqrt(2) cos(pi f)
+// are Chebyshev interpolants in f^2 (sl1m_sincos_poly.h); then the double-angle
+// formulas give sin(2 pi f) = h q and cos(2 pi f) = 1 - h^2.  Absolute error
+// below 6e-7, the size of the SFU's own.  16 FMA-pipe instructions.
+__device__ __forceinline__ void sincos_fma(float ph, float& s, float& c)
+{
+    const float f = frac_turns(ph * INV_TWO_PI_F);
+    const float z = f * f;
+    const float h = f * fmaf(fmaf(fmaf(fmaf(SCP4, z, SCP3), z, SCP2), z, SCP1), z, SCP0);
+    const float q = fmaf(fmaf(fmaf(fmaf(SCQ4, z, SCQ3), z, SCQ2), z, SCQ1), z, SCQ0);
+    s = h * q;
+    c = fmaf(-h, h, 1.0f);
 }
 
 __device__ __forceinline__ float ex2_approx(float x)
@@ -81,6 +107,9 @@ struct GaussConst {
     float beta, id, gamr, coef;  // beta = w s^2, id = 1/(1+beta^2), gamr = 2 pi beta^2 id
                                  // (radians per turn of t), coef = -pi s^2 id log2(e)
     float cphase;                // id beta s^2 (u^2+v^2)/2, turns
+    float k0, k1;                // log2 of the amplitude as k0 + k1 t, t = u l + v m - w r^2/2:
+                                 // |(u,v) - w (l,m)|^2 = u^2 + v^2 - 2 w t, so k0 = coef (u^2+v^2),
+                                 // k1 = -2 coef w
 };
 
 __device__ __forceinline__ GaussConst gauss_const(float u, float v, float w, float sigma)
@@ -92,6 +121,8 @@ __device__ __forceinline__ GaussConst gauss_const(float u, float v, float w, flo
     g.gamr = g.beta * g.beta * g.id * TWO_PI_F;
     g.coef = -3.14159265358979f * s2 * g.id * LOG2E_F;
     g.cphase = 0.5f * g.id * g.beta * s2 * fmaf(u, u, v * v);
+    g.k0 = g.coef * fmaf(u, u, v * v);
+    g.k1 = -2.0f * g.coef * w;
     return g;
 }
 

@@ -428,6 +428,28 @@ int sl1m_problem::rebuild(cudaStream_t st)
                 return sl1m_fail(ctx, SL1M_ERR_ARG, "antenna index out of range at visibility %lld",
                                  (long long)k);
     }
+    {
+        // the mixed kernels round products of coordinates to whole turns on the
+        // FP32 add pipe, exact below 2^22 turns; a centre times an offset is at
+        // most twice the largest product, so each must stay below 2^21 turns
+        double mu = 0, mv = 0, mw = 0, ml = 0, mm = 0, mn = 0;
+        for (int64_t k = 0; k < n_vis; ++k) {
+            mu = std::max(mu, std::fabs(uvw[3 * k]));
+            mv = std::max(mv, std::fabs(uvw[3 * k + 1]));
+            mw = std::max(mw, std::fabs(uvw[3 * k + 2]));
+        }
+        for (int64_t j = 0; j < n_pix; ++j) {
+            const double l = lm[2 * j], m = lm[2 * j + 1], r2 = l * l + m * m;
+            ml = std::max(ml, std::fabs(l));
+            mm = std::max(mm, std::fabs(m));
+            mn = std::max(mn, r2 / (1.0 + std::sqrt(1.0 - r2)));
+        }
+        const double lim = 2097152.0;
+        if (mu * ml >= lim || mv * mm >= lim || mw * mn >= lim)
+            return sl1m_fail(ctx, SL1M_ERR_ARG,
+                             "max |u l|, |v m| or |w (n-1)| reaches 2^21 turns (%g, %g, %g): outside the "
+                             "range of the exact phase split", mu * ml, mv * mm, mw * mn);
+    }
     if (!dev) dev = std::make_unique<ProblemDev>();
     ProblemDev& D = *dev;
     // ---- visibilities: k-d order on (u, v)
@@ -566,8 +588,13 @@ const UnitCost& sl1m_problem::unit_cost(int precision, int op)
     if (ucost_ok[precision][op]) return uc;
     ucost_ok[precision][op] = true;
     uc.unit.clear();
-    const double gfac = n_ant > 0 ? 1.4 : 1.0;
-    const auto base = [](int kind) { return kind == DIRAC ? 1.0 : 1.6; };
+    // cost of a Gaussian pair relative to a Dirac pair of the same launch,
+    // measured on GB300 (128x128 pixels x 32,000 visibilities, one kind at a
+    // time): forward 1.45, adjoint 1.6 without gains; 1.23 and 1.3 with gains
+    // (the gains gather weighs on both kinds alike)
+    const double gfac = n_ant > 0 ? 2.0 : 1.0;
+    const double gcost = n_ant > 0 ? (op == 0 ? 1.23 : 1.3) : (op == 0 ? 1.45 : 1.6);
+    const auto base = [gcost](int kind) { return kind == DIRAC ? 1.0 : gcost; };
     int k0 = gkind_pix.empty() ? 0 : gkind_pix[0];
     bool one_kind = true;
     for (int k : gkind_pix) one_kind &= k == k0;
@@ -1388,7 +1415,8 @@ int sl1m_solve(sl1m_problem* prob, const sl1m_solve_opts* o, double* img_out, sl
     return SL1M_OK;
 }
 
-int sl1m_autotune(sl1m_problem* prob, int precision, int32_t* nst_out, int32_t* ctas_per_sm_out)
+int sl1m_autotune(sl1m_problem* prob, int precision, int32_t* nst_out, int32_t* ctas_per_sm_out,
+                  int32_t* npoly_out)
 {
     if (!prob) return SL1M_ERR_ARG;
     sl1m_ctx* ctx = prob->ctx;
@@ -1412,41 +1440,56 @@ int sl1m_autotune(sl1m_problem* prob, int precision, int32_t* nst_out, int32_t* 
         const std::vector<int> ns = {op == 0 ? d.pix.n_gran : d.vis.n_gran};
         const std::vector<const UnitCost*> uc = {&prob->unit_cost(precision, op)};
         const long long units = (long long)nb[0] * ns[0];
-        // 0 = warp-decoupled forward (warp-private staging, no CTA barrier)
+        // stage 1: streamed granules per stage x CTAs per SM (0 = warp-decoupled
+        // forward: warp-private staging, no CTA barrier); stage 2: at the best of
+        // those, the share of pairs whose sincos runs on the FMA pipe
         std::vector<int> cands = {NST_DEFAULT};
-        if (precision == SL1M_MIXED && !gains) cands = op == 0 ? std::vector<int>{0, 2, 4, 8} : std::vector<int>{2, 4, 8};
+        const bool mixed_plain = precision == SL1M_MIXED && !gains;
+        if (mixed_plain) cands = op == 0 ? std::vector<int>{0, 2, 4, 8} : std::vector<int>{2, 4, 8};
         float best = 1e30f;
-        int bnst = NST_DEFAULT, bk = 0;
+        int bcode = NST_DEFAULT, bk = 0;
+        const auto time_shape = [&](int code, int k) -> float {
+            DevPlan P;
+            if (build_plan(nb, ns, ctx->num_sms * k, P, st, &uc) != cudaSuccess) { rc = SL1M_ERR_CUDA; return 0.f; }
+            const size_t need = (size_t)std::max(1, P.pl.n_slots) * BLK;
+            if ((op == 0 ? ctx->partial_f.reserve(need, st) : ctx->partial_a.reserve(need, st)) != cudaSuccess) {
+                rc = SL1M_ERR_OOM;
+                return 0.f;
+            }
+            float ms = 0.f;
+            for (int rep = 0; rep < 4; ++rep) {
+                if (rep == 1) cudaEventRecord(e0, st);
+                cudaError_t e = op == 0 ? launch_forward(precision, gains, prob->n_ant, Bop->desc.p, P.dpl.p, P.pl.C,
+                                                         ctx->partial_f.p, st, code)
+                                        : launch_adjoint(precision, gains, prob->n_ant, Bop->desc.p, P.dpl.p, P.pl.C,
+                                                         ctx->partial_a.p, st, code);
+                if (e != cudaSuccess) { rc = SL1M_ERR_CUDA; return 0.f; }
+                ctx->n_launch += 1;
+            }
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = SL1M_ERR_CUDA; return 0.f; }
+            cudaEventElapsedTime(&ms, e0, e1);
+            return ms;
+        };
         for (int nst : cands) {
             const int occ = occupancy((precision == SL1M_FP64 ? 0 : 2) + op, gains, std::max(1, prob->n_ant), nst);
             for (int k = 1; k <= occ && rc == SL1M_OK; ++k) {
-                DevPlan P;
-                if (build_plan(nb, ns, ctx->num_sms * k, P, st, &uc) != cudaSuccess) { rc = SL1M_ERR_CUDA; break; }
-                const size_t need = (size_t)std::max(1, P.pl.n_slots) * BLK;
-                if ((op == 0 ? ctx->partial_f.reserve(need, st) : ctx->partial_a.reserve(need, st)) != cudaSuccess) {
-                    rc = SL1M_ERR_OOM;
-                    break;
-                }
-                float ms = 0.f;
-                for (int rep = 0; rep < 4; ++rep) {
-                    if (rep == 1) cudaEventRecord(e0, st);
-                    cudaError_t e = op == 0 ? launch_forward(precision, gains, prob->n_ant, Bop->desc.p, P.dpl.p,
-                                                             P.pl.C, ctx->partial_f.p, st, nst)
-                                            : launch_adjoint(precision, gains, prob->n_ant, Bop->desc.p, P.dpl.p,
-                                                             P.pl.C, ctx->partial_a.p, st, nst);
-                    if (e != cudaSuccess) { rc = SL1M_ERR_CUDA; break; }
-                    ctx->n_launch += 1;
-                }
-                cudaEventRecord(e1, st);
-                if (cudaEventSynchronize(e1) != cudaSuccess) { rc = SL1M_ERR_CUDA; break; }
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best) { best = ms; bnst = nst; bk = k; }
+                const float ms = time_shape(nst, k);
+                if (rc == SL1M_OK && ms < best) { best = ms; bcode = nst; bk = k; }
             }
         }
+        if (mixed_plain && bcode != 0)
+            for (int npoly = 1; npoly <= 2 && rc == SL1M_OK; ++npoly) {
+                const int code = shape_code(bcode, npoly);
+                const int occ = occupancy(2 + op, false, 1, code);
+                const float ms = time_shape(code, std::min(bk, occ));
+                if (rc == SL1M_OK && ms < best) { best = ms; bcode = code; bk = std::min(bk, occ); }
+            }
         if (rc != SL1M_OK) break;
-        ctx->tune[tune_key(precision, op, gains, prob->has_gauss, units)] = {bnst, bk};
-        if (nst_out) nst_out[op] = bnst;
+        ctx->tune[tune_key(precision, op, gains, prob->has_gauss, units)] = {bcode, bk};
+        if (nst_out) nst_out[op] = shape_nst(bcode);
         if (ctas_per_sm_out) ctas_per_sm_out[op] = bk;
+        if (npoly_out) npoly_out[op] = shape_npoly(bcode);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1454,6 +1497,32 @@ int sl1m_autotune(sl1m_problem* prob, int precision, int32_t* nst_out, int32_t* 
     for (auto& b : prob->op_batch) b.reset();
     for (auto& b : prob->solve_batch) b.reset();
     if (rc != SL1M_OK) return sl1m_fail(ctx, rc, "autotune failed");
+    return SL1M_OK;
+}
+
+int sl1m_set_tile_shape(sl1m_problem* prob, int precision, int op, int nst, int ctas_per_sm, int npoly)
+{
+    if (!prob) return SL1M_ERR_ARG;
+    sl1m_ctx* ctx = prob->ctx;
+    NOT_WHILE_SERVING(ctx);
+    RET(check_prec(ctx, precision));
+    const bool gains = prob->n_ant > 0;
+    if (op < 0 || op > 1 || ctas_per_sm < 1 || npoly < 0 || npoly > 2)
+        return sl1m_fail(ctx, SL1M_ERR_ARG, "bad tile shape (op %d, ctas/SM %d, npoly %d)", op, ctas_per_sm, npoly);
+    if (!(nst == 2 || nst == 4 || nst == 8 || (nst == 0 && op == 0 && npoly == 0)))
+        return sl1m_fail(ctx, SL1M_ERR_ARG, "nst must be 2, 4 or 8 (or 0 for the forward, npoly 0)");
+    if ((gains || precision == SL1M_FP64) && (nst != NST_DEFAULT || npoly != 0))
+        return sl1m_fail(ctx, SL1M_ERR_ARG, "with gains or in FP64 only the CTAs per SM can be set");
+    RET(prob->rebuild(ctx->stream));
+    const DevProblem& d = prob->hp;
+    const long long units = op == 0 ? (long long)d.vis.n_blk * d.pix.n_gran : (long long)d.pix.n_blk * d.vis.n_gran;
+    const int code = shape_code(nst, npoly);
+    const int occ = occupancy((precision == SL1M_FP64 ? 0 : 2) + op, gains, std::max(1, prob->n_ant), code);
+    if (ctas_per_sm > occ)
+        return sl1m_fail(ctx, SL1M_ERR_ARG, "%d CTAs per SM do not fit (at most %d)", ctas_per_sm, occ);
+    ctx->tune[tune_key(precision, op, gains, prob->has_gauss, units)] = {code, ctas_per_sm};
+    for (auto& b : prob->op_batch) b.reset();
+    for (auto& b : prob->solve_batch) b.reset();
     return SL1M_OK;
 }
 

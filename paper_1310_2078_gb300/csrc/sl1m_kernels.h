@@ -12,6 +12,12 @@ enum FinishMode : int { FIN_OP = 0, FIN_POWER = 1, FIN_SOLVE = 2, FIN_INIT = 3 }
 // kernels (2, 4 or 8; the tile shape the autotuner picks); for the forward,
 // 0 selects the warp-decoupled kernel (each warp stages for itself).
 constexpr int NST_DEFAULT = 4;
+// Tile-shape code carried as `nst` below: streamed granules per stage (2, 4,
+// 8, or 0 for the warp-decoupled forward) plus 16 x npoly, the pairs of every
+// 8 whose sincos runs on the FMA pipe (0, 1 or 2; Dirac tiles without gains).
+constexpr int shape_code(int nst, int npoly) { return nst | (npoly << 4); }
+constexpr int shape_nst(int code) { return code & 15; }
+constexpr int shape_npoly(int code) { return code >> 4; }
 cudaError_t launch_forward(int precision, bool gains, int n_ant, const DevProblem* probs,
                            const Plan* plp, int C, double2* partial, cudaStream_t st, int nst = NST_DEFAULT);
 cudaError_t launch_adjoint(int precision, bool gains, int n_ant, const DevProblem* probs, const Plan* plp, int C,

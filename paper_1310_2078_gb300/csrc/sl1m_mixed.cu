@@ -36,18 +36,34 @@
 
 namespace sl1m {
 
+// Forward gains table in shared memory: one row of G pixels per antenna,
+// padded to GP so that the lanes' rows start in different banks (a row of
+// antenna a starts at bank 2 a mod 32); the pixel index then enters the
+// address as a constant offset.
+constexpr int GP = G + 1;
+
 // ----------------------------------------------------------- forward tiles
 
-template <bool GAINS, bool EXACT>
+// Pair (jj, r) of every 4 streamed elements x 2 owned elements takes its
+// sincos on the FMA pipe when it is one of the last NPOLY of those 8.
+template <int NPOLY>
+__device__ __forceinline__ constexpr bool fma_slot(int jj, int r) { return 2 * jj + r >= 8 - NPOLY; }
+
+template <bool GAINS, bool EXACT, int NPOLY = 0>
 __device__ __forceinline__ void fwd_dirac_tile(const float4* __restrict__ s_off,
                                                const float4* __restrict__ s_lo,
                                                const float* __restrict__ sB,
-                                               const float2* __restrict__ s_gain, int n_ant,
+                                               const float2* __restrict__ s_gain,
                                                const float4 (&dx)[2], const float4 (&dxl)[2],
                                                const int2 (&ant)[2], float (&sr)[2], float (&si)[2])
 {
-#pragma unroll 4
-    for (int j = 0; j < G; ++j) {
+    const float2* ga_row[2] = {s_gain + ant[0].x * GP, s_gain + ant[1].x * GP};   // GAINS only
+    const float2* gb_row[2] = {s_gain + ant[0].y * GP, s_gain + ant[1].y * GP};
+#pragma unroll 1
+    for (int j0 = 0; j0 < G; j0 += 4)
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+        const int j = j0 + jj;
         const float4 o = s_off[j];             // {dl, dm, dn, a = x/n}
         const float b = sB[j];                 // B_j in radians
         const float4 ol = EXACT ? s_lo[j] : o;
@@ -57,10 +73,11 @@ __device__ __forceinline__ void fwd_dirac_tile(const float4* __restrict__ s_off,
             if (EXACT) ph = frac_turns(fmaf(b, INV_TWO_PI_F, frac_dot3(dx[r], dxl[r], o, ol))) * TWO_PI_F;
             else ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, b)));   // dx in radians
             float sn, cs;
-            __sincosf(ph, &sn, &cs);
+            if (!EXACT && fma_slot<NPOLY>(jj, r)) sincos_fma(ph, sn, cs);
+            else __sincosf(ph, &sn, &cs);
             if (GAINS) {
-                const float2 ga = s_gain[j * n_ant + ant[r].x];
-                const float2 gb = s_gain[j * n_ant + ant[r].y];
+                const float2 ga = ga_row[r][j];
+                const float2 gb = gb_row[r][j];
                 const float gr = fmaf(ga.x, gb.x, ga.y * gb.y);    // G_a conj(G_b)
                 const float gi = fmaf(ga.y, gb.x, -ga.x * gb.y);
                 sr[r] = fmaf(o.w, fmaf(gr, cs, gi * sn), sr[r]);    // a g (cs - i sn)
@@ -78,12 +95,14 @@ __device__ __forceinline__ void fwd_gauss_tile(const float4* __restrict__ s_off,
                                                const float4* __restrict__ s_lo,
                                                const float4* __restrict__ s_pg,
                                                const float* __restrict__ sB,
-                                               const float2* __restrict__ s_gain, int n_ant, bool par,
+                                               const float2* __restrict__ s_gain, bool par,
                                                const float4 (&xh)[2], const float4 (&dx)[2],
                                                const float4 (&dxl)[2], const GaussConst (&gc)[2],
                                                const int2 (&ant)[2], float (&sr)[2], float (&si)[2])
 {
-#pragma unroll 2
+    const float2* ga_row[2] = {s_gain + ant[0].x * GP, s_gain + ant[1].x * GP};   // GAINS only
+    const float2* gb_row[2] = {s_gain + ant[0].y * GP, s_gain + ant[1].y * GP};
+#pragma unroll(GAINS ? 1 : 2)   // the gains variant stays within 80 registers
     for (int j = 0; j < G; ++j) {
         const float4 o = s_off[j];
         const float4 pg = s_pg[j];             // {l, m, r^2/2, nu}
@@ -106,11 +125,10 @@ __device__ __forceinline__ void fwd_gauss_tile(const float4* __restrict__ s_off,
             }
             float sn, cs;
             __sincosf(ph, &sn, &cs);
-            const float e1 = fmaf(-wf, pg.x, uf), e2 = fmaf(-wf, pg.y, vf);
-            const float amp = o.w * ex2_approx(gc[r].coef * fmaf(e1, e1, e2 * e2));
+            const float amp = o.w * ex2_approx(fmaf(gc[r].k1, t, gc[r].k0));   // (x/n) e^{Re(qc)}
             if (GAINS) {
-                const float2 ga = s_gain[j * n_ant + ant[r].x];
-                const float2 gb = s_gain[j * n_ant + ant[r].y];
+                const float2 ga = ga_row[r][j];
+                const float2 gb = gb_row[r][j];
                 const float gr = fmaf(ga.x, gb.x, ga.y * gb.y);
                 const float gi = fmaf(ga.y, gb.x, -ga.x * gb.y);
                 sr[r] = fmaf(amp, fmaf(gr, cs, gi * sn), sr[r]);
@@ -127,7 +145,7 @@ __device__ __forceinline__ void fwd_gauss_tile(const float4* __restrict__ s_off,
 // Streamed: pixel granules through shared memory, NST per barrier pair (a
 // tile shape the autotuner picks; the gains kernel stages one, since one
 // granule's gains for all antennas already fill most of shared memory).
-template <bool GAINS, int NST>
+template <bool GAINS, int NST, int NPOLY = 0>
 __global__ void __launch_bounds__(NTHREADS, 3)
 fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ plp, double2* __restrict__ partial)
 {
@@ -138,7 +156,7 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
     __shared__ float4 s_cen[NST][3];       // centre hi, lo, extent
     __shared__ int s_kind[NST];
     __shared__ float s_sig[NST];
-    extern __shared__ float2 s_gain[];     // GAINS: [G][n_ant]
+    extern __shared__ float2 s_gain[];     // GAINS: [n_ant][GP]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Plan pl = *plp;
@@ -203,8 +221,11 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                 s_sig[threadIdx.x] = P.gsig[g];
             }
             if (GAINS) {
-                const float2* src = P.gains32 + (size_t)gs * G * n_ant;
-                for (int i = threadIdx.x; i < G * n_ant; i += NTHREADS) s_gain[i] = src[i];
+                const float2* src = P.gains32 + (size_t)gs * G * n_ant;   // [pixel][antenna]
+                for (int i = threadIdx.x; i < G * n_ant; i += NTHREADS) {
+                    const int j = i / n_ant, a = i - j * n_ant;        // coalesced read
+                    s_gain[a * GP + j] = src[i];
+                }
             }
             __syncthreads();
             // B_j = frac(Xc . (Y_j - Yc)) for this warp's granule centre
@@ -227,10 +248,10 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                 if (kind == DIRAC) {
                     if (exact) {
                         const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]}, dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
-                        fwd_dirac_tile<GAINS, true>(s_off[q], s_lo[q], s_B[warp][q], s_gain, n_ant, dxt, dxl, ant,
+                        fwd_dirac_tile<GAINS, true>(s_off[q], s_lo[q], s_B[warp][q], s_gain, dxt, dxl, ant,
                                                     sr, si);
                     } else {
-                        fwd_dirac_tile<GAINS, false>(s_off[q], s_lo[q], s_B[warp][q], s_gain, n_ant, dx, dx, ant,
+                        fwd_dirac_tile<GAINS, false, NPOLY>(s_off[q], s_lo[q], s_B[warp][q], s_gain, dx, dx, ant,
                                                      sr, si);
                     }
 #pragma unroll
@@ -250,10 +271,10 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                     }
                     if (exact) {
                         const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]}, dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
-                        fwd_gauss_tile<GAINS, true>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], s_gain, n_ant, par, xh,
+                        fwd_gauss_tile<GAINS, true>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], s_gain, par, xh,
                                                     dxt, dxl, gc, ant, sr, si);
                     } else {
-                        fwd_gauss_tile<GAINS, false>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], s_gain, n_ant, par,
+                        fwd_gauss_tile<GAINS, false>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], s_gain, par,
                                                      xh, dx, dx, gc, ant, sr, si);
                     }
 #pragma unroll
@@ -360,10 +381,10 @@ fwd_mixed_wd_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict
                 if (kind == DIRAC) {
                     if (exact) {
                         const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]}, dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
-                        fwd_dirac_tile<false, true>(s_off[warp][q], s_lo[warp][q], s_B[warp][q], nullptr, 0, dxt, dxl,
+                        fwd_dirac_tile<false, true>(s_off[warp][q], s_lo[warp][q], s_B[warp][q], nullptr, dxt, dxl,
                                                     ant, sr, si);
                     } else {
-                        fwd_dirac_tile<false, false>(s_off[warp][q], s_lo[warp][q], s_B[warp][q], nullptr, 0, dx, dx,
+                        fwd_dirac_tile<false, false>(s_off[warp][q], s_lo[warp][q], s_B[warp][q], nullptr, dx, dx,
                                                      ant, sr, si);
                     }
 #pragma unroll
@@ -384,10 +405,10 @@ fwd_mixed_wd_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict
                     if (exact) {
                         const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]}, dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
                         fwd_gauss_tile<false, true>(s_off[warp][q], s_lo[warp][q], s_pg[warp][q], s_B[warp][q],
-                                                    nullptr, 0, par, xh, dxt, dxl, gc, ant, sr, si);
+                                                    nullptr, par, xh, dxt, dxl, gc, ant, sr, si);
                     } else {
                         fwd_gauss_tile<false, false>(s_off[warp][q], s_lo[warp][q], s_pg[warp][q], s_B[warp][q],
-                                                     nullptr, 0, par, xh, dx, dx, gc, ant, sr, si);
+                                                     nullptr, par, xh, dx, dx, gc, ant, sr, si);
                     }
 #pragma unroll
                     for (int r = 0; r < 2; ++r) {
@@ -421,7 +442,7 @@ struct SmemGain {
     __device__ float2 operator()(int a, int r) const { return tab[a * G + lane + 32 * r]; }
 };
 
-template <bool GAINS, bool EXACT, class GF>
+template <bool GAINS, bool EXACT, class GF, int NPOLY = 0>
 __device__ __forceinline__ void adj_dirac_tile(const float4* __restrict__ s_off,
                                                const float4* __restrict__ s_lo,
                                                const float2* __restrict__ s_r,
@@ -431,8 +452,11 @@ __device__ __forceinline__ void adj_dirac_tile(const float4* __restrict__ s_off,
                                                const float4 (&dx)[2], const float4 (&dxl)[2],
                                                float (&acc)[2])
 {
-#pragma unroll 4
-    for (int k = 0; k < G; ++k) {
+#pragma unroll 1
+    for (int k0 = 0; k0 < G; k0 += 4)
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const int k = k0 + kk;
         const float4 o = s_off[k];             // {du, dv, dw, W}
         const float b = sB[k];
         const float2 rr = s_r[k];
@@ -443,7 +467,8 @@ __device__ __forceinline__ void adj_dirac_tile(const float4* __restrict__ s_off,
             if (EXACT) ph = frac_turns((C[r] + b * INV_TWO_PI_F) + frac_dot3(dx[r], dxl[r], o, ol)) * TWO_PI_F;
             else ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, C[r] + b)));
             float sn, cs;
-            __sincosf(ph, &sn, &cs);                      // exp(+i ph) = cs + i sn
+            if (!EXACT && fma_slot<NPOLY>(kk, r)) sincos_fma(ph, sn, cs);
+            else __sincosf(ph, &sn, &cs);                 // exp(+i ph) = cs + i sn
             if (GAINS) {
                 const int2 ab = s_ant[k];
                 const float2 ga = gain(ab.x, r);
@@ -474,28 +499,28 @@ __device__ __forceinline__ void adj_gauss_tile(const float4* __restrict__ s_off,
 #pragma unroll 2
     for (int k = 0; k < G; ++k) {
         const float4 o = s_off[k];
-        const float4 va = s_abs[k];            // {u, v, w, 2 pi w}
+        const float4 va = s_abs[k];            // {u, v, -2 w, u^2 + v^2}
         const float4 gw = s_gw[k];             // {gamr, coef, r're, r'im}
         const float b = sB[k];
         const float4 ol = EXACT ? s_lo[k] : o;
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
-            const float t = fmaf(va.x, pgd[r].x, fmaf(va.y, pgd[r].y, -va.z * pgd[r].z));
+            // pgd = {l, m, r^2/4, pi nu}: t = u l + v m - w r^2/2
+            const float t = fmaf(va.x, pgd[r].x, fmaf(va.y, pgd[r].y, va.z * pgd[r].z));
             float ph;                                  // radians; C and dx in radians unless EXACT
             if (EXACT) {
                 ph = (C[r] + b * INV_TWO_PI_F) + frac_dot3(dx[r], dxl[r], o, ol);
                 ph = fmaf(-gw.x * INV_TWO_PI_F, t, ph);
-                if (par) ph = fmaf(-va.z, pgd[r].w, ph);
+                if (par) ph = fmaf(va.z, pgd[r].w * INV_TWO_PI_F, ph);   // -w nu, turns
                 ph = frac_turns(ph) * TWO_PI_F;
             } else {
                 ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, C[r] + b)));
                 ph = fmaf(-gw.x, t, ph);
-                if (par) ph = fmaf(-va.w, pgd[r].w, ph);   // va.w = 2 pi w
+                if (par) ph = fmaf(va.z, pgd[r].w, ph);                  // -2 pi w nu
             }
             float sn, cs;
             __sincosf(ph, &sn, &cs);
-            const float e1 = fmaf(-va.z, pgd[r].x, va.x), e2 = fmaf(-va.z, pgd[r].y, va.y);
-            const float amp = ex2_approx(gw.y * fmaf(e1, e1, e2 * e2));
+            const float amp = ex2_approx(gw.y * fmaf(va.z, t, va.w));   // coef |(u,v) - w (l,m)|^2
             const float zr = fmaf(cs, gw.z, -sn * gw.w);
             if (GAINS) {
                 const int2 ab = s_ant[k];
@@ -514,13 +539,13 @@ __device__ __forceinline__ void adj_gauss_tile(const float4* __restrict__ s_off,
 
 // Owned: pixels (warp = one pixel granule, lane = 2 pixels).
 // Streamed: visibility granules through shared memory, NSA per stage.
-template <int NSA>
+template <int NSA, int NPOLY = 0>
 __global__ void __launch_bounds__(NTHREADS, 3)
 adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ plp, double* __restrict__ partial)
 {
     __shared__ float4 s_off[NSA][G];            // {du, dv, dw, W}
     __shared__ float4 s_lo[NSA][G];
-    __shared__ float4 s_abs[NSA][G];            // {u, v, w, 2 pi w} (Gaussian owners)
+    __shared__ float4 s_abs[NSA][G];            // {u, v, -2 w, u^2 + v^2} (Gaussian owners)
     __shared__ float2 s_r[NSA][G];
     __shared__ int2 s_ant[NSA][G];      // unused without gains
     __shared__ float s_B[BLK_GRAN][NSA][G];
@@ -566,7 +591,7 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
             for (int r = 0; r < 2; ++r) {
                 xh[r] = P.pix.hi[eidx[r]];
                 dx[r] = to_rad(P.pix.off[eidx[r]]);
-                if (kind != DIRAC) pgd[r] = P.pgauss[eidx[r]];
+                if (kind != DIRAC) pgd[r] = pix_for_gauss(P.pgauss[eidx[r]]);
             }
         }
         const bool gauss = (kind != DIRAC);
@@ -581,7 +606,7 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                 const int e = (gs + q) * G + i;
                 s_off[q][i] = P.vis.off[e];
                 s_lo[q][i] = P.vis.offlo[e];
-                s_abs[q][i] = to_w2pi(P.vis.hi[e]);
+                s_abs[q][i] = vis_for_gauss(P.vis.hi[e]);
                 const double2 rr = R[e];
                 s_r[q][i] = make_float2((float)rr.x, (float)rr.y);
             }
@@ -599,7 +624,7 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                     float b = frac_dot3(ch, cl, s_off[q][k], s_lo[q][k]);
                     if (gauss) {
                         const float4 va = s_abs[q][k];
-                        const GaussConst gc = gauss_const(va.x, va.y, va.z, sigma);
+                        const GaussConst gc = gauss_const(va.x, va.y, -0.5f * va.z, sigma);
                         b = frac_turns(b + gc.cphase);
                         const float2 rr = s_r[q][k];
                         // r' = id (1 - i beta) r
@@ -626,7 +651,8 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                         adj_dirac_tile<false, true>(s_off[q], s_lo[q], s_r[q], s_ant[q], s_B[warp][q], ng, C, dxt,
                                                     dxl, acc);
                     } else {
-                        adj_dirac_tile<false, false>(s_off[q], s_lo[q], s_r[q], s_ant[q], s_B[warp][q], ng, Cr, dx,
+                        adj_dirac_tile<false, false, NoGain, NPOLY>(s_off[q], s_lo[q], s_r[q], s_ant[q], s_B[warp][q],
+                                                                    ng, Cr, dx,
                                                      dx, acc);
                     }
                 } else {
@@ -716,7 +742,7 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
             for (int r = 0; r < 2; ++r) {
                 xh[r] = P.pix.hi[eidx[r]];
                 dx[r] = to_rad(P.pix.off[eidx[r]]);
-                if (gauss) pgd[r] = P.pgauss[eidx[r]];
+                if (gauss) pgd[r] = pix_for_gauss(P.pgauss[eidx[r]]);
             }
             const SmemGain sg{s_gain, lane};
             double tot[2] = {0.0, 0.0};
@@ -728,7 +754,7 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
                     const int e = (gs + q) * G + i;
                     s_off[q][i] = P.vis.off[e];
                     s_lo[q][i] = P.vis.offlo[e];
-                    s_abs[q][i] = to_w2pi(P.vis.hi[e]);
+                    s_abs[q][i] = vis_for_gauss(P.vis.hi[e]);
                     const double2 rr = R[e];
                     s_r[q][i] = make_float2((float)rr.x, (float)rr.y);
                     s_ant[q][i] = P.ant[e];
@@ -748,7 +774,7 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
                     float b = frac_dot3(ch, cl, s_off[q][k], s_lo[q][k]);
                     if (gauss) {
                         const float4 va = s_abs[q][k];
-                        const GaussConst gc = gauss_const(va.x, va.y, va.z, sigma);
+                        const GaussConst gc = gauss_const(va.x, va.y, -0.5f * va.z, sigma);
                         b = frac_turns(b + gc.cphase);
                         const float2 rr = s_r[q][k];
                         s_gw[q][k] = make_float4(gc.gamr, gc.coef, gc.id * fmaf(gc.beta, rr.y, rr.x),
@@ -803,7 +829,7 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
 
 // ------------------------------------------------------------- launchers
 
-int fwd_smem_bytes(int n_ant, bool gains) { return gains ? G * n_ant * (int)sizeof(float2) : 0; }
+int fwd_smem_bytes(int n_ant, bool gains) { return gains ? GP * n_ant * (int)sizeof(float2) : 0; }
 int adj_gains_smem_bytes(int n_ant) { return G * n_ant * (int)sizeof(float2); }
 
 template <class K>
@@ -814,6 +840,33 @@ static int occ_of(K kernel, int dyn)
     return n < 1 ? 1 : n;
 }
 
+using FwdKernel = void (*)(const DevProblem*, const Plan*, double2*);
+using AdjKernel = void (*)(const DevProblem*, const Plan*, double*);
+
+// The no-gains kernel of a tile-shape code (nst 2 / 4 / 8, npoly 0 / 1 / 2).
+template <int N>
+static FwdKernel fwd_by_poly(int np)
+{
+    return np <= 0 ? fwd_mixed_kernel<false, N, 0> : np == 1 ? fwd_mixed_kernel<false, N, 1>
+                                                             : fwd_mixed_kernel<false, N, 2>;
+}
+template <int N>
+static AdjKernel adj_by_poly(int np)
+{
+    return np <= 0 ? adj_mixed_kernel<N, 0> : np == 1 ? adj_mixed_kernel<N, 1> : adj_mixed_kernel<N, 2>;
+}
+static FwdKernel fwd_kernel_of(int code)
+{
+    const int nst = shape_nst(code), np = shape_npoly(code);
+    if (nst == 0) return fwd_mixed_wd_kernel;
+    return nst <= 2 ? fwd_by_poly<2>(np) : nst <= 4 ? fwd_by_poly<4>(np) : fwd_by_poly<8>(np);
+}
+static AdjKernel adj_kernel_of(int code)
+{
+    const int nst = shape_nst(code), np = shape_npoly(code);
+    return nst <= 2 ? adj_by_poly<2>(np) : nst <= 4 ? adj_by_poly<4>(np) : adj_by_poly<8>(np);
+}
+
 cudaError_t launch_forward_mixed(bool gains, int n_ant, int nst, const DevProblem* probs, const Plan* plp, int C,
                                  double2* partial, cudaStream_t st)
 {
@@ -821,14 +874,8 @@ cudaError_t launch_forward_mixed(bool gains, int n_ant, int nst, const DevProble
         // the dynamic shared-memory limit was raised by occupancy_mixed()
         // when the batch was built (not here: this may run under capture)
         fwd_mixed_kernel<true, 1><<<C, NTHREADS, fwd_smem_bytes(n_ant, true), st>>>(probs, plp, partial);
-    } else if (nst == 0) {
-        fwd_mixed_wd_kernel<<<C, NTHREADS, 0, st>>>(probs, plp, partial);
-    } else if (nst <= 2) {
-        fwd_mixed_kernel<false, 2><<<C, NTHREADS, 0, st>>>(probs, plp, partial);
-    } else if (nst <= 4) {
-        fwd_mixed_kernel<false, 4><<<C, NTHREADS, 0, st>>>(probs, plp, partial);
     } else {
-        fwd_mixed_kernel<false, 8><<<C, NTHREADS, 0, st>>>(probs, plp, partial);
+        fwd_kernel_of(nst)<<<C, NTHREADS, 0, st>>>(probs, plp, partial);
     }
     return cudaGetLastError();
 }
@@ -837,9 +884,7 @@ cudaError_t launch_adjoint_mixed(bool gains, int n_ant, int nst, const DevProble
                                  double* partial, cudaStream_t st)
 {
     if (gains) adj_mixed_gains_kernel<<<C, NTHREADS, adj_gains_smem_bytes(n_ant), st>>>(probs, plp, partial);
-    else if (nst <= 2) adj_mixed_kernel<2><<<C, NTHREADS, 0, st>>>(probs, plp, partial);
-    else if (nst <= 4) adj_mixed_kernel<4><<<C, NTHREADS, 0, st>>>(probs, plp, partial);
-    else adj_mixed_kernel<8><<<C, NTHREADS, 0, st>>>(probs, plp, partial);
+    else adj_kernel_of(nst)<<<C, NTHREADS, 0, st>>>(probs, plp, partial);
     return cudaGetLastError();
 }
 
@@ -855,10 +900,7 @@ int occupancy_mixed(int op, bool gains, int n_ant, int nst)
             }
             return occ_of(fwd_mixed_kernel<true, 1>, sm);
         }
-        if (nst == 0) return occ_of(fwd_mixed_wd_kernel, 0);
-        if (nst <= 2) return occ_of(fwd_mixed_kernel<false, 2>, 0);
-        if (nst <= 4) return occ_of(fwd_mixed_kernel<false, 4>, 0);
-        return occ_of(fwd_mixed_kernel<false, 8>, 0);
+        return occ_of(fwd_kernel_of(nst), 0);
     }
     if (gains) {
         const int sm = adj_gains_smem_bytes(n_ant);
@@ -868,9 +910,7 @@ int occupancy_mixed(int op, bool gains, int n_ant, int nst)
         }
         return occ_of(adj_mixed_gains_kernel, sm);
     }
-    if (nst <= 2) return occ_of(adj_mixed_kernel<2>, 0);
-    if (nst <= 4) return occ_of(adj_mixed_kernel<4>, 0);
-    return occ_of(adj_mixed_kernel<8>, 0);
+    return occ_of(adj_kernel_of(nst), 0);
 }
 
 }  // namespace sl1m

@@ -37,7 +37,7 @@ EXPORTS = [
     "sl1m_counters", "sl1m_counters_reset", "sl1m_plan_preview", "sl1m_granule_order",
     "sl1m_server_start", "sl1m_server_submit", "sl1m_server_poll", "sl1m_server_wait",
     "sl1m_server_stop", "sl1m_server_info", "sl1m_forward_noalloc", "sl1m_autotune",
-    "sl1m_dirty_image", "sl1m_solve_refine", "sl1m_get_solution",
+    "sl1m_dirty_image", "sl1m_solve_refine", "sl1m_get_solution", "sl1m_set_tile_shape",
 ]
 
 
@@ -126,7 +126,8 @@ def load():
             "sl1m_adjoint": ([vp, vp, vp, C.c_int], C.c_int),
             "sl1m_forward_dev": ([vp, vp, vp, C.c_int], C.c_int),
             "sl1m_forward_noalloc": ([vp, vp, vp, C.c_int], C.c_int),
-            "sl1m_autotune": ([vp, C.c_int, vp, vp], C.c_int),
+            "sl1m_autotune": ([vp, C.c_int, vp, vp, vp], C.c_int),
+            "sl1m_set_tile_shape": ([vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
             "sl1m_dirty_image": ([vp, C.c_int, vp, C.POINTER(d)], C.c_int),
             "sl1m_solve_refine": ([vp, C.POINTER(SolveOpts), C.POINTER(RefineOpts), d, C.POINTER(RefineStats)],
                                   C.c_int),
@@ -402,11 +403,18 @@ class Problem:
         return img, st.as_dict()
 
     def autotune(self, precision=MIXED):
-        """sl1m_autotune: returns {"nst": [fwd, adj], "ctas_per_sm": [fwd, adj]}."""
+        """sl1m_autotune: returns {"nst": [fwd, adj], "ctas_per_sm": [fwd, adj],
+        "npoly": [fwd, adj]}."""
         nst = np.zeros(2, np.int32)
         k = np.zeros(2, np.int32)
-        self.ctx.check(self.lib.sl1m_autotune(self.h, int(precision), _ptr(nst), _ptr(k)))
-        return {"nst": nst.tolist(), "ctas_per_sm": k.tolist()}
+        npoly = np.zeros(2, np.int32)
+        self.ctx.check(self.lib.sl1m_autotune(self.h, int(precision), _ptr(nst), _ptr(k), _ptr(npoly)))
+        return {"nst": nst.tolist(), "ctas_per_sm": k.tolist(), "npoly": npoly.tolist()}
+
+    def set_tile_shape(self, op, nst, ctas_per_sm, npoly=0, precision=MIXED):
+        """sl1m_set_tile_shape (op 0 forward, 1 adjoint)."""
+        self.ctx.check(self.lib.sl1m_set_tile_shape(self.h, int(precision), int(op), int(nst),
+                                                    int(ctas_per_sm), int(npoly)))
 
     def solve_refine(self, lam, delta0, levels, refine_frac=0.01, keep_unrefined=True, L=0.0,
                      max_iter=200, rel_tol=0.0, precision=MIXED):

@@ -262,3 +262,24 @@ def test_invalid_arguments_rejected(ctx, gpu_lib):
         P.set_gains(np.ones((1, 3)))
         P.forward(np.ones(1))
     assert e.value.status == gpu_lib.ERR_ARG
+
+
+def test_coordinates_beyond_the_exact_split_are_refused(ctx, gpu_lib):
+    """|u l| up to 2^21 turns is split exactly; beyond that the operator
+    calls refuse the problem (no kernel runs)."""
+    lm = np.array([[0.5, 0.0], [0.0, 0.1]])
+    P = ctx.problem()
+    P.set_pixels(lm)
+    P.set_visibilities(np.array([[5.0e6, 1.0, 1.0], [10.0, 20.0, 5.0]]))      # |u l| = 2.5e6 turns
+    with pytest.raises(gpu_lib.SL1MError) as e:
+        P.forward(np.ones(2))
+    assert e.value.status == gpu_lib.ERR_ARG
+    # just below the limit both paths still match the oracle
+    u = 0.99 * 2 ** 21 / 0.5
+    P.set_visibilities(np.array([[u, 1.0, 1.0], [10.0, 20.0, 5.0]]))
+    x = np.array([1.0, 0.0])
+    O = oracle.Problem(np.array([[u, 1.0, 1.0], [10.0, 20.0, 5.0]]), lm)
+    want = oracle.forward(O, x)
+    for prec in (gpu_lib.FP64, gpu_lib.MIXED):
+        got = P.forward(x, prec)
+        assert np.max(np.abs(got - want)) <= 1e-5 * np.max(np.abs(want))
