@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="skip the (untimed) tile-shape autotuner")
+    ap.add_argument("--shape", default="",
+                    help="set the tile shapes instead of autotuning: 'nst,ctas_per_sm,npoly' of the "
+                         "forward, ':', the same of the adjoint (e.g. 8,3,1:4,3,1); profiler runs use "
+                         "this so the captured kernels are the ones a plain run's autotuner picks")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ops-only", action="store_true",
                     help="a step is one forward + one adjoint through the C ABI (device pointers)")
@@ -150,21 +154,80 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def ncu_traffic(kernel, nst, ctas, workload):
+KERNEL_SOURCES = ("sl1m_mixed.cu", "sl1m_fp64.cu", "sl1m_devfn.cuh", "sl1m_dev.h", "sl1m_sincos_poly.h")
+
+
+def kernel_source_hash():
+    """First 12 hex digits of the SHA-1 of the operator kernels' sources: a
+    profile summary records it, so counters taken on other kernel code are
+    not reported as this code's."""
+    import hashlib
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1310_2078_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(kernel, nst, npoly, ctas, workload):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, or None when no summary matches this kernel, tile shape, grid and
-    workload (the counters belong to the kernel as it was captured)."""
-    p = os.path.join(ROOT, "profiles", "launch_list_wide_field_dirac_256x256_40320vis.md")
+    summaries, or None when no summary matches this kernel, tile shape, grid,
+    workload and kernel source (the counters belong to the kernel as it was
+    captured)."""
+    src = kernel_source_hash()
+    pdir = os.path.join(ROOT, "profiles")
     try:
-        with open(p) as f:
-            text = f.read()
+        names = sorted(os.listdir(pdir))
     except OSError:
         return None
-    for m in re.finditer(r"^traffic: kernel=(\S+) nst=(\d+) ctas=(\d+) workload=(\S+) "
-                         r"dram_bytes_per_launch=(\d+)$", text, re.M):
-        if (m.group(1), int(m.group(2)), int(m.group(3)), m.group(4)) == (kernel, nst, ctas, workload):
-            return int(m.group(5))
+    pat = (r"^traffic: kernel=(\S+) nst=(\d+) npoly=(\d+) ctas=(\d+) workload=(\S+) "
+           r"src=([0-9a-f]+) dram_bytes_per_launch=(\d+)$")
+    for name in names:
+        try:
+            with open(os.path.join(pdir, name)) as f:
+                text = f.read()
+        except OSError:
+            continue
+        for m in re.finditer(pat, text, re.M):
+            key = (m.group(1), int(m.group(2)), int(m.group(3)), int(m.group(4)), m.group(5), m.group(6))
+            if key == (kernel, nst, npoly, ctas, workload, src):
+                return int(m.group(7))
     return None
+
+
+def sfu_peak(w):
+    """SFU issue bound of the operator kernels on workload w (Gpairs/s).
+
+    Per pair the SFU runs sin and cos (Dirac) plus exp2 (Gaussian); the
+    bound is N_SM x 16 MUFU/clk x max clock over the MUFU ops per pair,
+    weighted by the share of pairs of each kind (time per pair adds up).
+    For all-Dirac work a second figure is returned: the bound when a share
+    of the pairs takes its sincos on the FMA pipe, a linear program over two
+    limits per SM sub-partition -- one warp instruction issued per clock and
+    one MUFU warp instruction per 8 clocks -- with the fewest instructions a
+    pair can take: 8 on the SFU path (3 FFMA phase, 1 FMUL argument scale,
+    2 MUFU, 2 FFMA accumulate) and 21 on the FMA path (3 phase, 16 sincos,
+    2 accumulate)."""
+    per_sm_clk = N_SM * SM_MAX_MHZ * 1e6 / 1e9
+    kinds = np.zeros(w.n_pix, np.int32) if w.kind is None else np.asarray(w.kind)
+    f_gauss = float(np.mean(kinds != 0))
+    mufu = (1 - f_gauss) * SFU_OPS_PER_PAIR["dirac"] + f_gauss * SFU_OPS_PER_PAIR["gauss"]
+    peak = per_sm_clk * MUFU_PER_SM_CLK / mufu
+    basis = (f"SFU issue: {N_SM} SM x {MUFU_PER_SM_CLK} MUFU/clk x {SM_MAX_MHZ:.0f} MHz / "
+             f"{mufu:.3g} MUFU per pair ({100 * (1 - f_gauss):.0f}% Dirac pairs at 2, "
+             f"{100 * f_gauss:.0f}% Gaussian at 3)")
+    alt = None
+    if f_gauss == 0.0:
+        # per sub-partition and clock: x SFU-path and y FMA-path warp-pairs,
+        # 2 x <= 1/8 (MUFU), 8 x + 21 y <= 1 (issue); maximise x + y
+        x = 1.0 / 16.0
+        y = (1.0 - 8.0 * x) / 21.0
+        pairs_per_sm_clk = 4 * 32 * (x + y)
+        alt = {"peak": per_sm_clk * pairs_per_sm_clk,
+               "basis": "LP over issue (1 warp instr/clk/SMSP) and MUFU (1/8 per clk/SMSP): "
+                        "8 instr/pair on the SFU path, 21 with sincos on the FMA pipe; "
+                        f"{pairs_per_sm_clk:.2f} pairs/clk/SM at {100 * y / (x + y):.0f}% FMA-path pairs"}
+    return peak, basis, alt
 
 
 def baseline_inputs(w):
@@ -369,7 +432,14 @@ def main():
     V = P.forward(w.x_true, sl1m.FP64 if w.n_vis * w.n_pix < 5e9 else sl1m.MIXED) + w.noise
     P.set_vis_data(V)
     lam = w.lambda_frac * P.adjoint(V * (1 if w.weights is None else w.weights), prec).max()
-    tuned = None if args.no_autotune else P.autotune(prec)      # untimed set-up
+    if args.shape:                                              # untimed set-up
+        sh = [[int(v) for v in part.split(",")] for part in args.shape.split(":")]
+        for op in (0, 1):
+            P.set_tile_shape(op, sh[op][0], sh[op][1], sh[op][2], precision=prec)
+        tuned = {"nst": [sh[0][0], sh[1][0]], "ctas_per_sm": [sh[0][1], sh[1][1]],
+                 "npoly": [sh[0][2], sh[1][2]], "source": "--shape"}
+    else:
+        tuned = None if args.no_autotune else P.autotune(prec)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
 
     if args.ops_only:
@@ -434,18 +504,19 @@ def main():
     dom = max(keys, key=lambda k: prof[k]["ms"])
     pd = prof[dom]
     achieved = pd["pairs"] / (pd["ms"] / 1e3) / 1e9 if pd["ms"] > 0 else 0.0
-    kind = "gauss" if (w.kind is not None and np.any(w.kind != 0)) else "dirac"
-    peak = N_SM * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / SFU_OPS_PER_PAIR[kind] / 1e9
+    peak, peak_basis, alt = sfu_peak(w)
     traffic = None
     if tuned is not None:
         op = 0 if dom.startswith("fwd") else 1
-        traffic = ncu_traffic(dom, tuned["nst"][op], tuned["ctas_per_sm"][op] * N_SM, w.name)
+        traffic = ncu_traffic(dom, tuned["nst"][op], tuned["npoly"][op],
+                              tuned["ctas_per_sm"][op] * N_SM, w.name)
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": "Gpairs/s", "frac": achieved / peak,
-                "peak_basis": (f"SFU issue: {N_SM} SM x {MUFU_PER_SM_CLK} MUFU/clk x "
-                               f"{SM_MAX_MHZ:.0f} MHz / {SFU_OPS_PER_PAIR[kind]} MUFU per pair"),
+                "unit": "Gpairs/s", "frac": achieved / peak, "peak_basis": peak_basis,
                 "launches": pd["launches"], "avg_launch_ms": pd["ms"] / max(1, pd["launches"]),
                 "traffic": traffic}
+    if alt:
+        roofline["peak_sfu_plus_fma_sincos"] = alt
+        roofline["frac_of_sfu_plus_fma_sincos"] = achieved / alt["peak"]
     fin_ms = prof["fwd_finish"]["ms"] + prof["adj_finish"]["ms"]
     fin_bytes = prof["fwd_finish"]["bytes"] + prof["adj_finish"]["bytes"]
     vec = {"kernels": "fwd_finish+adj_finish (residual, threshold, momentum)",

@@ -1478,13 +1478,15 @@ int sl1m_autotune(sl1m_problem* prob, int precision, int32_t* nst_out, int32_t* 
                 if (rc == SL1M_OK && ms < best) { best = ms; bcode = nst; bk = k; }
             }
         }
-        if (mixed_plain && bcode != 0)
+        if (mixed_plain && bcode != 0) {
+            const int nst = bcode, k0 = bk;       // stage-1 choice (npoly 0)
             for (int npoly = 1; npoly <= 2 && rc == SL1M_OK; ++npoly) {
-                const int code = shape_code(bcode, npoly);
-                const int occ = occupancy(2 + op, false, 1, code);
-                const float ms = time_shape(code, std::min(bk, occ));
-                if (rc == SL1M_OK && ms < best) { best = ms; bcode = code; bk = std::min(bk, occ); }
+                const int code = shape_code(nst, npoly);
+                const int k = std::min(k0, occupancy(2 + op, false, 1, code));
+                const float ms = time_shape(code, k);
+                if (rc == SL1M_OK && ms < best) { best = ms; bcode = code; bk = k; }
             }
+        }
         if (rc != SL1M_OK) break;
         ctx->tune[tune_key(precision, op, gains, prob->has_gauss, units)] = {bcode, bk};
         if (nst_out) nst_out[op] = shape_nst(bcode);

@@ -31,9 +31,11 @@ def test_autotune_choice_is_valid_and_keeps_parity(gpu_lib, kw):
     # a solve built after tuning uses the tuned plans and still matches
     V = oracle.forward(O, (rng.random(5000) < 0.002) * 2.0)
     P.set_vis_data(V)
-    L, _ = oracle.power(O)
+    # parity holds at any common step constant; 1.5x a short power iteration
+    # keeps the steps stable without paying for a converged one on the CPU
+    L = 1.5 * oracle.power(O, max_iter=5)[0]
     lam = 0.05 * oracle.adjoint(O, V).max()
-    img, st = P.solve(lam, L=L, max_iter=15)
-    img_o, _ = oracle.fista(O, V, lam, L, 15)
+    img, st = P.solve(lam, L=L, max_iter=8)
+    img_o, _ = oracle.fista(O, V, lam, L, 8)
     assert np.max(np.abs(img - img_o)) <= 1e-4 * img_o.max()
     ctx.close()
