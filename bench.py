@@ -517,6 +517,11 @@ def main():
     if alt:
         roofline["peak_sfu_plus_fma_sincos"] = alt
         roofline["frac_of_sfu_plus_fma_sincos"] = achieved / alt["peak"]
+    per_kernel = {k: {"launches": prof[k]["launches"],
+                      "avg_launch_ms": prof[k]["ms"] / max(1, prof[k]["launches"]),
+                      "Gpairs_per_s": prof[k]["pairs"] / (prof[k]["ms"] / 1e3) / 1e9,
+                      "frac_of_peak": prof[k]["pairs"] / (prof[k]["ms"] / 1e3) / 1e9 / peak}
+                  for k in keys if prof[k]["ms"] > 0}
     fin_ms = prof["fwd_finish"]["ms"] + prof["adj_finish"]["ms"]
     fin_bytes = prof["fwd_finish"]["bytes"] + prof["adj_finish"]["bytes"]
     vec = {"kernels": "fwd_finish+adj_finish (residual, threshold, momentum)",
@@ -547,7 +552,7 @@ def main():
                "iters": [s["iters"] for s in stats], "power_iters": stats[-1]["power_iters"],
                "final": {"E": stats[-1]["E"], "resid2": stats[-1]["resid2"],
                          "nnz": stats[-1]["nnz"], "L": stats[-1]["L"]},
-               "roofline": roofline, "vector_updates": vec,
+               "roofline": roofline, "operator_kernels": per_kernel, "vector_updates": vec,
                "clocks": clk, "gpu_launches": counters["launches"],
                "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(out))

@@ -35,6 +35,13 @@ __host__ __device__ inline d4 make_d4(double x, double y, double z, double w)
 }
 
 constexpr int G = 64;                 // granule size
+// Gains of one pixel granule as the mixed kernels hold them: one row of G
+// pixels per antenna, padded to GP so that rows start in different shared-
+// memory banks; rows are padded to an even count so that a granule's table
+// (gain_rows(n_ant) x GP float2) is a multiple of 16 bytes, the unit of a
+// bulk (TMA) copy.  The same layout sits in HBM, [pixel granule][row][GP].
+constexpr int GP = G + 1;
+__host__ __device__ inline int gain_rows(int n_ant) { return (n_ant + 1) & ~1; }
 constexpr int BLK_GRAN = 8;           // owned granules per CTA (one per warp)
 constexpr int BLK = G * BLK_GRAN;     // owned elements per CTA block
 constexpr int NTHREADS = 256;         // 8 warps
@@ -127,7 +134,7 @@ struct DevProblem {
     const float* gsig;        // [pix.n_gran] sigma per pixel granule (FP32 path)
     const double* gsig64;     // [pix.n_gran] sigma per pixel granule (FP64 path)
     const int* gkind;         // [pix.n_gran] kind per pixel granule
-    const float2* gains32;    // [pix.n_pad][n_ant] or null
+    const float2* gains32;    // [pix.n_gran][gain_rows(n_ant)][GP] or null
     const double2* gains64;   // [pix.n_pad][n_ant] or null
     int n_ant;
     // operator mode (st == null): one forward x -> fwd_out or adjoint r -> adj_out

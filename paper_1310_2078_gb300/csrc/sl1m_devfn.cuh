@@ -74,6 +74,65 @@ __device__ __forceinline__ void sincos_fma(float ph, float& s, float& c)
     c = fmaf(-h, h, 1.0f);
 }
 
+// ---- bulk (TMA) copies global -> shared, completed on an mbarrier
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// makes the barrier initialisation visible to the async (TMA) proxy
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// orders this CTA's earlier generic-proxy shared-memory accesses before
+// later async-proxy (TMA) writes to the same memory
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// One thread: arrive on bar expecting `bytes` more, then copy `bytes`
+// (a multiple of 16; both addresses 16-byte aligned) from src to dst.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// Wait until the phase of bar with this parity has completed.  Bounded: after
+// 2^20 unsuccessful tries (each may suspend the thread for a while) it gives
+// up and returns false; the caller records the fault and carries on, so no
+// barrier of the CTA is left waiting.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity)
+{
+    const unsigned a = smem_u32(bar);
+    for (int i = 0; i < (1 << 20); ++i) {
+        unsigned ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+// Dynamic shared memory of this launch, in bytes.
+__device__ __forceinline__ unsigned dyn_smem_bytes()
+{
+    unsigned r;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
+
 __device__ __forceinline__ float ex2_approx(float x)
 {
     float y;

@@ -533,14 +533,19 @@ int sl1m_problem::rebuild(cudaStream_t st)
         gkind_pix = gk;
         pix_orig = H.orig;
         if (n_ant > 0) {
-            std::vector<float2> g32((size_t)H.n_pad * n_ant, make_float2(0.f, 0.f));
+            // FP32: per pixel granule one row of GP per antenna (gain_rows(n_ant)
+            // rows), the shared-memory layout, so a granule's table is one bulk
+            // copy; FP64: [pixel][antenna]
+            const size_t tab = (size_t)gain_rows(n_ant) * GP;
+            std::vector<float2> g32((size_t)H.n_gran * tab, make_float2(0.f, 0.f));
             std::vector<double2> g64((size_t)H.n_pad * n_ant, make_double2(0.0, 0.0));
             for (int t = 0; t < H.n_pad; ++t) {
                 const int o = H.orig[t];
                 if (o < 0) continue;
+                const size_t row0 = (size_t)(t / G) * tab + (size_t)(t % G);
                 for (int a = 0; a < n_ant; ++a) {
                     const double re = gains[((size_t)o * n_ant + a) * 2], im = gains[((size_t)o * n_ant + a) * 2 + 1];
-                    g32[(size_t)t * n_ant + a] = make_float2((float)re, (float)im);
+                    g32[row0 + (size_t)a * GP] = make_float2((float)re, (float)im);
                     g64[(size_t)t * n_ant + a] = make_double2(re, im);
                 }
             }
@@ -634,7 +639,7 @@ size_t sl1m_problem::estimate_bytes() const
 {
     const size_t nv = (size_t)((n_vis + G - 1) / G) * G, np = (size_t)((n_pix + G - 1) / G) * G;
     size_t b = nv * (4 * 16 + 32 + 4 + 8 + 16) + np * (4 * 16 + 32 + 4 + 16 + 32);
-    b += (size_t)n_ant * np * (8 + 16);
+    if (n_ant > 0) b += (size_t)gain_rows(n_ant) * GP * (np / G) * 8 + (size_t)n_ant * np * 16;   // FP32 + FP64
     b += np * 8 * 4 + nv * 16 * 3;                 // solver vectors
     b += (nv + np) * 16 * 3;                       // operator scratch
     return b + (1 << 16);
@@ -963,6 +968,18 @@ int batch_ticks(sl1m_ctx* ctx, Batch& B, int n)
     return SL1M_OK;
 }
 
+// A gains kernel's bounded wait for a bulk copy gave up (the flag was read
+// on the context's stream before its last synchronisation): the results of
+// the launches since the previous check are invalid.
+static int check_wait_fault(sl1m_ctx* ctx, unsigned fault)
+{
+    if (!fault) return SL1M_OK;
+    CK(wait_fault_clear(ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return sl1m_fail(ctx, SL1M_ERR_CUDA, "a bulk copy into shared memory did not complete within the kernel's "
+                                         "bounded wait; the results of this call are invalid");
+}
+
 int batch_phases(sl1m_ctx* ctx, Batch& B, std::vector<int>& out)
 {
     const int np = (int)B.probs.size();
@@ -970,8 +987,10 @@ int batch_phases(sl1m_ctx* ctx, Batch& B, std::vector<int>& out)
     CKL(launch_phases(B.desc.p, B.n_probs_dev.p, std::max(1, std::min(64, (np + 127) / 128)), B.phases_dev.p,
                       ctx->stream));
     CK(cudaMemcpyAsync(out.data(), B.phases_dev.p, sizeof(int) * np, cudaMemcpyDeviceToHost, ctx->stream));
+    unsigned fault = 0;
+    CK(wait_fault_read(&fault, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    return SL1M_OK;
+    return check_wait_fault(ctx, fault);
 }
 
 // Operator-mode batch of a single problem (cached per precision).
@@ -1299,7 +1318,10 @@ int sl1m_forward(sl1m_problem* prob, const double* x, double* vis_out, int preci
     CK(cudaMemcpyAsync(D.x_user.p, x, sizeof(double) * prob->n_pix, cudaMemcpyHostToDevice, ctx->stream));
     RET(sl1m_forward_dev(prob, D.x_user.p, (double*)D.vis_user.p, precision));
     CK(cudaMemcpyAsync(vis_out, D.vis_user.p, sizeof(double2) * prob->n_vis, cudaMemcpyDeviceToHost, ctx->stream));
+    unsigned fault = 0;
+    CK(wait_fault_read(&fault, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    RET(check_wait_fault(ctx, fault));
     ctx->h2d += (long long)sizeof(double) * prob->n_pix;
     ctx->d2h += (long long)sizeof(double2) * prob->n_vis;
     return SL1M_OK;
@@ -1320,7 +1342,10 @@ int sl1m_adjoint(sl1m_problem* prob, const double* r, double* img_out, int preci
     CK(cudaMemcpyAsync(D.r_user.p, r, sizeof(double2) * prob->n_vis, cudaMemcpyHostToDevice, ctx->stream));
     RET(sl1m_adjoint_dev(prob, (const double*)D.r_user.p, D.img_user.p, precision));
     CK(cudaMemcpyAsync(img_out, D.img_user.p, sizeof(double) * prob->n_pix, cudaMemcpyDeviceToHost, ctx->stream));
+    unsigned fault = 0;
+    CK(wait_fault_read(&fault, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    RET(check_wait_fault(ctx, fault));
     ctx->h2d += (long long)sizeof(double2) * prob->n_vis;
     ctx->d2h += (long long)sizeof(double) * prob->n_pix;
     return SL1M_OK;

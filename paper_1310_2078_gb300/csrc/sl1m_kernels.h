@@ -25,6 +25,11 @@ cudaError_t launch_adjoint(int precision, bool gains, int n_ant, const DevProble
 // which: 0 fwd fp64, 1 adj fp64, 2 fwd mixed, 3 adj mixed
 int occupancy(int which, bool gains, int n_ant, int nst = NST_DEFAULT);
 int fwd_smem_bytes(int n_ant, bool gains);
+// The mixed gains kernels' bounded waits for their bulk copies set a device
+// flag when they give up; read it into *host_flag (asynchronously on st: valid
+// after the stream is synchronised) and clear it.
+cudaError_t wait_fault_read(unsigned* host_flag, cudaStream_t st);
+cudaError_t wait_fault_clear(cudaStream_t st);
 
 // solver kernels (sl1m_solver.cu)
 cudaError_t launch_gather_real(const double* src, double* dst, const int* orig, int n_pad,

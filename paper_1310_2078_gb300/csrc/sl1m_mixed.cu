@@ -36,11 +36,14 @@
 
 namespace sl1m {
 
-// Forward gains table in shared memory: one row of G pixels per antenna,
-// padded to GP so that the lanes' rows start in different banks (a row of
+// Gains tables in shared memory: one row of G pixels per antenna, padded to
+// GP (sl1m_dev.h) so that the lanes' rows start in different banks (a row of
 // antenna a starts at bank 2 a mod 32); the pixel index then enters the
 // address as a constant offset.
-constexpr int GP = G + 1;
+
+// Set (never cleared here) by a CTA whose bounded wait for a bulk copy gave
+// up; the host reads and clears it (mixed_wait_fault_take).
+__device__ unsigned int g_wait_fault;
 
 // ----------------------------------------------------------- forward tiles
 
@@ -90,12 +93,12 @@ __device__ __forceinline__ void fwd_dirac_tile(const float4* __restrict__ s_off,
     }
 }
 
-template <bool GAINS, bool EXACT>
+template <bool GAINS, bool EXACT, bool PAR>
 __device__ __forceinline__ void fwd_gauss_tile(const float4* __restrict__ s_off,
                                                const float4* __restrict__ s_lo,
                                                const float4* __restrict__ s_pg,
                                                const float* __restrict__ sB,
-                                               const float2* __restrict__ s_gain, bool par,
+                                               const float2* __restrict__ s_gain,
                                                const float4 (&xh)[2], const float4 (&dx)[2],
                                                const float4 (&dxl)[2], const GaussConst (&gc)[2],
                                                const int2 (&ant)[2], float (&sr)[2], float (&si)[2])
@@ -116,12 +119,12 @@ __device__ __forceinline__ void fwd_gauss_tile(const float4* __restrict__ s_off,
             if (EXACT) {
                 ph = fmaf(b, INV_TWO_PI_F, frac_dot3(dx[r], dxl[r], o, ol));
                 ph = fmaf(-gc[r].gamr * INV_TWO_PI_F, t, ph);
-                if (par) ph = fmaf(-wf, pg.w, ph);
+                if (PAR) ph = fmaf(-wf, pg.w, ph);
                 ph = frac_turns(ph) * TWO_PI_F;
             } else {
                 ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, b)));
                 ph = fmaf(-gc[r].gamr, t, ph);
-                if (par) ph = fmaf(-wf * TWO_PI_F, pg.w, ph);
+                if (PAR) ph = fmaf(-wf * TWO_PI_F, pg.w, ph);
             }
             float sn, cs;
             __sincosf(ph, &sn, &cs);
@@ -156,13 +159,28 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
     __shared__ float4 s_cen[NST][3];       // centre hi, lo, extent
     __shared__ int s_kind[NST];
     __shared__ float s_sig[NST];
-    extern __shared__ float2 s_gain[];     // GAINS: [n_ant][GP]
+    // GAINS: one or two buffers of a pixel granule's gains [gain_rows(n_ant)][GP],
+    // each filled by a bulk (TMA) copy that completes on its mbarrier; with two,
+    // the next granule's table is copied while the current one is in use
+    extern __shared__ __align__(128) float2 s_gain[];
+    __shared__ __align__(8) unsigned long long s_gbar[2];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Plan pl = *plp;
     const long long c = blockIdx.x;
     long long u, u_end;
     cta_range(pl, c, u, u_end);
+    unsigned gpar = 0;        // GAINS: parity of the next wait on buffer b (bit b)
+    int gcur = 0;             // GAINS: buffer of the current stage when double-buffered
+    bool gfault = false;      // GAINS: a bounded wait gave up
+    if (GAINS) {
+        if (threadIdx.x == 0) {
+            mbar_init(&s_gbar[0], 1);
+            mbar_init(&s_gbar[1], 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+    }
 
     while (u < u_end) {
         const int p = find_prob(pl, u);
@@ -179,8 +197,10 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
         const int g1 = (int)min((long long)upb, (long long)g0 + (u_end - u));
         const int vg = blk * BLK_GRAN + warp;
         const bool vg_ok = vg < P.vis.n_gran;
-        const int n_ant = P.n_ant;
         const int e0 = (vg_ok ? vg : 0) * G + lane;     // this lane's visibilities: e0, e0 + 32
+        const int gtab_n = GAINS ? gain_rows(P.n_ant) * GP : 0;                 // float2 per table
+        const unsigned gbytes = (unsigned)gtab_n * (unsigned)sizeof(float2);
+        const bool gdbl = GAINS && 2u * gbytes <= dyn_smem_bytes();
 
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 xh[2] = {z4, z4}, dx[2] = {z4, z4};
@@ -202,6 +222,17 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
         for (int gs = g0; gs < g1; gs += NST) {
             const int ns = min(NST, g1 - gs);
             __syncthreads();                       // previous stage consumed
+            if (GAINS && threadIdx.x == 0) {
+                // the buffers' last readers (generic proxy) are done: order them
+                // before the copies' writes (async proxy)
+                fence_proxy_async_smem();
+                const int b = gdbl ? gcur : 0;
+                if (gs == g0 || !gdbl)
+                    bulk_load(s_gain + b * gtab_n, P.gains32 + (size_t)gs * gtab_n, gbytes, &s_gbar[b]);
+                if (gdbl && gs + 1 < g1)          // prefetch the next granule's table
+                    bulk_load(s_gain + (b ^ 1) * gtab_n, P.gains32 + (size_t)(gs + 1) * gtab_n, gbytes,
+                              &s_gbar[b ^ 1]);
+            }
             for (int t = threadIdx.x; t < ns * G; t += NTHREADS) {
                 const int q = t / G, i = t % G;
                 const int g = gs + q;
@@ -220,14 +251,15 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                 s_kind[threadIdx.x] = P.gkind[g];
                 s_sig[threadIdx.x] = P.gsig[g];
             }
-            if (GAINS) {
-                const float2* src = P.gains32 + (size_t)gs * G * n_ant;   // [pixel][antenna]
-                for (int i = threadIdx.x; i < G * n_ant; i += NTHREADS) {
-                    const int j = i / n_ant, a = i - j * n_ant;        // coalesced read
-                    s_gain[a * GP + j] = src[i];
-                }
-            }
             __syncthreads();
+            const float2* gtab = s_gain;
+            if (GAINS) {
+                const int b = gdbl ? gcur : 0;
+                if (!mbar_wait(&s_gbar[b], (gpar >> b) & 1u)) gfault = true;
+                gpar ^= 1u << b;
+                gtab = s_gain + b * gtab_n;
+                if (gdbl) gcur ^= 1;
+            }
             // B_j = frac(Xc . (Y_j - Yc)) for this warp's granule centre
             for (int q = 0; q < ns; ++q) {
 #pragma unroll
@@ -248,10 +280,10 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                 if (kind == DIRAC) {
                     if (exact) {
                         const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]}, dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
-                        fwd_dirac_tile<GAINS, true>(s_off[q], s_lo[q], s_B[warp][q], s_gain, dxt, dxl, ant,
+                        fwd_dirac_tile<GAINS, true>(s_off[q], s_lo[q], s_B[warp][q], gtab, dxt, dxl, ant,
                                                     sr, si);
                     } else {
-                        fwd_dirac_tile<GAINS, false, NPOLY>(s_off[q], s_lo[q], s_B[warp][q], s_gain, dx, dx, ant,
+                        fwd_dirac_tile<GAINS, false, NPOLY>(s_off[q], s_lo[q], s_B[warp][q], gtab, dx, dx, ant,
                                                      sr, si);
                     }
 #pragma unroll
@@ -271,11 +303,16 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                     }
                     if (exact) {
                         const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]}, dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
-                        fwd_gauss_tile<GAINS, true>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], s_gain, par, xh,
-                                                    dxt, dxl, gc, ant, sr, si);
+                        if (par) fwd_gauss_tile<GAINS, true, true>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], gtab,
+                                                                   xh, dxt, dxl, gc, ant, sr, si);
+                        else fwd_gauss_tile<GAINS, true, false>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], gtab,
+                                                                xh, dxt, dxl, gc, ant, sr, si);
+                    } else if (par) {
+                        fwd_gauss_tile<GAINS, false, true>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], gtab,
+                                                           xh, dx, dx, gc, ant, sr, si);
                     } else {
-                        fwd_gauss_tile<GAINS, false>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], s_gain, par,
-                                                     xh, dx, dx, gc, ant, sr, si);
+                        fwd_gauss_tile<GAINS, false, false>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], gtab,
+                                                            xh, dx, dx, gc, ant, sr, si);
                     }
 #pragma unroll
                     for (int r = 0; r < 2; ++r) {
@@ -298,6 +335,7 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
         }
         u += g1 - g0;
     }
+    if (GAINS && gfault) atomicOr(&g_wait_fault, 1u);
 }
 
 // Forward, warp-decoupled variant (no gains): every warp stages the streamed
@@ -404,11 +442,16 @@ fwd_mixed_wd_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict
                     }
                     if (exact) {
                         const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]}, dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
-                        fwd_gauss_tile<false, true>(s_off[warp][q], s_lo[warp][q], s_pg[warp][q], s_B[warp][q],
-                                                    nullptr, par, xh, dxt, dxl, gc, ant, sr, si);
+                        if (par) fwd_gauss_tile<false, true, true>(s_off[warp][q], s_lo[warp][q], s_pg[warp][q],
+                                                                   s_B[warp][q], nullptr, xh, dxt, dxl, gc, ant, sr, si);
+                        else fwd_gauss_tile<false, true, false>(s_off[warp][q], s_lo[warp][q], s_pg[warp][q],
+                                                                s_B[warp][q], nullptr, xh, dxt, dxl, gc, ant, sr, si);
+                    } else if (par) {
+                        fwd_gauss_tile<false, false, true>(s_off[warp][q], s_lo[warp][q], s_pg[warp][q], s_B[warp][q],
+                                                           nullptr, xh, dx, dx, gc, ant, sr, si);
                     } else {
-                        fwd_gauss_tile<false, false>(s_off[warp][q], s_lo[warp][q], s_pg[warp][q], s_B[warp][q],
-                                                     nullptr, par, xh, dx, dx, gc, ant, sr, si);
+                        fwd_gauss_tile<false, false, false>(s_off[warp][q], s_lo[warp][q], s_pg[warp][q], s_B[warp][q],
+                                                            nullptr, xh, dx, dx, gc, ant, sr, si);
                     }
 #pragma unroll
                     for (int r = 0; r < 2; ++r) {
@@ -435,11 +478,11 @@ fwd_mixed_wd_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict
 struct NoGain {
     __device__ float2 operator()(int, int) const { return make_float2(1.f, 0.f); }
 };
-// gains in shared memory, [antenna][pixel of the owned granule]
+// gains in shared memory, [antenna][pixel of the owned granule], rows of GP
 struct SmemGain {
     const float2* tab;
     int lane;
-    __device__ float2 operator()(int a, int r) const { return tab[a * G + lane + 32 * r]; }
+    __device__ float2 operator()(int a, int r) const { return tab[a * GP + lane + 32 * r]; }
 };
 
 template <bool GAINS, bool EXACT, class GF, int NPOLY = 0>
@@ -485,13 +528,13 @@ __device__ __forceinline__ void adj_dirac_tile(const float4* __restrict__ s_off,
     }
 }
 
-template <bool GAINS, bool EXACT, class GF>
+template <bool GAINS, bool EXACT, bool PAR, class GF>
 __device__ __forceinline__ void adj_gauss_tile(const float4* __restrict__ s_off,
                                                const float4* __restrict__ s_lo,
                                                const float4* __restrict__ s_abs,
                                                const int2* __restrict__ s_ant,
                                                const float* __restrict__ sB,
-                                               const float4* __restrict__ s_gw, const GF& gain, bool par,
+                                               const float4* __restrict__ s_gw, const GF& gain,
                                                const float (&C)[2],
                                                const float4 (&dx)[2], const float4 (&dxl)[2],
                                                const float4 (&pgd)[2], float (&acc)[2])
@@ -511,12 +554,12 @@ __device__ __forceinline__ void adj_gauss_tile(const float4* __restrict__ s_off,
             if (EXACT) {
                 ph = (C[r] + b * INV_TWO_PI_F) + frac_dot3(dx[r], dxl[r], o, ol);
                 ph = fmaf(-gw.x * INV_TWO_PI_F, t, ph);
-                if (par) ph = fmaf(va.z, pgd[r].w * INV_TWO_PI_F, ph);   // -w nu, turns
+                if (PAR) ph = fmaf(va.z, pgd[r].w * INV_TWO_PI_F, ph);   // -w nu, turns
                 ph = frac_turns(ph) * TWO_PI_F;
             } else {
                 ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, C[r] + b)));
                 ph = fmaf(-gw.x, t, ph);
-                if (par) ph = fmaf(va.z, pgd[r].w, ph);                  // -2 pi w nu
+                if (PAR) ph = fmaf(va.z, pgd[r].w, ph);                  // -2 pi w nu
             }
             float sn, cs;
             __sincosf(ph, &sn, &cs);
@@ -659,11 +702,11 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                     if (exact) {
                         const float4 dxt[2] = {P.pix.off[eidx[0]], P.pix.off[eidx[1]]},
                                  dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
-                        adj_gauss_tile<false, true>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[warp][q],
-                                                    s_gw[warp][q], ng, par, C, dxt, dxl, pgd, acc);
+                        if (par) adj_gauss_tile<false, true, true>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[warp][q], s_gw[warp][q], ng, C, dxt, dxl, pgd, acc);
+                        else adj_gauss_tile<false, true, false>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[warp][q], s_gw[warp][q], ng, C, dxt, dxl, pgd, acc);
                     } else {
-                        adj_gauss_tile<false, false>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[warp][q],
-                                                     s_gw[warp][q], ng, par, Cr, dx, dx, pgd, acc);
+                        if (par) adj_gauss_tile<false, false, true>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[warp][q], s_gw[warp][q], ng, Cr, dx, dx, pgd, acc);
+                        else adj_gauss_tile<false, false, false>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[warp][q], s_gw[warp][q], ng, Cr, dx, dx, pgd, acc);
                     }
                 }
 #pragma unroll
@@ -698,13 +741,23 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
     __shared__ float4 s_gw[BLK_GRAN][G];
     __shared__ float4 s_cen[BLK_GRAN][3];
     __shared__ double s_red[BLK_GRAN][G];
-    extern __shared__ float2 s_gain[];      // [n_ant][G]
+    // the owned granule's gains [gain_rows(n_ant)][GP], filled by a bulk
+    // (TMA) copy that completes on s_gbar
+    extern __shared__ __align__(128) float2 s_gain[];
+    __shared__ __align__(8) unsigned long long s_gbar;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Plan pl = *plp;
     const long long c = blockIdx.x;
     long long u, u_end;
     cta_range(pl, c, u, u_end);
+    unsigned gpar = 0;          // parity of the next wait on s_gbar
+    bool gfault = false;        // a bounded wait gave up
+    if (threadIdx.x == 0) {
+        mbar_init(&s_gbar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
 
     while (u < u_end) {
         const int p = find_prob(pl, u);
@@ -719,16 +772,17 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
         const int blk = (int)(loc / upb);
         const int g0 = (int)(loc % upb);
         const int g1 = (int)min((long long)upb, (long long)g0 + (u_end - u));
-        const int n_ant = P.n_ant;
+        const int gtab_n = gain_rows(P.n_ant) * GP;      // float2 per granule table
         const int gb = pl.prob_b0[p] + blk;
         double* dst = partial + (size_t)slot_of(pl, gb) * BLK;
         for (int og = 0; og < BLK_GRAN; ++og) {
             const int pgi = blk * BLK_GRAN + og;
             if (pgi >= P.pix.n_gran) break;                  // uniform over the CTA
             __syncthreads();                                 // s_gain / s_red free again
-            for (int i = threadIdx.x; i < G * n_ant; i += NTHREADS) {
-                const int j = i / n_ant, a = i - j * n_ant;  // coalesced read of [pixel][antenna]
-                s_gain[a * G + j] = P.gains32[(size_t)(pgi * G + j) * n_ant + a];
+            if (threadIdx.x == 0) {
+                fence_proxy_async_smem();                    // the table's last readers are done
+                bulk_load(s_gain, P.gains32 + (size_t)pgi * gtab_n, (unsigned)gtab_n * (unsigned)sizeof(float2),
+                          &s_gbar);
             }
             const float4 ch = P.pix.cen_hi[pgi], cl = P.pix.cen_lo[pgi], ext = P.pix.ext[pgi];
             const int kind = P.gkind[pgi];
@@ -745,6 +799,8 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
                 if (gauss) pgd[r] = pix_for_gauss(P.pgauss[eidx[r]]);
             }
             const SmemGain sg{s_gain, lane};
+            if (!mbar_wait(&s_gbar, gpar)) gfault = true;
+            gpar ^= 1u;
             double tot[2] = {0.0, 0.0};
             for (int gs = g0; gs < g1; gs += BLK_GRAN) {
                 const int ns = min(BLK_GRAN, g1 - gs);
@@ -801,11 +857,11 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
                     if (exact) {
                         const float4 dxt[2] = {P.pix.off[eidx[0]], P.pix.off[eidx[1]]},
                                  dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
-                        adj_gauss_tile<true, true>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[q], s_gw[q], sg, par, C,
-                                                   dxt, dxl, pgd, acc);
+                        if (par) adj_gauss_tile<true, true, true>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[q], s_gw[q], sg, C, dxt, dxl, pgd, acc);
+                        else adj_gauss_tile<true, true, false>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[q], s_gw[q], sg, C, dxt, dxl, pgd, acc);
                     } else {
-                        adj_gauss_tile<true, false>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[q], s_gw[q], sg, par,
-                                                    Cr, dx, dx, pgd, acc);
+                        if (par) adj_gauss_tile<true, false, true>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[q], s_gw[q], sg, Cr, dx, dx, pgd, acc);
+                        else adj_gauss_tile<true, false, false>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[q], s_gw[q], sg, Cr, dx, dx, pgd, acc);
                     }
                 }
 #pragma unroll
@@ -825,12 +881,34 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
         }
         u += g1 - g0;
     }
+    if (gfault) atomicOr(&g_wait_fault, 1u);
 }
 
 // ------------------------------------------------------------- launchers
 
-int fwd_smem_bytes(int n_ant, bool gains) { return gains ? GP * n_ant * (int)sizeof(float2) : 0; }
-int adj_gains_smem_bytes(int n_ant) { return G * n_ant * (int)sizeof(float2); }
+// Bytes of one pixel granule's gains table in shared memory.
+static int gains_table_bytes(int n_ant) { return gain_rows(n_ant) * GP * (int)sizeof(float2); }
+// The forward double-buffers the table (prefetching the next granule's while
+// the current one is in use) when two fit in this much dynamic shared memory;
+// the kernel reads the choice back from the launch's dynamic size.
+constexpr int FWD_GAINS_DBL_MAX = 200 * 1024;
+int fwd_smem_bytes(int n_ant, bool gains)
+{
+    if (!gains) return 0;
+    const int t = gains_table_bytes(n_ant);
+    return 2 * t <= FWD_GAINS_DBL_MAX ? 2 * t : t;
+}
+int adj_gains_smem_bytes(int n_ant) { return gains_table_bytes(n_ant); }
+
+cudaError_t wait_fault_read(unsigned* host_flag, cudaStream_t st)
+{
+    return cudaMemcpyFromSymbolAsync(host_flag, g_wait_fault, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, st);
+}
+cudaError_t wait_fault_clear(cudaStream_t st)
+{
+    static const unsigned zero = 0;
+    return cudaMemcpyToSymbolAsync(g_wait_fault, &zero, sizeof(unsigned), 0, cudaMemcpyHostToDevice, st);
+}
 
 template <class K>
 static int occ_of(K kernel, int dyn)
