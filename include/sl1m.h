@@ -37,7 +37,11 @@ extern "C" {
 #define SL1M_ERR_ARG 1        /* null pointer, bad size, l^2+m^2 >= 1, sigma < 0,
                                  non-finite input, antenna index out of range */
 #define SL1M_ERR_OOM 2        /* device or host allocation failed              */
-#define SL1M_ERR_CUDA 3       /* a CUDA runtime call failed                    */
+#define SL1M_ERR_CUDA 3       /* a CUDA runtime call failed, or a kernel's
+                                 bounded wait for a bulk copy into shared
+                                 memory gave up (a device flag, read by every
+                                 synchronous call; the *_dev calls leave it to
+                                 the next synchronous call on the context)   */
 #define SL1M_ERR_NONFINITE 4  /* a non-finite value appeared during a solve    */
 #define SL1M_ERR_TIMEOUT 5    /* a bounded wait expired                        */
 #define SL1M_ERR_BUSY 6       /* admission refused (memory budget)             */

@@ -42,6 +42,15 @@ constexpr int G = 64;                 // granule size
 // bulk (TMA) copy.  The same layout sits in HBM, [pixel granule][row][GP].
 constexpr int GP = G + 1;
 __host__ __device__ inline int gain_rows(int n_ant) { return (n_ant + 1) & ~1; }
+// Baselines of a visibility granule.  With gains, the members of each
+// visibility granule are sorted by antenna pair (a, b); a granule of an
+// interferometer's data holds few distinct pairs (the uv track of a baseline
+// is compact), so the forward builds, per tile, x_j G_ja conj(G_jb) once per
+// distinct pair and pixel instead of once per visibility and pixel.  Granules
+// with more than NB_MAX pairs take the per-visibility gathers instead.
+constexpr int NB_MAX = 28;
+constexpr int BT_CH = 16;             // pixels per chunk of that table
+constexpr int BT_P = BT_CH + 1;       // its padded row (rows start in different banks)
 constexpr int BLK_GRAN = 8;           // owned granules per CTA (one per warp)
 constexpr int BLK = G * BLK_GRAN;     // owned elements per CTA block
 constexpr int NTHREADS = 256;         // 8 warps
@@ -128,6 +137,9 @@ struct DevProblem {
     Side vis;
     Side pix;
     const int2* ant;          // [vis.n_pad] antenna pair (a, b)
+    const int* vslot;         // gains: [vis.n_pad] slot of the visibility's pair in its granule's list
+    const int2* gbl;          // gains: [vis.n_gran][NB_MAX] the granule's distinct pairs, sorted
+    const int* gnb;           // gains: [vis.n_gran] number of pairs, 0 if more than NB_MAX
     const double2* V;         // [vis.n_pad] measured visibilities (sorted)
     const float4* pgauss;     // [pix.n_pad] {l, m, (l^2+m^2)/2, nu = n-1+(l^2+m^2)/2}
     const d4* pgauss64;       // same in FP64

@@ -100,32 +100,19 @@ static void kd_append(std::vector<int>& order, std::vector<int> members, const d
 // a shared-memory row of 8-byte words: 16 lanes are served together, without
 // conflict when their antennas differ modulo 16.  Lane t owns slots t and
 // t+32 of a granule, so slots {0-15, 16-31, 32-47, 48-63} form the groups.
-// Reorder each granule (its members stay the same) greedily so that every
-// group holds distinct a mod 16 and b mod 16 as far as possible.
-static void spread_antennas(std::vector<int>& order, const std::vector<int>& ant)
+// With gains: sort the members of each granule (its membership is unchanged)
+// by antenna pair (a, b), padding last, so that equal pairs are adjacent: the
+// adjoint computes a pair's gain product once per run, and the forward lists
+// the granule's distinct pairs.
+static void sort_baselines(std::vector<int>& order, const std::vector<int>& ant)
 {
-    for (size_t g0 = 0; g0 + G <= order.size(); g0 += G) {
-        std::vector<int> pool(order.begin() + g0, order.begin() + g0 + G);
-        std::vector<int> out;
-        out.reserve(G);
-        for (int grp = 0; grp < 4; ++grp) {
-            int ca[16] = {0}, cb[16] = {0};
-            for (int s = 0; s < 16; ++s) {
-                size_t best = 0;
-                int best_cost = 1 << 30;
-                for (size_t i = 0; i < pool.size(); ++i) {
-                    const int o = pool[i];
-                    const int cost = o < 0 ? 1 : ca[ant[2 * o] & 15] + cb[ant[2 * o + 1] & 15];
-                    if (cost < best_cost) { best_cost = cost; best = i; if (cost == 0) break; }
-                }
-                const int o = pool[best];
-                pool.erase(pool.begin() + best);
-                if (o >= 0) { ca[ant[2 * o] & 15]++; cb[ant[2 * o + 1] & 15]++; }
-                out.push_back(o);
-            }
-        }
-        std::copy(out.begin(), out.end(), order.begin() + g0);
-    }
+    for (size_t g0 = 0; g0 + G <= order.size(); g0 += G)
+        std::stable_sort(order.begin() + g0, order.begin() + g0 + G, [&](int x, int y) {
+            if (x < 0 || y < 0) return x >= 0 && y < 0;            // padding last
+            const long long kx = (long long)ant[2 * x] << 32 | (unsigned)ant[2 * x + 1];
+            const long long ky = (long long)ant[2 * y] << 32 | (unsigned)ant[2 * y + 1];
+            return kx < ky;
+        });
 }
 
 struct HostSide {
@@ -395,6 +382,8 @@ sl1m_ctx::~sl1m_ctx()
 struct ProblemDev {
     DevSide vis, pix;
     DBuf<int2> ant;
+    DBuf<int> vslot, gnb;
+    DBuf<int2> gbl;
     DBuf<double2> V;
     DBuf<float4> pgauss;
     DBuf<d4> pgauss64;
@@ -458,7 +447,7 @@ int sl1m_problem::rebuild(cudaStream_t st)
         for (int64_t k = 0; k < n_vis; ++k) members[k] = (int)k;
         std::vector<int> order;
         kd_append(order, std::move(members), uvw.data(), uvw.data() + 1, 3);
-        if (n_ant > 0) spread_antennas(order, ant);
+        if (n_ant > 0) sort_baselines(order, ant);
         std::vector<d4> xyz(n_vis);
         for (int64_t k = 0; k < n_vis; ++k)
             xyz[k] = make_d4(uvw[3 * k], uvw[3 * k + 1], uvw[3 * k + 2], weights.empty() ? 1.0 : weights[k]);
@@ -477,6 +466,32 @@ int sl1m_problem::rebuild(cudaStream_t st)
         CK(D.ant.upload(a.data(), a.size(), st));
         CK(D.V.upload(Vs.data(), Vs.size(), st));
         vis_orig = H.orig;
+        if (n_ant > 0) {
+            // each granule's distinct antenna pairs (adjacent after sort_baselines)
+            std::vector<int> vslot(H.n_pad, 0), gnb(H.n_gran, 0);
+            std::vector<int2> gbl((size_t)H.n_gran * NB_MAX, make_int2(0, 0));
+            for (int g = 0; g < H.n_gran; ++g) {
+                int nb = 0;
+                bool over = false;
+                for (int i = g * G; i < (g + 1) * G; ++i) {
+                    const int2 ab = a[i];
+                    if (nb == 0 || ab.x != gbl[(size_t)g * NB_MAX + nb - 1].x ||
+                        ab.y != gbl[(size_t)g * NB_MAX + nb - 1].y) {
+                        if (nb == NB_MAX) { over = true; break; }
+                        gbl[(size_t)g * NB_MAX + nb++] = ab;
+                    }
+                    vslot[i] = nb - 1;
+                }
+                gnb[g] = over ? 0 : nb;
+            }
+            CK(D.vslot.upload(vslot.data(), vslot.size(), st));
+            CK(D.gbl.upload(gbl.data(), gbl.size(), st));
+            CK(D.gnb.upload(gnb.data(), gnb.size(), st));
+        } else {
+            D.vslot.free();
+            D.gbl.free();
+            D.gnb.free();
+        }
     }
     // ---- pixels: classes of equal (kind, sigma), each in k-d order on (l, m)
     {
@@ -557,6 +572,9 @@ int sl1m_problem::rebuild(cudaStream_t st)
         }
     }
     hp.ant = D.ant.p;
+    hp.vslot = n_ant > 0 ? D.vslot.p : nullptr;
+    hp.gbl = n_ant > 0 ? D.gbl.p : nullptr;
+    hp.gnb = n_ant > 0 ? D.gnb.p : nullptr;
     hp.V = D.V.p;
     hp.pgauss = D.pgauss.p;
     hp.pgauss64 = D.pgauss64.p;
@@ -594,11 +612,10 @@ const UnitCost& sl1m_problem::unit_cost(int precision, int op)
     ucost_ok[precision][op] = true;
     uc.unit.clear();
     // cost of a Gaussian pair relative to a Dirac pair of the same launch,
-    // measured on GB300 (128x128 pixels x 32,000 visibilities, one kind at a
-    // time): forward 1.45, adjoint 1.6 without gains; 1.23 and 1.3 with gains
-    // (the gains gather weighs on both kinds alike)
+    // measured on GB300 (4 x 128x128 pixels of one kind x 32,000 visibilities):
+    // forward 1.53, adjoint 1.60 without gains; 1.34 and 1.45 with gains
     const double gfac = n_ant > 0 ? 2.0 : 1.0;
-    const double gcost = n_ant > 0 ? (op == 0 ? 1.23 : 1.3) : (op == 0 ? 1.45 : 1.6);
+    const double gcost = n_ant > 0 ? (op == 0 ? 1.34 : 1.45) : (op == 0 ? 1.53 : 1.60);
     const auto base = [gcost](int kind) { return kind == DIRAC ? 1.0 : gcost; };
     int k0 = gkind_pix.empty() ? 0 : gkind_pix[0];
     bool one_kind = true;
@@ -639,7 +656,10 @@ size_t sl1m_problem::estimate_bytes() const
 {
     const size_t nv = (size_t)((n_vis + G - 1) / G) * G, np = (size_t)((n_pix + G - 1) / G) * G;
     size_t b = nv * (4 * 16 + 32 + 4 + 8 + 16) + np * (4 * 16 + 32 + 4 + 16 + 32);
-    if (n_ant > 0) b += (size_t)gain_rows(n_ant) * GP * (np / G) * 8 + (size_t)n_ant * np * 16;   // FP32 + FP64
+    if (n_ant > 0) {
+        b += (size_t)gain_rows(n_ant) * GP * (np / G) * 8 + (size_t)n_ant * np * 16;   // FP32 + FP64
+        b += nv * 4 + (nv / G) * (NB_MAX * 8 + 4);                                     // pair lists
+    }
     b += np * 8 * 4 + nv * 16 * 3;                 // solver vectors
     b += (nv + np) * 16 * 3;                       // operator scratch
     return b + (1 << 16);
@@ -760,7 +780,7 @@ size_t sl1m_problem::dev_bytes() const
     };
     side(D.vis);
     side(D.pix);
-    b += D.ant.bytes() + D.V.bytes() + D.pgauss.bytes() + D.pgauss64.bytes() + D.gsig.bytes() +
+    b += D.ant.bytes() + D.vslot.bytes() + D.gbl.bytes() + D.gnb.bytes() + D.V.bytes() + D.pgauss.bytes() + D.pgauss64.bytes() + D.gsig.bytes() +
          D.gsig64.bytes() + D.gkind.bytes() + D.gains32.bytes() + D.gains64.bytes();
     b += D.x_user.bytes() + D.x_sorted.bytes() + D.adj_sorted.bytes() + D.img_user.bytes() +
          D.r_user.bytes() + D.r_sorted.bytes() + D.fwd_sorted.bytes() + D.vis_user.bytes();

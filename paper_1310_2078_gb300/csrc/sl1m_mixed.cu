@@ -144,12 +144,118 @@ __device__ __forceinline__ void fwd_gauss_tile(const float4* __restrict__ s_off,
     }
 }
 
+// ---- forward with gains through the granule's pair table
+// T[s][jj] = a_j G_{j a_s} conj(G_{j b_s}) (a_j = x_j / n_j, j = c0 + jj) for
+// the nb distinct antenna pairs (a_s, b_s) of the warp's visibility granule
+// and BT_CH pixels of the streamed granule; rows of BT_P, so the lanes of a
+// half-warp (one pair, consecutive pixels) write distinct banks.
+__device__ __forceinline__ void build_pair_table(float2* __restrict__ T, const int2* __restrict__ bl, int nb,
+                                                 const float4* __restrict__ s_off,
+                                                 const float2* __restrict__ gtab, int c0, int lane)
+{
+    for (int e = lane; e < nb * BT_CH; e += 32) {
+        const int s = e / BT_CH, jj = e % BT_CH, j = c0 + jj;
+        const int2 ab = bl[s];
+        const float2 ga = gtab[ab.x * GP + j], gb = gtab[ab.y * GP + j];
+        const float a = s_off[j].w;
+        T[s * BT_P + jj] = make_float2(a * fmaf(ga.x, gb.x, ga.y * gb.y), a * fmaf(ga.y, gb.x, -ga.x * gb.y));
+    }
+}
+
+// Dirac tile with gains from the pair table: per pair one table load (the
+// visibility's row toff = slot * BT_P) replaces two gathers and the complex
+// product of the gains.
+template <bool EXACT>
+__device__ __forceinline__ void fwd_dirac_tile_pt(const float4* __restrict__ s_off,
+                                                  const float4* __restrict__ s_lo,
+                                                  const float* __restrict__ sB,
+                                                  const float2* __restrict__ gtab, float2* __restrict__ T,
+                                                  const int2* __restrict__ bl, int nb, const int (&toff)[2],
+                                                  const float4 (&dx)[2], const float4 (&dxl)[2], int lane,
+                                                  float (&sr)[2], float (&si)[2])
+{
+#pragma unroll 1
+    for (int c0 = 0; c0 < G; c0 += BT_CH) {
+        build_pair_table(T, bl, nb, s_off, gtab, c0, lane);
+        __syncwarp();
+#pragma unroll 4
+        for (int jj = 0; jj < BT_CH; ++jj) {
+            const int j = c0 + jj;
+            const float4 o = s_off[j];
+            const float b = sB[j];
+            const float4 ol = EXACT ? s_lo[j] : o;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                float ph;
+                if (EXACT) ph = frac_turns(fmaf(b, INV_TWO_PI_F, frac_dot3(dx[r], dxl[r], o, ol))) * TWO_PI_F;
+                else ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, b)));
+                float sn, cs;
+                __sincosf(ph, &sn, &cs);
+                const float2 t = T[toff[r] + jj];                      // a g
+                sr[r] = fmaf(t.x, cs, fmaf(t.y, sn, sr[r]));          // a g (cs - i sn)
+                si[r] = fmaf(t.y, cs, fmaf(-t.x, sn, si[r]));
+            }
+        }
+        __syncwarp();                                                  // table free for the next chunk
+    }
+}
+
+template <bool EXACT, bool PAR>
+__device__ __forceinline__ void fwd_gauss_tile_pt(const float4* __restrict__ s_off,
+                                                  const float4* __restrict__ s_lo,
+                                                  const float4* __restrict__ s_pg,
+                                                  const float* __restrict__ sB,
+                                                  const float2* __restrict__ gtab, float2* __restrict__ T,
+                                                  const int2* __restrict__ bl, int nb, const int (&toff)[2],
+                                                  const float4 (&xh)[2], const float4 (&dx)[2],
+                                                  const float4 (&dxl)[2], const GaussConst (&gc)[2], int lane,
+                                                  float (&sr)[2], float (&si)[2])
+{
+#pragma unroll 1
+    for (int c0 = 0; c0 < G; c0 += BT_CH) {
+        build_pair_table(T, bl, nb, s_off, gtab, c0, lane);
+        __syncwarp();
+#pragma unroll 2
+        for (int jj = 0; jj < BT_CH; ++jj) {
+            const int j = c0 + jj;
+            const float4 o = s_off[j];
+            const float4 pg = s_pg[j];
+            const float b = sB[j];
+            const float4 ol = EXACT ? s_lo[j] : o;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const float wf = xh[r].z;
+                const float t = fmaf(xh[r].x, pg.x, fmaf(xh[r].y, pg.y, -wf * pg.z));
+                float ph;
+                if (EXACT) {
+                    ph = fmaf(b, INV_TWO_PI_F, frac_dot3(dx[r], dxl[r], o, ol));
+                    ph = fmaf(-gc[r].gamr * INV_TWO_PI_F, t, ph);
+                    if (PAR) ph = fmaf(-wf, pg.w, ph);
+                    ph = frac_turns(ph) * TWO_PI_F;
+                } else {
+                    ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, b)));
+                    ph = fmaf(-gc[r].gamr, t, ph);
+                    if (PAR) ph = fmaf(-wf * TWO_PI_F, pg.w, ph);
+                }
+                float sn, cs;
+                __sincosf(ph, &sn, &cs);
+                const float amp = ex2_approx(fmaf(gc[r].k1, t, gc[r].k0));   // e^{Re(qc)}; a is in T
+                const float2 tv = T[toff[r] + jj];
+                const float ca = amp * cs, sa = amp * sn;
+                sr[r] = fmaf(tv.x, ca, fmaf(tv.y, sa, sr[r]));
+                si[r] = fmaf(tv.y, ca, fmaf(-tv.x, sa, si[r]));
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // Owned: visibilities (warp = one vis granule, lane = 2 visibilities).
 // Streamed: pixel granules through shared memory, NST per barrier pair (a
 // tile shape the autotuner picks; the gains kernel stages one, since one
 // granule's gains for all antennas already fill most of shared memory).
 template <bool GAINS, int NST, int NPOLY = 0>
-__global__ void __launch_bounds__(NTHREADS, 3)
+__global__ void __launch_bounds__(NTHREADS, GAINS ? 2 : 3)   // gains: pair-table path + gathers fit in 128
 fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ plp, double2* __restrict__ partial)
 {
     __shared__ float4 s_off[NST][G];       // {dl, dm, dn, a = x/n}
@@ -164,6 +270,9 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
     // the next granule's table is copied while the current one is in use
     extern __shared__ __align__(128) float2 s_gain[];
     __shared__ __align__(8) unsigned long long s_gbar[2];
+    // GAINS: per warp, its visibility granule's pair list and pair table
+    __shared__ int2 s_bl[GAINS ? BLK_GRAN : 1][GAINS ? NB_MAX : 1];
+    __shared__ float2 s_pt[GAINS ? BLK_GRAN : 1][GAINS ? NB_MAX * BT_P : 1];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Plan pl = *plp;
@@ -218,6 +327,16 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
             }
         }
         double tr[2] = {0.0, 0.0}, ti[2] = {0.0, 0.0};
+        int nb = 0, toff[2] = {0, 0};          // GAINS: pairs in the granule's list (0: gathers)
+        if (GAINS) {
+            if (vg_ok) nb = P.gnb[vg];
+            if (nb > 0) {
+#pragma unroll
+                for (int r = 0; r < 2; ++r) toff[r] = P.vslot[e0 + 32 * r] * BT_P;
+                if (lane < nb) s_bl[warp][lane] = P.gbl[(size_t)vg * NB_MAX + lane];
+            }
+            __syncwarp();
+        }
 
         for (int gs = g0; gs < g1; gs += NST) {
             const int ns = min(NST, g1 - gs);
@@ -278,7 +397,17 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                 for (int r = 0; r < 2; ++r) C[r] = frac_dot3(xh[r], P.vis.lo[e0 + 32 * r], yc_h, yc_l);
                 float sr[2] = {0.f, 0.f}, si[2] = {0.f, 0.f};
                 if (kind == DIRAC) {
-                    if (exact) {
+                    if (GAINS && nb > 0) {
+                        if (exact) {
+                            const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]},
+                                         dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
+                            fwd_dirac_tile_pt<true>(s_off[q], s_lo[q], s_B[warp][q], gtab, s_pt[warp], s_bl[warp], nb,
+                                                    toff, dxt, dxl, lane, sr, si);
+                        } else {
+                            fwd_dirac_tile_pt<false>(s_off[q], s_lo[q], s_B[warp][q], gtab, s_pt[warp], s_bl[warp],
+                                                     nb, toff, dx, dx, lane, sr, si);
+                        }
+                    } else if (exact) {
                         const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]}, dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
                         fwd_dirac_tile<GAINS, true>(s_off[q], s_lo[q], s_B[warp][q], gtab, dxt, dxl, ant,
                                                     sr, si);
@@ -301,7 +430,24 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                         gc[r] = gauss_const(xh[r].x, xh[r].y, xh[r].z, s_sig[q]);
                         C[r] = frac_turns(C[r] + gc[r].cphase);
                     }
-                    if (exact) {
+                    if (GAINS && nb > 0) {
+                        if (exact) {
+                            const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]},
+                                         dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
+                            if (par) fwd_gauss_tile_pt<true, true>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], gtab,
+                                                                   s_pt[warp], s_bl[warp], nb, toff, xh, dxt, dxl, gc,
+                                                                   lane, sr, si);
+                            else fwd_gauss_tile_pt<true, false>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], gtab,
+                                                                s_pt[warp], s_bl[warp], nb, toff, xh, dxt, dxl, gc,
+                                                                lane, sr, si);
+                        } else if (par) {
+                            fwd_gauss_tile_pt<false, true>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], gtab, s_pt[warp],
+                                                           s_bl[warp], nb, toff, xh, dx, dx, gc, lane, sr, si);
+                        } else {
+                            fwd_gauss_tile_pt<false, false>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], gtab, s_pt[warp],
+                                                            s_bl[warp], nb, toff, xh, dx, dx, gc, lane, sr, si);
+                        }
+                    } else if (exact) {
                         const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]}, dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
                         if (par) fwd_gauss_tile<GAINS, true, true>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], gtab,
                                                                    xh, dxt, dxl, gc, ant, sr, si);
@@ -485,16 +631,34 @@ struct SmemGain {
     __device__ float2 operator()(int a, int r) const { return tab[a * GP + lane + 32 * r]; }
 };
 
+// With gains the streamed visibilities of a granule are sorted by antenna
+// pair and carry the pair as key = a << 16 | b (in the w slot of their
+// offsets, which the adjoint does not otherwise use): g[r] = G_ja conj(G_jb)
+// for the lane's two pixels is formed once per run of equal pairs.
+template <class GF>
+__device__ __forceinline__ void pair_gains(int key, int& cur, const GF& gain, float2 (&g)[2])
+{
+    if (key == cur) return;                       // warp-uniform: every lane has the same k
+    cur = key;
+    const int a = key >> 16, b = key & 0xffff;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const float2 ga = gain(a, r), gb = gain(b, r);
+        g[r] = make_float2(fmaf(ga.x, gb.x, ga.y * gb.y), fmaf(ga.y, gb.x, -ga.x * gb.y));
+    }
+}
+
 template <bool GAINS, bool EXACT, class GF, int NPOLY = 0>
 __device__ __forceinline__ void adj_dirac_tile(const float4* __restrict__ s_off,
                                                const float4* __restrict__ s_lo,
                                                const float2* __restrict__ s_r,
-                                               const int2* __restrict__ s_ant,
                                                const float* __restrict__ sB, const GF& gain,
                                                const float (&C)[2],
                                                const float4 (&dx)[2], const float4 (&dxl)[2],
                                                float (&acc)[2])
 {
+    int cur = -1;                    // GAINS: key of the antenna pair whose products g holds
+    float2 g[2];
 #pragma unroll 1
     for (int k0 = 0; k0 < G; k0 += 4)
 #pragma unroll
@@ -504,6 +668,7 @@ __device__ __forceinline__ void adj_dirac_tile(const float4* __restrict__ s_off,
         const float b = sB[k];
         const float2 rr = s_r[k];
         const float4 ol = EXACT ? s_lo[k] : o;
+        if (GAINS) pair_gains(__float_as_int(o.w), cur, gain, g);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             float ph;                                  // radians; C and dx in radians unless EXACT
@@ -513,14 +678,9 @@ __device__ __forceinline__ void adj_dirac_tile(const float4* __restrict__ s_off,
             if (!EXACT && fma_slot<NPOLY>(kk, r)) sincos_fma(ph, sn, cs);
             else __sincosf(ph, &sn, &cs);                 // exp(+i ph) = cs + i sn
             if (GAINS) {
-                const int2 ab = s_ant[k];
-                const float2 ga = gain(ab.x, r);
-                const float2 gb = gain(ab.y, r);
-                const float gr = fmaf(ga.x, gb.x, ga.y * gb.y);
-                const float gi = fmaf(ga.y, gb.x, -ga.x * gb.y);
                 const float zr = fmaf(cs, rr.x, -sn * rr.y);
                 const float zi = fmaf(cs, rr.y, sn * rr.x);
-                acc[r] = fmaf(gr, zr, fmaf(gi, zi, acc[r]));  // Re(conj(g) z)
+                acc[r] = fmaf(g[r].x, zr, fmaf(g[r].y, zi, acc[r]));  // Re(conj(g) z)
             } else {
                 acc[r] = fmaf(cs, rr.x, fmaf(-sn, rr.y, acc[r]));
             }
@@ -532,13 +692,14 @@ template <bool GAINS, bool EXACT, bool PAR, class GF>
 __device__ __forceinline__ void adj_gauss_tile(const float4* __restrict__ s_off,
                                                const float4* __restrict__ s_lo,
                                                const float4* __restrict__ s_abs,
-                                               const int2* __restrict__ s_ant,
                                                const float* __restrict__ sB,
                                                const float4* __restrict__ s_gw, const GF& gain,
                                                const float (&C)[2],
                                                const float4 (&dx)[2], const float4 (&dxl)[2],
                                                const float4 (&pgd)[2], float (&acc)[2])
 {
+    int cur = -1;                    // GAINS: key of the antenna pair whose products g holds
+    float2 g[2];
 #pragma unroll 2
     for (int k = 0; k < G; ++k) {
         const float4 o = s_off[k];
@@ -546,6 +707,7 @@ __device__ __forceinline__ void adj_gauss_tile(const float4* __restrict__ s_off,
         const float4 gw = s_gw[k];             // {gamr, coef, r're, r'im}
         const float b = sB[k];
         const float4 ol = EXACT ? s_lo[k] : o;
+        if (GAINS) pair_gains(__float_as_int(o.w), cur, gain, g);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             // pgd = {l, m, r^2/4, pi nu}: t = u l + v m - w r^2/2
@@ -566,13 +728,8 @@ __device__ __forceinline__ void adj_gauss_tile(const float4* __restrict__ s_off,
             const float amp = ex2_approx(gw.y * fmaf(va.z, t, va.w));   // coef |(u,v) - w (l,m)|^2
             const float zr = fmaf(cs, gw.z, -sn * gw.w);
             if (GAINS) {
-                const int2 ab = s_ant[k];
-                const float2 ga = gain(ab.x, r);
-                const float2 gb = gain(ab.y, r);
-                const float gr = fmaf(ga.x, gb.x, ga.y * gb.y);
-                const float gi = fmaf(ga.y, gb.x, -ga.x * gb.y);
                 const float zi = fmaf(cs, gw.w, sn * gw.z);
-                acc[r] = fmaf(amp, fmaf(gr, zr, gi * zi), acc[r]);
+                acc[r] = fmaf(amp, fmaf(g[r].x, zr, g[r].y * zi), acc[r]);
             } else {
                 acc[r] = fmaf(amp, zr, acc[r]);
             }
@@ -590,7 +747,6 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
     __shared__ float4 s_lo[NSA][G];
     __shared__ float4 s_abs[NSA][G];            // {u, v, -2 w, u^2 + v^2} (Gaussian owners)
     __shared__ float2 s_r[NSA][G];
-    __shared__ int2 s_ant[NSA][G];      // unused without gains
     __shared__ float s_B[BLK_GRAN][NSA][G];
     __shared__ float4 s_gw[BLK_GRAN][NSA][G];   // Gaussian owners: {gamr, coef, r're, r'im}
     __shared__ float4 s_cen[NSA][3];
@@ -691,10 +847,10 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                     if (exact) {
                         const float4 dxt[2] = {P.pix.off[eidx[0]], P.pix.off[eidx[1]]},
                                  dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
-                        adj_dirac_tile<false, true>(s_off[q], s_lo[q], s_r[q], s_ant[q], s_B[warp][q], ng, C, dxt,
+                        adj_dirac_tile<false, true>(s_off[q], s_lo[q], s_r[q], s_B[warp][q], ng, C, dxt,
                                                     dxl, acc);
                     } else {
-                        adj_dirac_tile<false, false, NoGain, NPOLY>(s_off[q], s_lo[q], s_r[q], s_ant[q], s_B[warp][q],
+                        adj_dirac_tile<false, false, NoGain, NPOLY>(s_off[q], s_lo[q], s_r[q], s_B[warp][q],
                                                                     ng, Cr, dx,
                                                      dx, acc);
                     }
@@ -702,11 +858,11 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                     if (exact) {
                         const float4 dxt[2] = {P.pix.off[eidx[0]], P.pix.off[eidx[1]]},
                                  dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
-                        if (par) adj_gauss_tile<false, true, true>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[warp][q], s_gw[warp][q], ng, C, dxt, dxl, pgd, acc);
-                        else adj_gauss_tile<false, true, false>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[warp][q], s_gw[warp][q], ng, C, dxt, dxl, pgd, acc);
+                        if (par) adj_gauss_tile<false, true, true>(s_off[q], s_lo[q], s_abs[q], s_B[warp][q], s_gw[warp][q], ng, C, dxt, dxl, pgd, acc);
+                        else adj_gauss_tile<false, true, false>(s_off[q], s_lo[q], s_abs[q], s_B[warp][q], s_gw[warp][q], ng, C, dxt, dxl, pgd, acc);
                     } else {
-                        if (par) adj_gauss_tile<false, false, true>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[warp][q], s_gw[warp][q], ng, Cr, dx, dx, pgd, acc);
-                        else adj_gauss_tile<false, false, false>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[warp][q], s_gw[warp][q], ng, Cr, dx, dx, pgd, acc);
+                        if (par) adj_gauss_tile<false, false, true>(s_off[q], s_lo[q], s_abs[q], s_B[warp][q], s_gw[warp][q], ng, Cr, dx, dx, pgd, acc);
+                        else adj_gauss_tile<false, false, false>(s_off[q], s_lo[q], s_abs[q], s_B[warp][q], s_gw[warp][q], ng, Cr, dx, dx, pgd, acc);
                     }
                 }
 #pragma unroll
@@ -736,7 +892,6 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
     __shared__ float4 s_lo[BLK_GRAN][G];
     __shared__ float4 s_abs[BLK_GRAN][G];
     __shared__ float2 s_r[BLK_GRAN][G];
-    __shared__ int2 s_ant[BLK_GRAN][G];
     __shared__ float s_B[BLK_GRAN][G];
     __shared__ float4 s_gw[BLK_GRAN][G];
     __shared__ float4 s_cen[BLK_GRAN][3];
@@ -808,12 +963,14 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
                 for (int t = threadIdx.x; t < ns * G; t += NTHREADS) {
                     const int q = t / G, i = t % G;
                     const int e = (gs + q) * G + i;
-                    s_off[q][i] = P.vis.off[e];
+                    float4 o = P.vis.off[e];
+                    const int2 ab = P.ant[e];
+                    o.w = __int_as_float(ab.x << 16 | ab.y);   // the pair key (pair_gains)
+                    s_off[q][i] = o;
                     s_lo[q][i] = P.vis.offlo[e];
                     s_abs[q][i] = vis_for_gauss(P.vis.hi[e]);
                     const double2 rr = R[e];
                     s_r[q][i] = make_float2((float)rr.x, (float)rr.y);
-                    s_ant[q][i] = P.ant[e];
                 }
                 if (threadIdx.x < ns) {
                     const int g = gs + threadIdx.x;
@@ -849,19 +1006,19 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
                     if (exact) {
                         const float4 dxt[2] = {P.pix.off[eidx[0]], P.pix.off[eidx[1]]},
                                  dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
-                        adj_dirac_tile<true, true>(s_off[q], s_lo[q], s_r[q], s_ant[q], s_B[q], sg, C, dxt, dxl, acc);
+                        adj_dirac_tile<true, true>(s_off[q], s_lo[q], s_r[q], s_B[q], sg, C, dxt, dxl, acc);
                     } else {
-                        adj_dirac_tile<true, false>(s_off[q], s_lo[q], s_r[q], s_ant[q], s_B[q], sg, Cr, dx, dx, acc);
+                        adj_dirac_tile<true, false>(s_off[q], s_lo[q], s_r[q], s_B[q], sg, Cr, dx, dx, acc);
                     }
                 } else {
                     if (exact) {
                         const float4 dxt[2] = {P.pix.off[eidx[0]], P.pix.off[eidx[1]]},
                                  dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
-                        if (par) adj_gauss_tile<true, true, true>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[q], s_gw[q], sg, C, dxt, dxl, pgd, acc);
-                        else adj_gauss_tile<true, true, false>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[q], s_gw[q], sg, C, dxt, dxl, pgd, acc);
+                        if (par) adj_gauss_tile<true, true, true>(s_off[q], s_lo[q], s_abs[q], s_B[q], s_gw[q], sg, C, dxt, dxl, pgd, acc);
+                        else adj_gauss_tile<true, true, false>(s_off[q], s_lo[q], s_abs[q], s_B[q], s_gw[q], sg, C, dxt, dxl, pgd, acc);
                     } else {
-                        if (par) adj_gauss_tile<true, false, true>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[q], s_gw[q], sg, Cr, dx, dx, pgd, acc);
-                        else adj_gauss_tile<true, false, false>(s_off[q], s_lo[q], s_abs[q], s_ant[q], s_B[q], s_gw[q], sg, Cr, dx, dx, pgd, acc);
+                        if (par) adj_gauss_tile<true, false, true>(s_off[q], s_lo[q], s_abs[q], s_B[q], s_gw[q], sg, Cr, dx, dx, pgd, acc);
+                        else adj_gauss_tile<true, false, false>(s_off[q], s_lo[q], s_abs[q], s_B[q], s_gw[q], sg, Cr, dx, dx, pgd, acc);
                     }
                 }
 #pragma unroll
