@@ -146,6 +146,7 @@ struct DevProblem {
     const float* gsig;        // [pix.n_gran] sigma per pixel granule (FP32 path)
     const double* gsig64;     // [pix.n_gran] sigma per pixel granule (FP64 path)
     const int* gkind;         // [pix.n_gran] kind per pixel granule
+    const float4* pghdr;      // [pix.n_gran][4] centre hi, centre lo, extent, {sigma, kind, 0, 0}
     const float2* gains32;    // [pix.n_gran][gain_rows(n_ant)][GP] or null
     const double2* gains64;   // [pix.n_pad][n_ant] or null
     int n_ant;

@@ -94,16 +94,27 @@ __device__ __forceinline__ void fence_proxy_async_smem()
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
-// One thread: arrive on bar expecting `bytes` more, then copy `bytes`
-// (a multiple of 16; both addresses 16-byte aligned) from src to dst.
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar)
+// One thread: arrive on bar (its one expected arrival) and announce `bytes`
+// of copies that will complete on it.
+__device__ __forceinline__ void mbar_arrive_expect(unsigned long long* bar, unsigned bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
+}
+// Copy `bytes` (a multiple of 16; both addresses 16-byte aligned) from global
+// src to shared dst; completes `bytes` of bar's announced transactions.
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, unsigned long long* bar)
+{
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      smem_u32(dst)),
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
+}
+// One thread: arrive on bar expecting `bytes`, then copy them from src to dst.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar)
+{
+    mbar_arrive_expect(bar, bytes);
+    bulk_copy(dst, src, bytes, bar);
 }
 // Wait until the phase of bar with this parity has completed.  Bounded: after
 // 2^20 unsuccessful tries (each may suspend the thread for a while) it gives

@@ -390,6 +390,7 @@ struct ProblemDev {
     DBuf<float> gsig;
     DBuf<double> gsig64;
     DBuf<int> gkind;
+    DBuf<float4> pghdr;
     DBuf<float2> gains32;
     DBuf<double2> gains64;
     // operator scratch
@@ -545,6 +546,15 @@ int sl1m_problem::rebuild(cudaStream_t st)
         CK(D.gsig.upload(gs.data(), gs.size(), st));
         CK(D.gsig64.upload(gs64.data(), gs64.size(), st));
         CK(D.gkind.upload(gk.data(), gk.size(), st));
+        // per pixel granule, as the forward's bulk copies take it
+        std::vector<float4> hdr((size_t)H.n_gran * 4);
+        for (int g = 0; g < H.n_gran; ++g) {
+            hdr[4 * (size_t)g] = H.cen_hi[g];
+            hdr[4 * (size_t)g + 1] = H.cen_lo[g];
+            hdr[4 * (size_t)g + 2] = H.ext[g];
+            hdr[4 * (size_t)g + 3] = make_float4(gs[g], (float)gk[g], 0.f, 0.f);
+        }
+        CK(D.pghdr.upload(hdr.data(), hdr.size(), st));
         gkind_pix = gk;
         pix_orig = H.orig;
         if (n_ant > 0) {
@@ -581,6 +591,7 @@ int sl1m_problem::rebuild(cudaStream_t st)
     hp.gsig = D.gsig.p;
     hp.gsig64 = D.gsig64.p;
     hp.gkind = D.gkind.p;
+    hp.pghdr = D.pghdr.p;
     hp.gains32 = n_ant > 0 ? D.gains32.p : nullptr;
     hp.gains64 = n_ant > 0 ? D.gains64.p : nullptr;
     hp.n_ant = n_ant;
@@ -781,7 +792,7 @@ size_t sl1m_problem::dev_bytes() const
     side(D.vis);
     side(D.pix);
     b += D.ant.bytes() + D.vslot.bytes() + D.gbl.bytes() + D.gnb.bytes() + D.V.bytes() + D.pgauss.bytes() + D.pgauss64.bytes() + D.gsig.bytes() +
-         D.gsig64.bytes() + D.gkind.bytes() + D.gains32.bytes() + D.gains64.bytes();
+         D.gsig64.bytes() + D.gkind.bytes() + D.pghdr.bytes() + D.gains32.bytes() + D.gains64.bytes();
     b += D.x_user.bytes() + D.x_sorted.bytes() + D.adj_sorted.bytes() + D.img_user.bytes() +
          D.r_user.bytes() + D.r_sorted.bytes() + D.fwd_sorted.bytes() + D.vis_user.bytes();
     b += D.I0.bytes() + D.I1.bytes() + D.y.bytes() + D.xv.bytes() + D.blk_r2.bytes() + D.blk_l1.bytes() +
@@ -1485,12 +1496,11 @@ int sl1m_autotune(sl1m_problem* prob, int precision, int32_t* nst_out, int32_t* 
         const std::vector<int> ns = {op == 0 ? d.pix.n_gran : d.vis.n_gran};
         const std::vector<const UnitCost*> uc = {&prob->unit_cost(precision, op)};
         const long long units = (long long)nb[0] * ns[0];
-        // stage 1: streamed granules per stage x CTAs per SM (0 = warp-decoupled
-        // forward: warp-private staging, no CTA barrier); stage 2: at the best of
-        // those, the share of pairs whose sincos runs on the FMA pipe
+        // stage 1: streamed granules per stage x CTAs per SM; stage 2: at the
+        // best of those, the share of pairs whose sincos runs on the FMA pipe
         std::vector<int> cands = {NST_DEFAULT};
         const bool mixed_plain = precision == SL1M_MIXED && !gains;
-        if (mixed_plain) cands = op == 0 ? std::vector<int>{0, 2, 4, 8} : std::vector<int>{2, 4, 8};
+        if (mixed_plain) cands = {2, 4, 8};
         float best = 1e30f;
         int bcode = NST_DEFAULT, bk = 0;
         const auto time_shape = [&](int code, int k) -> float {
@@ -1523,7 +1533,7 @@ int sl1m_autotune(sl1m_problem* prob, int precision, int32_t* nst_out, int32_t* 
                 if (rc == SL1M_OK && ms < best) { best = ms; bcode = nst; bk = k; }
             }
         }
-        if (mixed_plain && bcode != 0) {
+        if (mixed_plain) {
             const int nst = bcode, k0 = bk;       // stage-1 choice (npoly 0)
             for (int npoly = 1; npoly <= 2 && rc == SL1M_OK; ++npoly) {
                 const int code = shape_code(nst, npoly);
@@ -1556,8 +1566,8 @@ int sl1m_set_tile_shape(sl1m_problem* prob, int precision, int op, int nst, int 
     const bool gains = prob->n_ant > 0;
     if (op < 0 || op > 1 || ctas_per_sm < 1 || npoly < 0 || npoly > 2)
         return sl1m_fail(ctx, SL1M_ERR_ARG, "bad tile shape (op %d, ctas/SM %d, npoly %d)", op, ctas_per_sm, npoly);
-    if (!(nst == 2 || nst == 4 || nst == 8 || (nst == 0 && op == 0 && npoly == 0)))
-        return sl1m_fail(ctx, SL1M_ERR_ARG, "nst must be 2, 4 or 8 (or 0 for the forward, npoly 0)");
+    if (!(nst == 2 || nst == 4 || nst == 8))
+        return sl1m_fail(ctx, SL1M_ERR_ARG, "nst must be 2, 4 or 8");
     if ((gains || precision == SL1M_FP64) && (nst != NST_DEFAULT || npoly != 0))
         return sl1m_fail(ctx, SL1M_ERR_ARG, "with gains or in FP64 only the CTAs per SM can be set");
     RET(prob->rebuild(ctx->stream));

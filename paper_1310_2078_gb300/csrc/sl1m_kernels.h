@@ -9,12 +9,11 @@ enum FinishMode : int { FIN_OP = 0, FIN_POWER = 1, FIN_SOLVE = 2, FIN_INIT = 3 }
 // operator kernels (sl1m_mixed.cu, sl1m_fp64.cu); precision 0 = FP64, 1 = mixed.
 // plp: device-resident plan; C: its grid size (known on the host).
 // nst: streamed granules per shared-memory stage of the mixed no-gains
-// kernels (2, 4 or 8; the tile shape the autotuner picks); for the forward,
-// 0 selects the warp-decoupled kernel (each warp stages for itself).
+// kernels (2, 4 or 8; the tile shape the autotuner picks).
 constexpr int NST_DEFAULT = 4;
-// Tile-shape code carried as `nst` below: streamed granules per stage (2, 4,
-// 8, or 0 for the warp-decoupled forward) plus 16 x npoly, the pairs of every
-// 8 whose sincos runs on the FMA pipe (0, 1 or 2; Dirac tiles without gains).
+// Tile-shape code carried as `nst` below: streamed granules per stage (2, 4
+// or 8) plus 16 x npoly, the pairs of every 8 whose sincos runs on the FMA
+// pipe (0, 1 or 2; Dirac tiles without gains).
 constexpr int shape_code(int nst, int npoly) { return nst | (npoly << 4); }
 constexpr int shape_nst(int code) { return code & 15; }
 constexpr int shape_npoly(int code) { return code >> 4; }
@@ -24,7 +23,7 @@ cudaError_t launch_adjoint(int precision, bool gains, int n_ant, const DevProble
                            double* partial, cudaStream_t st, int nst = NST_DEFAULT);
 // which: 0 fwd fp64, 1 adj fp64, 2 fwd mixed, 3 adj mixed
 int occupancy(int which, bool gains, int n_ant, int nst = NST_DEFAULT);
-int fwd_smem_bytes(int n_ant, bool gains);
+int fwd_smem_bytes(int n_ant, bool gains, int nst);
 // The mixed gains kernels' bounded waits for their bulk copies set a device
 // flag when they give up; read it into *host_flag (asynchronously on st: valid
 // after the stream is synchronised) and clear it.

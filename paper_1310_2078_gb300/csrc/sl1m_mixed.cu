@@ -55,7 +55,7 @@ __device__ __forceinline__ constexpr bool fma_slot(int jj, int r) { return 2 * j
 template <bool GAINS, bool EXACT, int NPOLY = 0>
 __device__ __forceinline__ void fwd_dirac_tile(const float4* __restrict__ s_off,
                                                const float4* __restrict__ s_lo,
-                                               const float* __restrict__ sB,
+                                               const float2* __restrict__ sBa,
                                                const float2* __restrict__ s_gain,
                                                const float4 (&dx)[2], const float4 (&dxl)[2],
                                                const int2 (&ant)[2], float (&sr)[2], float (&si)[2])
@@ -67,8 +67,9 @@ __device__ __forceinline__ void fwd_dirac_tile(const float4* __restrict__ s_off,
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) {
         const int j = j0 + jj;
-        const float4 o = s_off[j];             // {dl, dm, dn, a = x/n}
-        const float b = sB[j];                 // B_j in radians
+        const float4 o = s_off[j];             // {dl, dm, dn, -}
+        const float2 ba = sBa[j];              // {B_j in radians, a_j = x_j / n_j}
+        const float b = ba.x;
         const float4 ol = EXACT ? s_lo[j] : o;
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
@@ -83,11 +84,11 @@ __device__ __forceinline__ void fwd_dirac_tile(const float4* __restrict__ s_off,
                 const float2 gb = gb_row[r][j];
                 const float gr = fmaf(ga.x, gb.x, ga.y * gb.y);    // G_a conj(G_b)
                 const float gi = fmaf(ga.y, gb.x, -ga.x * gb.y);
-                sr[r] = fmaf(o.w, fmaf(gr, cs, gi * sn), sr[r]);    // a g (cs - i sn)
-                si[r] = fmaf(o.w, fmaf(gi, cs, -gr * sn), si[r]);
+                sr[r] = fmaf(ba.y, fmaf(gr, cs, gi * sn), sr[r]);    // a g (cs - i sn)
+                si[r] = fmaf(ba.y, fmaf(gi, cs, -gr * sn), si[r]);
             } else {
-                sr[r] = fmaf(o.w, cs, sr[r]);
-                si[r] = fmaf(-o.w, sn, si[r]);
+                sr[r] = fmaf(ba.y, cs, sr[r]);
+                si[r] = fmaf(-ba.y, sn, si[r]);
             }
         }
     }
@@ -97,7 +98,7 @@ template <bool GAINS, bool EXACT, bool PAR>
 __device__ __forceinline__ void fwd_gauss_tile(const float4* __restrict__ s_off,
                                                const float4* __restrict__ s_lo,
                                                const float4* __restrict__ s_pg,
-                                               const float* __restrict__ sB,
+                                               const float2* __restrict__ sBa,
                                                const float2* __restrict__ s_gain,
                                                const float4 (&xh)[2], const float4 (&dx)[2],
                                                const float4 (&dxl)[2], const GaussConst (&gc)[2],
@@ -109,7 +110,8 @@ __device__ __forceinline__ void fwd_gauss_tile(const float4* __restrict__ s_off,
     for (int j = 0; j < G; ++j) {
         const float4 o = s_off[j];
         const float4 pg = s_pg[j];             // {l, m, r^2/2, nu}
-        const float b = sB[j];
+        const float2 ba = sBa[j];
+        const float b = ba.x;
         const float4 ol = EXACT ? s_lo[j] : o;
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
@@ -128,7 +130,7 @@ __device__ __forceinline__ void fwd_gauss_tile(const float4* __restrict__ s_off,
             }
             float sn, cs;
             __sincosf(ph, &sn, &cs);
-            const float amp = o.w * ex2_approx(fmaf(gc[r].k1, t, gc[r].k0));   // (x/n) e^{Re(qc)}
+            const float amp = ba.y * ex2_approx(fmaf(gc[r].k1, t, gc[r].k0));   // (x/n) e^{Re(qc)}
             if (GAINS) {
                 const float2 ga = ga_row[r][j];
                 const float2 gb = gb_row[r][j];
@@ -150,14 +152,14 @@ __device__ __forceinline__ void fwd_gauss_tile(const float4* __restrict__ s_off,
 // and BT_CH pixels of the streamed granule; rows of BT_P, so the lanes of a
 // half-warp (one pair, consecutive pixels) write distinct banks.
 __device__ __forceinline__ void build_pair_table(float2* __restrict__ T, const int2* __restrict__ bl, int nb,
-                                                 const float4* __restrict__ s_off,
+                                                 const float2* __restrict__ sBa,
                                                  const float2* __restrict__ gtab, int c0, int lane)
 {
     for (int e = lane; e < nb * BT_CH; e += 32) {
         const int s = e / BT_CH, jj = e % BT_CH, j = c0 + jj;
         const int2 ab = bl[s];
         const float2 ga = gtab[ab.x * GP + j], gb = gtab[ab.y * GP + j];
-        const float a = s_off[j].w;
+        const float a = sBa[j].y;
         T[s * BT_P + jj] = make_float2(a * fmaf(ga.x, gb.x, ga.y * gb.y), a * fmaf(ga.y, gb.x, -ga.x * gb.y));
     }
 }
@@ -168,7 +170,7 @@ __device__ __forceinline__ void build_pair_table(float2* __restrict__ T, const i
 template <bool EXACT>
 __device__ __forceinline__ void fwd_dirac_tile_pt(const float4* __restrict__ s_off,
                                                   const float4* __restrict__ s_lo,
-                                                  const float* __restrict__ sB,
+                                                  const float2* __restrict__ sBa,
                                                   const float2* __restrict__ gtab, float2* __restrict__ T,
                                                   const int2* __restrict__ bl, int nb, const int (&toff)[2],
                                                   const float4 (&dx)[2], const float4 (&dxl)[2], int lane,
@@ -176,13 +178,13 @@ __device__ __forceinline__ void fwd_dirac_tile_pt(const float4* __restrict__ s_o
 {
 #pragma unroll 1
     for (int c0 = 0; c0 < G; c0 += BT_CH) {
-        build_pair_table(T, bl, nb, s_off, gtab, c0, lane);
+        build_pair_table(T, bl, nb, sBa, gtab, c0, lane);
         __syncwarp();
 #pragma unroll 4
         for (int jj = 0; jj < BT_CH; ++jj) {
             const int j = c0 + jj;
             const float4 o = s_off[j];
-            const float b = sB[j];
+            const float b = sBa[j].x;
             const float4 ol = EXACT ? s_lo[j] : o;
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
@@ -204,7 +206,7 @@ template <bool EXACT, bool PAR>
 __device__ __forceinline__ void fwd_gauss_tile_pt(const float4* __restrict__ s_off,
                                                   const float4* __restrict__ s_lo,
                                                   const float4* __restrict__ s_pg,
-                                                  const float* __restrict__ sB,
+                                                  const float2* __restrict__ sBa,
                                                   const float2* __restrict__ gtab, float2* __restrict__ T,
                                                   const int2* __restrict__ bl, int nb, const int (&toff)[2],
                                                   const float4 (&xh)[2], const float4 (&dx)[2],
@@ -213,14 +215,14 @@ __device__ __forceinline__ void fwd_gauss_tile_pt(const float4* __restrict__ s_o
 {
 #pragma unroll 1
     for (int c0 = 0; c0 < G; c0 += BT_CH) {
-        build_pair_table(T, bl, nb, s_off, gtab, c0, lane);
+        build_pair_table(T, bl, nb, sBa, gtab, c0, lane);
         __syncwarp();
 #pragma unroll 2
         for (int jj = 0; jj < BT_CH; ++jj) {
             const int j = c0 + jj;
             const float4 o = s_off[j];
             const float4 pg = s_pg[j];
-            const float b = sB[j];
+            const float b = sBa[j].x;
             const float4 ol = EXACT ? s_lo[j] : o;
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
@@ -250,46 +252,82 @@ __device__ __forceinline__ void fwd_gauss_tile_pt(const float4* __restrict__ s_o
     }
 }
 
+// Forward stage buffers in dynamic shared memory: two of them, each holding
+// NST streamed pixel granules as they sit in HBM -- offsets {dl, dm, dn, 1/n},
+// offset residuals, Gaussian data {l, m, r^2/2, nu}, x (FP64) and the granule
+// headers {centre hi, centre lo, extent, {sigma, kind}} -- filled by bulk (TMA)
+// copies that complete on one mbarrier per buffer.  The copies of stage s + 1
+// are issued when stage s starts, so they land while stage s is computed.
+template <int NST>
+struct FwdStage {
+    static constexpr int OFF = 0;                          // float4 [NST][G]
+    static constexpr int LO = OFF + NST * G * 16;          // float4 [NST][G]
+    static constexpr int PG = LO + NST * G * 16;           // float4 [NST][G]
+    static constexpr int X = PG + NST * G * 16;            // double [NST][G]
+    static constexpr int HDR = X + NST * G * 8;            // float4 [NST][4]
+    static constexpr int BYTES = HDR + NST * 64;           // a multiple of 16
+};
+template <int NST>
+constexpr int fwd_stage_bytes() { return 2 * FwdStage<NST>::BYTES; }
+
+// One thread: copy the ns granules from gs of P's pixel side (the forward
+// input X) into stage buffer `buf`, completing on bar.
+template <int NST>
+__device__ __forceinline__ void fwd_stage_load(unsigned char* buf, const DevProblem& P, const double* X, int gs,
+                                               int ns, unsigned long long* bar)
+{
+    using S = FwdStage<NST>;
+    const size_t e = (size_t)gs * G;
+    const unsigned n4 = (unsigned)(ns * G * 16), n8 = (unsigned)(ns * G * 8), nh = (unsigned)(ns * 64);
+    fence_proxy_async_smem();              // the buffer's last readers (generic proxy) are done
+    mbar_arrive_expect(bar, 3 * n4 + n8 + nh);
+    bulk_copy(buf + S::OFF, P.pix.off + e, n4, bar);
+    bulk_copy(buf + S::LO, P.pix.offlo + e, n4, bar);
+    bulk_copy(buf + S::PG, P.pgauss + e, n4, bar);
+    bulk_copy(buf + S::X, X + e, n8, bar);
+    bulk_copy(buf + S::HDR, P.pghdr + (size_t)gs * 4, nh, bar);
+}
+
 // Owned: visibilities (warp = one vis granule, lane = 2 visibilities).
-// Streamed: pixel granules through shared memory, NST per barrier pair (a
-// tile shape the autotuner picks; the gains kernel stages one, since one
-// granule's gains for all antennas already fill most of shared memory).
+// Streamed: pixel granules through the stage buffers, NST per stage (a tile
+// shape the autotuner picks; the gains kernel stages one, since one granule's
+// gains for all antennas already fill most of shared memory).  One CTA
+// barrier per stage: it frees the buffer the next copies go to.
 template <bool GAINS, int NST, int NPOLY = 0>
 __global__ void __launch_bounds__(NTHREADS, GAINS ? 2 : 3)   // gains: pair-table path + gathers fit in 128
 fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ plp, double2* __restrict__ partial)
 {
-    __shared__ float4 s_off[NST][G];       // {dl, dm, dn, a = x/n}
-    __shared__ float4 s_lo[NST][G];        // offset residuals
-    __shared__ float4 s_pg[NST][G];        // {l, m, r^2/2, nu}
-    __shared__ float s_B[BLK_GRAN][NST][G];   // B_j in radians
-    __shared__ float4 s_cen[NST][3];       // centre hi, lo, extent
-    __shared__ int s_kind[NST];
-    __shared__ float s_sig[NST];
-    // GAINS: one or two buffers of a pixel granule's gains [gain_rows(n_ant)][GP],
-    // each filled by a bulk (TMA) copy that completes on its mbarrier; with two,
-    // the next granule's table is copied while the current one is in use
-    extern __shared__ __align__(128) float2 s_gain[];
-    __shared__ __align__(8) unsigned long long s_gbar[2];
+    using S = FwdStage<NST>;
+    // dynamic: [stage buffer 0][stage buffer 1][GAINS: one or two gains tables
+    // [gain_rows(n_ant)][GP], each filled by a bulk copy; with two, the next
+    // granule's table is copied while the current one is in use]
+    extern __shared__ __align__(128) unsigned char s_dyn[];
+    __shared__ float2 s_Ba[BLK_GRAN][NST][G];            // per warp: {B_j in radians, a_j = x_j / n_j}
+    __shared__ __align__(8) unsigned long long s_sbar[2];   // stage buffers
+    __shared__ __align__(8) unsigned long long s_gbar[2];   // GAINS: gains tables
     // GAINS: per warp, its visibility granule's pair list and pair table
     __shared__ int2 s_bl[GAINS ? BLK_GRAN : 1][GAINS ? NB_MAX : 1];
     __shared__ float2 s_pt[GAINS ? BLK_GRAN : 1][GAINS ? NB_MAX * BT_P : 1];
+    float2* const s_gain = reinterpret_cast<float2*>(s_dyn + 2 * S::BYTES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Plan pl = *plp;
     const long long c = blockIdx.x;
     long long u, u_end;
     cta_range(pl, c, u, u_end);
-    unsigned gpar = 0;        // GAINS: parity of the next wait on buffer b (bit b)
-    int gcur = 0;             // GAINS: buffer of the current stage when double-buffered
-    bool gfault = false;      // GAINS: a bounded wait gave up
-    if (GAINS) {
-        if (threadIdx.x == 0) {
-            mbar_init(&s_gbar[0], 1);
-            mbar_init(&s_gbar[1], 1);
-            fence_mbar_init();
-        }
-        __syncthreads();
+    int scur = 0;             // stage buffer of the current stage
+    unsigned spar = 0;        // parity of the next wait on stage buffer b (bit b)
+    unsigned gpar = 0;        // GAINS: parity of the next wait on gains buffer b (bit b)
+    int gcur = 0;             // GAINS: gains buffer of the current stage when double-buffered
+    bool fault = false;       // a bounded wait gave up
+    if (threadIdx.x == 0) {
+        mbar_init(&s_sbar[0], 1);
+        mbar_init(&s_sbar[1], 1);
+        mbar_init(&s_gbar[0], 1);
+        mbar_init(&s_gbar[1], 1);
+        fence_mbar_init();
     }
+    __syncthreads();
 
     while (u < u_end) {
         const int p = find_prob(pl, u);
@@ -309,7 +347,10 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
         const int e0 = (vg_ok ? vg : 0) * G + lane;     // this lane's visibilities: e0, e0 + 32
         const int gtab_n = GAINS ? gain_rows(P.n_ant) * GP : 0;                 // float2 per table
         const unsigned gbytes = (unsigned)gtab_n * (unsigned)sizeof(float2);
-        const bool gdbl = GAINS && 2u * gbytes <= dyn_smem_bytes();
+        const bool gdbl = GAINS && 2u * gbytes <= dyn_smem_bytes() - 2u * S::BYTES;
+        // the range's first stage; its buffer's last readers finished before
+        // the barrier of the previous range's last stage
+        if (threadIdx.x == 0) fwd_stage_load<NST>(s_dyn + scur * S::BYTES, P, X, g0, min(NST, g1 - g0), &s_sbar[scur]);
 
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 xh[2] = {z4, z4}, dx[2] = {z4, z4};
@@ -340,58 +381,58 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
 
         for (int gs = g0; gs < g1; gs += NST) {
             const int ns = min(NST, g1 - gs);
-            __syncthreads();                       // previous stage consumed
-            if (GAINS && threadIdx.x == 0) {
-                // the buffers' last readers (generic proxy) are done: order them
-                // before the copies' writes (async proxy)
-                fence_proxy_async_smem();
-                const int b = gdbl ? gcur : 0;
-                if (gs == g0 || !gdbl)
-                    bulk_load(s_gain + b * gtab_n, P.gains32 + (size_t)gs * gtab_n, gbytes, &s_gbar[b]);
-                if (gdbl && gs + 1 < g1)          // prefetch the next granule's table
-                    bulk_load(s_gain + (b ^ 1) * gtab_n, P.gains32 + (size_t)(gs + 1) * gtab_n, gbytes,
-                              &s_gbar[b ^ 1]);
+            __syncthreads();                       // the previous stage is consumed
+            if (threadIdx.x == 0) {
+                if (gs + NST < g1)                 // prefetch the next stage
+                    fwd_stage_load<NST>(s_dyn + (scur ^ 1) * S::BYTES, P, X, gs + NST, min(NST, g1 - gs - NST),
+                                        &s_sbar[scur ^ 1]);
+                if (GAINS) {
+                    const int b = gdbl ? gcur : 0;
+                    fence_proxy_async_smem();
+                    if (gs == g0 || !gdbl)
+                        bulk_load(s_gain + b * gtab_n, P.gains32 + (size_t)gs * gtab_n, gbytes, &s_gbar[b]);
+                    if (gdbl && gs + 1 < g1)      // prefetch the next granule's table
+                        bulk_load(s_gain + (b ^ 1) * gtab_n, P.gains32 + (size_t)(gs + 1) * gtab_n, gbytes,
+                                  &s_gbar[b ^ 1]);
+                }
             }
-            for (int t = threadIdx.x; t < ns * G; t += NTHREADS) {
-                const int q = t / G, i = t % G;
-                const int g = gs + q;
-                const int e = g * G + i;
-                float4 o = P.pix.off[e];
-                o.w = (float)(X[e] * P.pix.d[e].w);     // x / n (0 on padding)
-                s_off[q][i] = o;
-                s_lo[q][i] = P.pix.offlo[e];
-                if (P.gkind[g] != DIRAC) s_pg[q][i] = P.pgauss[e];
-            }
-            if (threadIdx.x < ns) {
-                const int g = gs + threadIdx.x;
-                s_cen[threadIdx.x][0] = P.pix.cen_hi[g];
-                s_cen[threadIdx.x][1] = P.pix.cen_lo[g];
-                s_cen[threadIdx.x][2] = P.pix.ext[g];
-                s_kind[threadIdx.x] = P.gkind[g];
-                s_sig[threadIdx.x] = P.gsig[g];
-            }
-            __syncthreads();
+            if (!mbar_wait(&s_sbar[scur], (spar >> scur) & 1u)) fault = true;
+            spar ^= 1u << scur;
+            const unsigned char* sb = s_dyn + scur * S::BYTES;
+            const float4* s_off = reinterpret_cast<const float4*>(sb + S::OFF);
+            const float4* s_lo = reinterpret_cast<const float4*>(sb + S::LO);
+            const float4* s_pg = reinterpret_cast<const float4*>(sb + S::PG);
+            const double* s_x = reinterpret_cast<const double*>(sb + S::X);
+            const float4* s_hdr = reinterpret_cast<const float4*>(sb + S::HDR);
+            scur ^= 1;
             const float2* gtab = s_gain;
             if (GAINS) {
                 const int b = gdbl ? gcur : 0;
-                if (!mbar_wait(&s_gbar[b], (gpar >> b) & 1u)) gfault = true;
+                if (!mbar_wait(&s_gbar[b], (gpar >> b) & 1u)) fault = true;
                 gpar ^= 1u << b;
                 gtab = s_gain + b * gtab_n;
                 if (gdbl) gcur ^= 1;
             }
-            // B_j = frac(Xc . (Y_j - Yc)) for this warp's granule centre
+            // per warp: B_j = frac(Xc . (Y_j - Yc)) for its granule centre, and a_j = x_j / n_j
             for (int q = 0; q < ns; ++q) {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const int j = lane + 32 * h;
-                    s_B[warp][q][j] = frac_dot3(ch, cl, s_off[q][j], s_lo[q][j]) * TWO_PI_F;
+                    const int j = q * G + lane + 32 * h;
+                    const float4 o = s_off[j];
+                    s_Ba[warp][q][lane + 32 * h] = make_float2(frac_dot3(ch, cl, o, s_lo[j]) * TWO_PI_F,
+                                                               __double2float_rn(s_x[j]) * o.w);
                 }
             }
             __syncwarp();
             for (int q = 0; q < ns; ++q) {
-                const int kind = s_kind[q];
-                const float4 yc_h = s_cen[q][0], yc_l = s_cen[q][1];
-                const bool exact = dot3(ext, s_cen[q][2]) > D_MAX;       // warp-uniform
+                const float4 meta = s_hdr[4 * q + 3];                    // {sigma, kind, -, -}
+                const int kind = (int)meta.y;
+                const float4 yc_h = s_hdr[4 * q], yc_l = s_hdr[4 * q + 1];
+                const bool exact = dot3(ext, s_hdr[4 * q + 2]) > D_MAX;  // warp-uniform
+                const float4* q_off = s_off + q * G;
+                const float4* q_lo = s_lo + q * G;
+                const float4* q_pg = s_pg + q * G;
+                const float2* q_Ba = s_Ba[warp][q];
                 float C[2];
 #pragma unroll
                 for (int r = 0; r < 2; ++r) C[r] = frac_dot3(xh[r], P.vis.lo[e0 + 32 * r], yc_h, yc_l);
@@ -401,19 +442,18 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                         if (exact) {
                             const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]},
                                          dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
-                            fwd_dirac_tile_pt<true>(s_off[q], s_lo[q], s_B[warp][q], gtab, s_pt[warp], s_bl[warp], nb,
-                                                    toff, dxt, dxl, lane, sr, si);
+                            fwd_dirac_tile_pt<true>(q_off, q_lo, q_Ba, gtab, s_pt[warp], s_bl[warp], nb, toff, dxt,
+                                                    dxl, lane, sr, si);
                         } else {
-                            fwd_dirac_tile_pt<false>(s_off[q], s_lo[q], s_B[warp][q], gtab, s_pt[warp], s_bl[warp],
-                                                     nb, toff, dx, dx, lane, sr, si);
+                            fwd_dirac_tile_pt<false>(q_off, q_lo, q_Ba, gtab, s_pt[warp], s_bl[warp], nb, toff, dx,
+                                                     dx, lane, sr, si);
                         }
                     } else if (exact) {
-                        const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]}, dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
-                        fwd_dirac_tile<GAINS, true>(s_off[q], s_lo[q], s_B[warp][q], gtab, dxt, dxl, ant,
-                                                    sr, si);
+                        const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]},
+                                     dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
+                        fwd_dirac_tile<GAINS, true>(q_off, q_lo, q_Ba, gtab, dxt, dxl, ant, sr, si);
                     } else {
-                        fwd_dirac_tile<GAINS, false, NPOLY>(s_off[q], s_lo[q], s_B[warp][q], gtab, dx, dx, ant,
-                                                     sr, si);
+                        fwd_dirac_tile<GAINS, false, NPOLY>(q_off, q_lo, q_Ba, gtab, dx, dx, ant, sr, si);
                     }
 #pragma unroll
                     for (int r = 0; r < 2; ++r) {
@@ -427,38 +467,37 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                     GaussConst gc[2];
 #pragma unroll
                     for (int r = 0; r < 2; ++r) {
-                        gc[r] = gauss_const(xh[r].x, xh[r].y, xh[r].z, s_sig[q]);
+                        gc[r] = gauss_const(xh[r].x, xh[r].y, xh[r].z, meta.x);
                         C[r] = frac_turns(C[r] + gc[r].cphase);
                     }
                     if (GAINS && nb > 0) {
                         if (exact) {
                             const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]},
                                          dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
-                            if (par) fwd_gauss_tile_pt<true, true>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], gtab,
-                                                                   s_pt[warp], s_bl[warp], nb, toff, xh, dxt, dxl, gc,
-                                                                   lane, sr, si);
-                            else fwd_gauss_tile_pt<true, false>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], gtab,
-                                                                s_pt[warp], s_bl[warp], nb, toff, xh, dxt, dxl, gc,
-                                                                lane, sr, si);
+                            if (par) fwd_gauss_tile_pt<true, true>(q_off, q_lo, q_pg, q_Ba, gtab, s_pt[warp],
+                                                                   s_bl[warp], nb, toff, xh, dxt, dxl, gc, lane, sr,
+                                                                   si);
+                            else fwd_gauss_tile_pt<true, false>(q_off, q_lo, q_pg, q_Ba, gtab, s_pt[warp],
+                                                                s_bl[warp], nb, toff, xh, dxt, dxl, gc, lane, sr, si);
                         } else if (par) {
-                            fwd_gauss_tile_pt<false, true>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], gtab, s_pt[warp],
-                                                           s_bl[warp], nb, toff, xh, dx, dx, gc, lane, sr, si);
+                            fwd_gauss_tile_pt<false, true>(q_off, q_lo, q_pg, q_Ba, gtab, s_pt[warp], s_bl[warp], nb,
+                                                           toff, xh, dx, dx, gc, lane, sr, si);
                         } else {
-                            fwd_gauss_tile_pt<false, false>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], gtab, s_pt[warp],
-                                                            s_bl[warp], nb, toff, xh, dx, dx, gc, lane, sr, si);
+                            fwd_gauss_tile_pt<false, false>(q_off, q_lo, q_pg, q_Ba, gtab, s_pt[warp], s_bl[warp], nb,
+                                                            toff, xh, dx, dx, gc, lane, sr, si);
                         }
                     } else if (exact) {
-                        const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]}, dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
-                        if (par) fwd_gauss_tile<GAINS, true, true>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], gtab,
-                                                                   xh, dxt, dxl, gc, ant, sr, si);
-                        else fwd_gauss_tile<GAINS, true, false>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], gtab,
-                                                                xh, dxt, dxl, gc, ant, sr, si);
+                        const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]},
+                                     dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
+                        if (par) fwd_gauss_tile<GAINS, true, true>(q_off, q_lo, q_pg, q_Ba, gtab, xh, dxt, dxl, gc,
+                                                                   ant, sr, si);
+                        else fwd_gauss_tile<GAINS, true, false>(q_off, q_lo, q_pg, q_Ba, gtab, xh, dxt, dxl, gc, ant,
+                                                                sr, si);
                     } else if (par) {
-                        fwd_gauss_tile<GAINS, false, true>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], gtab,
-                                                           xh, dx, dx, gc, ant, sr, si);
+                        fwd_gauss_tile<GAINS, false, true>(q_off, q_lo, q_pg, q_Ba, gtab, xh, dx, dx, gc, ant, sr, si);
                     } else {
-                        fwd_gauss_tile<GAINS, false, false>(s_off[q], s_lo[q], s_pg[q], s_B[warp][q], gtab,
-                                                            xh, dx, dx, gc, ant, sr, si);
+                        fwd_gauss_tile<GAINS, false, false>(q_off, q_lo, q_pg, q_Ba, gtab, xh, dx, dx, gc, ant, sr,
+                                                            si);
                     }
 #pragma unroll
                     for (int r = 0; r < 2; ++r) {
@@ -481,141 +520,7 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
         }
         u += g1 - g0;
     }
-    if (GAINS && gfault) atomicOr(&g_wait_fault, 1u);
-}
-
-// Forward, warp-decoupled variant (no gains): every warp stages the streamed
-// pixel granules into its own slice of shared memory and synchronises only
-// with itself, so a tile that takes the exact phase path delays its own warp
-// and no CTA barrier couples the 8 warps.  Each warp re-reads the granule
-// data the other warps read (from L1/L2, ~0.4 B per pair).  An autotuner
-// candidate beside the CTA-staged kernel.
-constexpr int NSW = 2;   // granules per warp stage
-
-__global__ void __launch_bounds__(NTHREADS, 2)
-fwd_mixed_wd_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ plp,
-                    double2* __restrict__ partial)
-{
-    __shared__ float4 s_off[BLK_GRAN][NSW][G];
-    __shared__ float4 s_lo[BLK_GRAN][NSW][G];
-    __shared__ float4 s_pg[BLK_GRAN][NSW][G];
-    __shared__ float s_B[BLK_GRAN][NSW][G];
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const Plan pl = *plp;
-    const long long c = blockIdx.x;
-    long long u, u_end;
-    cta_range(pl, c, u, u_end);
-
-    while (u < u_end) {
-        const int p = find_prob(pl, u);
-        const DevProblem& P = probs[p];
-        const long long loc = u - pl.prob_u0[p];
-        const double* X;
-        if (!fwd_role(P, X)) {
-            u = min(u_end, pl.prob_u0[p + 1]);
-            continue;
-        }
-        const int upb = P.pix.n_gran;
-        const int blk = (int)(loc / upb);
-        const int g0 = (int)(loc % upb);
-        const int g1 = (int)min((long long)upb, (long long)g0 + (u_end - u));
-        u += g1 - g0;
-        const int vg = blk * BLK_GRAN + warp;
-        if (vg >= P.vis.n_gran) continue;               // this warp owns nothing in this block
-        const int e0 = vg * G + lane;
-        const float4 ch = P.vis.cen_hi[vg], cl = P.vis.cen_lo[vg], ext = P.vis.ext[vg];
-        float4 xh[2], dx[2];
-        const int2 ant[2] = {make_int2(0, 0), make_int2(0, 0)};
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            xh[r] = P.vis.hi[e0 + 32 * r];
-            dx[r] = to_rad(P.vis.off[e0 + 32 * r]);
-        }
-        double tr[2] = {0.0, 0.0}, ti[2] = {0.0, 0.0};
-        for (int gs = g0; gs < g1; gs += NSW) {
-            const int ns = min(NSW, g1 - gs);
-            __syncwarp();                               // this warp's previous stage consumed
-            for (int q = 0; q < ns; ++q) {
-                const int g = gs + q;
-                const bool gauss = P.gkind[g] != DIRAC;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int i = lane + 32 * h;
-                    const int e = g * G + i;
-                    float4 o = P.pix.off[e];
-                    o.w = (float)(X[e] * P.pix.d[e].w);
-                    s_off[warp][q][i] = o;
-                    const float4 lo = P.pix.offlo[e];
-                    s_lo[warp][q][i] = lo;
-                    if (gauss) s_pg[warp][q][i] = P.pgauss[e];
-                    s_B[warp][q][i] = frac_dot3(ch, cl, o, lo) * TWO_PI_F;
-                }
-            }
-            __syncwarp();
-            for (int q = 0; q < ns; ++q) {
-                const int g = gs + q;
-                const int kind = P.gkind[g];
-                const float4 yc_h = P.pix.cen_hi[g], yc_l = P.pix.cen_lo[g];
-                const bool exact = dot3(ext, P.pix.ext[g]) > D_MAX;
-                float C[2];
-#pragma unroll
-                for (int r = 0; r < 2; ++r) C[r] = frac_dot3(xh[r], P.vis.lo[e0 + 32 * r], yc_h, yc_l);
-                float sr[2] = {0.f, 0.f}, si[2] = {0.f, 0.f};
-                if (kind == DIRAC) {
-                    if (exact) {
-                        const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]}, dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
-                        fwd_dirac_tile<false, true>(s_off[warp][q], s_lo[warp][q], s_B[warp][q], nullptr, dxt, dxl,
-                                                    ant, sr, si);
-                    } else {
-                        fwd_dirac_tile<false, false>(s_off[warp][q], s_lo[warp][q], s_B[warp][q], nullptr, dx, dx,
-                                                     ant, sr, si);
-                    }
-#pragma unroll
-                    for (int r = 0; r < 2; ++r) {
-                        float sn, cs;
-                        __sincosf(C[r] * TWO_PI_F, &sn, &cs);
-                        tr[r] += (double)fmaf(cs, sr[r], sn * si[r]);
-                        ti[r] += (double)fmaf(cs, si[r], -sn * sr[r]);
-                    }
-                } else {
-                    const bool par = (kind == PARAXIAL);
-                    GaussConst gc[2];
-#pragma unroll
-                    for (int r = 0; r < 2; ++r) {
-                        gc[r] = gauss_const(xh[r].x, xh[r].y, xh[r].z, P.gsig[g]);
-                        C[r] = frac_turns(C[r] + gc[r].cphase);
-                    }
-                    if (exact) {
-                        const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]}, dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
-                        if (par) fwd_gauss_tile<false, true, true>(s_off[warp][q], s_lo[warp][q], s_pg[warp][q],
-                                                                   s_B[warp][q], nullptr, xh, dxt, dxl, gc, ant, sr, si);
-                        else fwd_gauss_tile<false, true, false>(s_off[warp][q], s_lo[warp][q], s_pg[warp][q],
-                                                                s_B[warp][q], nullptr, xh, dxt, dxl, gc, ant, sr, si);
-                    } else if (par) {
-                        fwd_gauss_tile<false, false, true>(s_off[warp][q], s_lo[warp][q], s_pg[warp][q], s_B[warp][q],
-                                                           nullptr, xh, dx, dx, gc, ant, sr, si);
-                    } else {
-                        fwd_gauss_tile<false, false, false>(s_off[warp][q], s_lo[warp][q], s_pg[warp][q], s_B[warp][q],
-                                                            nullptr, xh, dx, dx, gc, ant, sr, si);
-                    }
-#pragma unroll
-                    for (int r = 0; r < 2; ++r) {
-                        const float ar = gc[r].id * fmaf(-gc[r].beta, si[r], sr[r]);
-                        const float ai = gc[r].id * fmaf(gc[r].beta, sr[r], si[r]);
-                        float sn, cs;
-                        __sincosf(C[r] * TWO_PI_F, &sn, &cs);
-                        tr[r] += (double)fmaf(cs, ar, sn * ai);
-                        ti[r] += (double)fmaf(cs, ai, -sn * ar);
-                    }
-                }
-            }
-        }
-        const int gb = pl.prob_b0[p] + blk;
-        double2* dst = partial + (size_t)slot_of(pl, gb) * BLK + warp * G + lane;
-#pragma unroll
-        for (int r = 0; r < 2; ++r) dst[32 * r] = make_double2(tr[r], ti[r]);
-    }
+    if (fault) atomicOr(&g_wait_fault, 1u);
 }
 
 // ----------------------------------------------------------- adjoint tiles
@@ -1045,15 +950,22 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
 
 // Bytes of one pixel granule's gains table in shared memory.
 static int gains_table_bytes(int n_ant) { return gain_rows(n_ant) * GP * (int)sizeof(float2); }
-// The forward double-buffers the table (prefetching the next granule's while
-// the current one is in use) when two fit in this much dynamic shared memory;
-// the kernel reads the choice back from the launch's dynamic size.
-constexpr int FWD_GAINS_DBL_MAX = 200 * 1024;
-int fwd_smem_bytes(int n_ant, bool gains)
+// Dynamic shared memory of the forward: its two stage buffers and, with gains,
+// one or two gains tables.  The table is double-buffered (the next granule's
+// prefetched while the current one is in use) when two fit in this much; the
+// kernel reads the choice back from the launch's dynamic size.  With the
+// kernel's 36 KB of static shared memory the total stays within 227 KB.
+constexpr int FWD_GAINS_DBL_MAX = 180 * 1024;
+static int fwd_stage_bytes_of(int nst)
 {
-    if (!gains) return 0;
+    return nst <= 1 ? fwd_stage_bytes<1>() : nst <= 2 ? fwd_stage_bytes<2>()
+                                          : nst <= 4 ? fwd_stage_bytes<4>() : fwd_stage_bytes<8>();
+}
+int fwd_smem_bytes(int n_ant, bool gains, int nst)
+{
+    if (!gains) return fwd_stage_bytes_of(shape_nst(nst));
     const int t = gains_table_bytes(n_ant);
-    return 2 * t <= FWD_GAINS_DBL_MAX ? 2 * t : t;
+    return fwd_stage_bytes<1>() + (2 * t <= FWD_GAINS_DBL_MAX ? 2 * t : t);
 }
 int adj_gains_smem_bytes(int n_ant) { return gains_table_bytes(n_ant); }
 
@@ -1093,7 +1005,6 @@ static AdjKernel adj_by_poly(int np)
 static FwdKernel fwd_kernel_of(int code)
 {
     const int nst = shape_nst(code), np = shape_npoly(code);
-    if (nst == 0) return fwd_mixed_wd_kernel;
     return nst <= 2 ? fwd_by_poly<2>(np) : nst <= 4 ? fwd_by_poly<4>(np) : fwd_by_poly<8>(np);
 }
 static AdjKernel adj_kernel_of(int code)
@@ -1105,13 +1016,12 @@ static AdjKernel adj_kernel_of(int code)
 cudaError_t launch_forward_mixed(bool gains, int n_ant, int nst, const DevProblem* probs, const Plan* plp, int C,
                                  double2* partial, cudaStream_t st)
 {
-    if (gains) {
-        // the dynamic shared-memory limit was raised by occupancy_mixed()
-        // when the batch was built (not here: this may run under capture)
-        fwd_mixed_kernel<true, 1><<<C, NTHREADS, fwd_smem_bytes(n_ant, true), st>>>(probs, plp, partial);
-    } else {
-        fwd_kernel_of(nst)<<<C, NTHREADS, 0, st>>>(probs, plp, partial);
-    }
+    // the dynamic shared-memory limits were raised by occupancy_mixed() when
+    // the batch was built (not here: this may run under capture)
+    if (gains)
+        fwd_mixed_kernel<true, 1><<<C, NTHREADS, fwd_smem_bytes(n_ant, true, 1), st>>>(probs, plp, partial);
+    else
+        fwd_kernel_of(nst)<<<C, NTHREADS, fwd_smem_bytes(0, false, nst), st>>>(probs, plp, partial);
     return cudaGetLastError();
 }
 
@@ -1128,14 +1038,16 @@ int occupancy_mixed(int op, bool gains, int n_ant, int nst)
     static int fwd_smem_limit = 0, adj_smem_limit = 0;   // only ever raised
     if (op == 0) {
         if (gains) {
-            const int sm = fwd_smem_bytes(n_ant, true);
+            const int sm = fwd_smem_bytes(n_ant, true, 1);
             if (sm > fwd_smem_limit) {
                 cudaFuncSetAttribute(fwd_mixed_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
                 fwd_smem_limit = sm;
             }
             return occ_of(fwd_mixed_kernel<true, 1>, sm);
         }
-        return occ_of(fwd_kernel_of(nst), 0);
+        const int sm = fwd_smem_bytes(0, false, nst);      // fixed per tile shape
+        cudaFuncSetAttribute(fwd_kernel_of(nst), cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        return occ_of(fwd_kernel_of(nst), sm);
     }
     if (gains) {
         const int sm = adj_gains_smem_bytes(n_ant);
