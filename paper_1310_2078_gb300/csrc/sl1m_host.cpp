@@ -96,10 +96,50 @@ static void kd_append(std::vector<int>& order, std::vector<int> members, const d
     while (order.size() % G) order.push_back(-1);
 }
 
-// With gains, the forward kernel's lanes gather G[j][a_k] and G[j][b_k] from
-// a shared-memory row of 8-byte words: 16 lanes are served together, without
-// conflict when their antennas differ modulo 16.  Lane t owns slots t and
-// t+32 of a granule, so slots {0-15, 16-31, 32-47, 48-63} form the groups.
+// Reorder whole visibility granules (members unchanged) by the share of
+// (visibility granule, pixel granule) tiles whose extents bound the phase
+// product term above D_MAX turns, which the mixed kernels evaluate on the
+// exact, about 3x dearer, path.  The forward's 8 warps each own one granule
+// of a block and meet at every stage, so a block costs what its slowest
+// granule costs: a wide granule among narrow ones leaves 7 warps idle.  A
+// stable sort by that share (most granules: 0, kept in k-d order) groups the
+// wide ones into the same blocks.  The share is taken against up to 1,024
+// pixel granules (every ceil(n/1024)-th), with the extents as half the
+// bounding box, as layout_side computes them.
+static void group_by_exact_share(std::vector<int>& order, const double* uvw, const std::vector<float4>& pext)
+{
+    const size_t ng = order.size() / G;
+    if (ng < 2 || pext.empty()) return;
+    const size_t step = (pext.size() + 1023) / 1024;
+    std::vector<std::pair<float, int>> key(ng);
+    bool any = false;
+    for (size_t g = 0; g < ng; ++g) {
+        double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+        for (size_t i = g * G; i < (g + 1) * G; ++i) {
+            const int o = order[i];
+            if (o < 0) continue;
+            for (int a = 0; a < 3; ++a) {
+                mn[a] = std::min(mn[a], uvw[3 * (size_t)o + a]);
+                mx[a] = std::max(mx[a], uvw[3 * (size_t)o + a]);
+            }
+        }
+        const float e[3] = {(float)(0.5 * (mx[0] - mn[0])), (float)(0.5 * (mx[1] - mn[1])),
+                            (float)(0.5 * (mx[2] - mn[2]))};
+        int n_ex = 0, n = 0;
+        for (size_t p = 0; p < pext.size(); p += step, ++n)
+            n_ex += e[0] * pext[p].x + e[1] * pext[p].y + e[2] * pext[p].z > D_MAX;
+        key[g] = {(float)n_ex / (float)std::max(1, n), (int)g};
+        any |= n_ex > 0;
+    }
+    if (!any) return;
+    std::stable_sort(key.begin(), key.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+    std::vector<int> out(order.size());
+    for (size_t g = 0; g < ng; ++g)
+        std::copy(order.begin() + (size_t)key[g].second * G, order.begin() + ((size_t)key[g].second + 1) * G,
+                  out.begin() + g * G);
+    order.swap(out);
+}
+
 // With gains: sort the members of each granule (its membership is unchanged)
 // by antenna pair (a, b), padding last, so that equal pairs are adjacent: the
 // adjoint computes a pair's gain product once per run, and the forward lists
@@ -442,58 +482,6 @@ int sl1m_problem::rebuild(cudaStream_t st)
     }
     if (!dev) dev = std::make_unique<ProblemDev>();
     ProblemDev& D = *dev;
-    // ---- visibilities: k-d order on (u, v)
-    {
-        std::vector<int> members(n_vis);
-        for (int64_t k = 0; k < n_vis; ++k) members[k] = (int)k;
-        std::vector<int> order;
-        kd_append(order, std::move(members), uvw.data(), uvw.data() + 1, 3);
-        if (n_ant > 0) sort_baselines(order, ant);
-        std::vector<d4> xyz(n_vis);
-        for (int64_t k = 0; k < n_vis; ++k)
-            xyz[k] = make_d4(uvw[3 * k], uvw[3 * k + 1], uvw[3 * k + 2], weights.empty() ? 1.0 : weights[k]);
-        HostSide H;
-        layout_side(order, xyz, (int)n_vis, H);
-        CK(upload_side(H, D.vis, hp.vis, st));
-        gext_vis = H.ext;
-        std::vector<int2> a(H.n_pad, make_int2(0, 0));
-        std::vector<double2> Vs(H.n_pad, make_double2(0.0, 0.0));
-        for (int i = 0; i < H.n_pad; ++i) {
-            const int o = H.orig[i];
-            if (o < 0) continue;
-            if (!ant.empty()) a[i] = make_int2(ant[2 * o], ant[2 * o + 1]);
-            Vs[i] = make_double2(vis[2 * o], vis[2 * o + 1]);
-        }
-        CK(D.ant.upload(a.data(), a.size(), st));
-        CK(D.V.upload(Vs.data(), Vs.size(), st));
-        vis_orig = H.orig;
-        if (n_ant > 0) {
-            // each granule's distinct antenna pairs (adjacent after sort_baselines)
-            std::vector<int> vslot(H.n_pad, 0), gnb(H.n_gran, 0);
-            std::vector<int2> gbl((size_t)H.n_gran * NB_MAX, make_int2(0, 0));
-            for (int g = 0; g < H.n_gran; ++g) {
-                int nb = 0;
-                bool over = false;
-                for (int i = g * G; i < (g + 1) * G; ++i) {
-                    const int2 ab = a[i];
-                    if (nb == 0 || ab.x != gbl[(size_t)g * NB_MAX + nb - 1].x ||
-                        ab.y != gbl[(size_t)g * NB_MAX + nb - 1].y) {
-                        if (nb == NB_MAX) { over = true; break; }
-                        gbl[(size_t)g * NB_MAX + nb++] = ab;
-                    }
-                    vslot[i] = nb - 1;
-                }
-                gnb[g] = over ? 0 : nb;
-            }
-            CK(D.vslot.upload(vslot.data(), vslot.size(), st));
-            CK(D.gbl.upload(gbl.data(), gbl.size(), st));
-            CK(D.gnb.upload(gnb.data(), gnb.size(), st));
-        } else {
-            D.vslot.free();
-            D.gbl.free();
-            D.gnb.free();
-        }
-    }
     // ---- pixels: classes of equal (kind, sigma), each in k-d order on (l, m)
     {
         std::vector<std::pair<std::pair<int, double>, int>> cls(n_pix);
@@ -579,6 +567,60 @@ int sl1m_problem::rebuild(cudaStream_t st)
         } else {
             D.gains32.free();
             D.gains64.free();
+        }
+    }
+    // ---- visibilities: k-d order on (u, v); granules grouped by their share of
+    // exact-phase tiles (after the pixels, whose extents that share needs)
+    {
+        std::vector<int> members(n_vis);
+        for (int64_t k = 0; k < n_vis; ++k) members[k] = (int)k;
+        std::vector<int> order;
+        kd_append(order, std::move(members), uvw.data(), uvw.data() + 1, 3);
+        group_by_exact_share(order, uvw.data(), gext_pix);
+        if (n_ant > 0) sort_baselines(order, ant);
+        std::vector<d4> xyz(n_vis);
+        for (int64_t k = 0; k < n_vis; ++k)
+            xyz[k] = make_d4(uvw[3 * k], uvw[3 * k + 1], uvw[3 * k + 2], weights.empty() ? 1.0 : weights[k]);
+        HostSide H;
+        layout_side(order, xyz, (int)n_vis, H);
+        CK(upload_side(H, D.vis, hp.vis, st));
+        gext_vis = H.ext;
+        std::vector<int2> a(H.n_pad, make_int2(0, 0));
+        std::vector<double2> Vs(H.n_pad, make_double2(0.0, 0.0));
+        for (int i = 0; i < H.n_pad; ++i) {
+            const int o = H.orig[i];
+            if (o < 0) continue;
+            if (!ant.empty()) a[i] = make_int2(ant[2 * o], ant[2 * o + 1]);
+            Vs[i] = make_double2(vis[2 * o], vis[2 * o + 1]);
+        }
+        CK(D.ant.upload(a.data(), a.size(), st));
+        CK(D.V.upload(Vs.data(), Vs.size(), st));
+        vis_orig = H.orig;
+        if (n_ant > 0) {
+            // each granule's distinct antenna pairs (adjacent after sort_baselines)
+            std::vector<int> vslot(H.n_pad, 0), gnb(H.n_gran, 0);
+            std::vector<int2> gbl((size_t)H.n_gran * NB_MAX, make_int2(0, 0));
+            for (int g = 0; g < H.n_gran; ++g) {
+                int nb = 0;
+                bool over = false;
+                for (int i = g * G; i < (g + 1) * G; ++i) {
+                    const int2 ab = a[i];
+                    if (nb == 0 || ab.x != gbl[(size_t)g * NB_MAX + nb - 1].x ||
+                        ab.y != gbl[(size_t)g * NB_MAX + nb - 1].y) {
+                        if (nb == NB_MAX) { over = true; break; }
+                        gbl[(size_t)g * NB_MAX + nb++] = ab;
+                    }
+                    vslot[i] = nb - 1;
+                }
+                gnb[g] = over ? 0 : nb;
+            }
+            CK(D.vslot.upload(vslot.data(), vslot.size(), st));
+            CK(D.gbl.upload(gbl.data(), gbl.size(), st));
+            CK(D.gnb.upload(gnb.data(), gnb.size(), st));
+        } else {
+            D.vslot.free();
+            D.gbl.free();
+            D.gnb.free();
         }
     }
     hp.ant = D.ant.p;
