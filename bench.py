@@ -246,7 +246,6 @@ def cpu_baseline(w, gpu_fwd=None, gpu_adj=None, budget_s: float = 12.0):
     sample)."""
     import oracle
     O = oracle.Problem(w.uvw, w.lm, w.sigma, w.kind, w.weights, w.ant_pair, w.gains)
-    rng = np.random.default_rng(0)
     x, r = baseline_inputs(w)
     # calibrate: 8 rows
     t0 = time.perf_counter()
@@ -254,8 +253,10 @@ def cpu_baseline(w, gpu_fwd=None, gpu_adj=None, budget_s: float = 12.0):
     per_row = (time.perf_counter() - t0) / 8
     n_rows = max(8, int(0.5 * budget_s / per_row))
     n_cols = max(8, int(0.5 * budget_s / (per_row * w.n_vis / w.n_pix)))
-    rows = rng.choice(w.n_vis, min(n_rows, w.n_vis), replace=False)
-    cols = rng.choice(w.n_pix, min(n_cols, w.n_pix), replace=False)
+    # prefixes of fixed permutations: a run that samples more rows or columns
+    # keeps every row and column of a smaller sample, so errors compare across runs
+    rows = np.random.default_rng(1).permutation(w.n_vis)[:min(n_rows, w.n_vis)]
+    cols = np.random.default_rng(2).permutation(w.n_pix)[:min(n_cols, w.n_pix)]
     t0 = time.perf_counter()
     fo = oracle.forward(O, x, rows=rows)
     ao = oracle.adjoint(O, r, cols=cols)
