@@ -111,7 +111,7 @@ int sl1m_set_pixels(sl1m_problem* prob, int64_t n_pix, const double* lm,
  * per pixel and antenna; the entry for visibility k is multiplied by
  * g_jk = G[j][a_k] * conj(G[j][b_k]).  G == NULL or n_ant == 0 removes the
  * gains.  The mixed-precision kernels hold one pixel granule's gains for all
- * antennas in shared memory: n_ant <= 320 (SL1M_ERR_ARG above). */
+ * antennas in shared memory: n_ant <= 300 (SL1M_ERR_ARG above). */
 int sl1m_set_gains(sl1m_problem* prob, int32_t n_ant, const double* G);
 
 /* Forward operator, Eq. sme: vis_out_k = sum_j A_kj x_j.

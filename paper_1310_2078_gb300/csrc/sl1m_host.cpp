@@ -1323,7 +1323,7 @@ int sl1m_set_gains(sl1m_problem* prob, int32_t n_ant, const double* Gn)
         prob->dirty = true;
         return SL1M_OK;
     }
-    if (n_ant < 0 || n_ant > 320) return sl1m_fail(ctx, SL1M_ERR_ARG, "n_ant must be in [1, 320]");
+    if (n_ant < 0 || n_ant > 300) return sl1m_fail(ctx, SL1M_ERR_ARG, "n_ant must be in [1, 300]");
     if (prob->n_pix <= 0) return sl1m_fail(ctx, SL1M_ERR_STATE, "set pixels before gains");
     const size_t cnt = (size_t)2 * prob->n_pix * n_ant;
     if (!all_finite(Gn, cnt)) return sl1m_fail(ctx, SL1M_ERR_ARG, "non-finite gains");

@@ -787,34 +787,72 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
 // Adjoint with gains.  The CTA's 8 warps share one owned pixel granule at a
 // time -- its gains for all antennas in shared memory as [antenna][pixel], so
 // a lane's loads never conflict -- and split the streamed visibility granules
-// of the run among themselves (warp w takes the w-th of every 8).  For each
-// owned granule the 8 warp sums are added in warp order (deterministic).
+// of the run among themselves (warp w takes the w-th of every 8).  Each warp
+// runs its own pipeline: lane 0 bulk-copies the raw records of the warp's
+// next granule (offsets, residuals, coordinates, r, antenna pairs, centre and
+// extent) into the warp's slice, which completes on the warp's mbarrier; the
+// warp derives what its tiles read, then at once copies its following granule
+// into the freed slice, so the copy runs under the tiles.  No CTA barrier
+// inside the run.  For each owned granule the 8 warp sums are added in warp
+// order (deterministic).
+struct AdjRaw {                                   // one warp's slice, bytes
+    static constexpr int OFF = 0, LO = 1024, HI = 2048, R = 3072, ANT = 4096, CEN = 4608;
+    static constexpr int BYTES = CEN + 48;        // a multiple of 16
+};
+
+// Lane 0: copy visibility granule g of P (residual R) into a warp's raw slice.
+__device__ __forceinline__ void adj_raw_load(unsigned char* raw, const DevProblem& P, const double2* R, int g,
+                                             unsigned long long* bar)
+{
+    const size_t e = (size_t)g * G;
+    fence_proxy_async_smem();                     // the slice's last readers (generic proxy) are done
+    mbar_arrive_expect(bar, AdjRaw::BYTES);
+    bulk_copy(raw + AdjRaw::OFF, P.vis.off + e, 1024, bar);
+    bulk_copy(raw + AdjRaw::LO, P.vis.offlo + e, 1024, bar);
+    bulk_copy(raw + AdjRaw::HI, P.vis.hi + e, 1024, bar);
+    bulk_copy(raw + AdjRaw::R, R + e, 1024, bar);
+    bulk_copy(raw + AdjRaw::ANT, P.ant + e, 512, bar);
+    bulk_copy(raw + AdjRaw::CEN, P.vis.cen_hi + g, 16, bar);
+    bulk_copy(raw + AdjRaw::CEN + 16, P.vis.cen_lo + g, 16, bar);
+    bulk_copy(raw + AdjRaw::CEN + 32, P.vis.ext + g, 16, bar);
+}
+
 __global__ void __launch_bounds__(NTHREADS, 2)
 adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ plp,
                        double* __restrict__ partial)
 {
-    __shared__ float4 s_off[BLK_GRAN][G];
-    __shared__ float4 s_lo[BLK_GRAN][G];
-    __shared__ float4 s_abs[BLK_GRAN][G];
+    // per warp, what its tiles read for its current granule
+    __shared__ float4 s_off[BLK_GRAN][G];       // {du, dv, dw, pair key}
+    __shared__ float4 s_abs[BLK_GRAN][G];       // {u, v, -2 w, u^2 + v^2}
     __shared__ float2 s_r[BLK_GRAN][G];
     __shared__ float s_B[BLK_GRAN][G];
-    __shared__ float4 s_gw[BLK_GRAN][G];
-    __shared__ float4 s_cen[BLK_GRAN][3];
+    __shared__ float4 s_gw[BLK_GRAN][G];        // Gaussian owners: {gamr, coef, r're, r'im}
     __shared__ double s_red[BLK_GRAN][G];
-    // the owned granule's gains [gain_rows(n_ant)][GP], filled by a bulk
-    // (TMA) copy that completes on s_gbar
-    extern __shared__ __align__(128) float2 s_gain[];
-    __shared__ __align__(8) unsigned long long s_gbar;
+    __shared__ __align__(8) unsigned long long s_wbar[BLK_GRAN];   // each warp's raw slice
+    __shared__ __align__(8) unsigned long long s_gbar;             // the gains table
+    // dynamic: [raw slices, BLK_GRAN x AdjRaw::BYTES][the owned granule's gains
+    // [gain_rows(n_ant)][GP]], each filled by bulk (TMA) copies
+    extern __shared__ __align__(128) unsigned char s_dyn[];
+    float2* const s_gain = reinterpret_cast<float2*>(s_dyn + BLK_GRAN * AdjRaw::BYTES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* const raw = s_dyn + warp * AdjRaw::BYTES;
+    const float4* const raw_off = reinterpret_cast<const float4*>(raw + AdjRaw::OFF);
+    const float4* const raw_lo = reinterpret_cast<const float4*>(raw + AdjRaw::LO);
+    const float4* const raw_hi = reinterpret_cast<const float4*>(raw + AdjRaw::HI);
+    const double2* const raw_r = reinterpret_cast<const double2*>(raw + AdjRaw::R);
+    const int2* const raw_ant = reinterpret_cast<const int2*>(raw + AdjRaw::ANT);
+    const float4* const raw_cen = reinterpret_cast<const float4*>(raw + AdjRaw::CEN);
     const Plan pl = *plp;
     const long long c = blockIdx.x;
     long long u, u_end;
     cta_range(pl, c, u, u_end);
     unsigned gpar = 0;          // parity of the next wait on s_gbar
-    bool gfault = false;        // a bounded wait gave up
+    unsigned wpar = 0;          // parity of this warp's next wait on s_wbar[warp]
+    bool fault = false;         // a bounded wait gave up
     if (threadIdx.x == 0) {
         mbar_init(&s_gbar, 1);
+        for (int w = 0; w < BLK_GRAN; ++w) mbar_init(&s_wbar[w], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -844,6 +882,7 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
                 bulk_load(s_gain, P.gains32 + (size_t)pgi * gtab_n, (unsigned)gtab_n * (unsigned)sizeof(float2),
                           &s_gbar);
             }
+            if (lane == 0 && g0 + warp < g1) adj_raw_load(raw, P, R, g0 + warp, &s_wbar[warp]);
             const float4 ch = P.pix.cen_hi[pgi], cl = P.pix.cen_lo[pgi], ext = P.pix.ext[pgi];
             const int kind = P.gkind[pgi];
             const float sigma = P.gsig[pgi];
@@ -859,75 +898,66 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
                 if (gauss) pgd[r] = pix_for_gauss(P.pgauss[eidx[r]]);
             }
             const SmemGain sg{s_gain, lane};
-            if (!mbar_wait(&s_gbar, gpar)) gfault = true;
+            if (!mbar_wait(&s_gbar, gpar)) fault = true;
             gpar ^= 1u;
             double tot[2] = {0.0, 0.0};
-            for (int gs = g0; gs < g1; gs += BLK_GRAN) {
-                const int ns = min(BLK_GRAN, g1 - gs);
-                __syncthreads();
-                for (int t = threadIdx.x; t < ns * G; t += NTHREADS) {
-                    const int q = t / G, i = t % G;
-                    const int e = (gs + q) * G + i;
-                    float4 o = P.vis.off[e];
-                    const int2 ab = P.ant[e];
-                    o.w = __int_as_float(ab.x << 16 | ab.y);   // the pair key (pair_gains)
-                    s_off[q][i] = o;
-                    s_lo[q][i] = P.vis.offlo[e];
-                    s_abs[q][i] = vis_for_gauss(P.vis.hi[e]);
-                    const double2 rr = R[e];
-                    s_r[q][i] = make_float2((float)rr.x, (float)rr.y);
-                }
-                if (threadIdx.x < ns) {
-                    const int g = gs + threadIdx.x;
-                    s_cen[threadIdx.x][0] = P.vis.cen_hi[g];
-                    s_cen[threadIdx.x][1] = P.vis.cen_lo[g];
-                    s_cen[threadIdx.x][2] = P.vis.ext[g];
-                }
-                __syncthreads();
-                if (warp >= ns) continue;                    // this warp has no granule in this stage
-                const int q = warp;
+            for (int g = g0 + warp; g < g1; g += BLK_GRAN) {
+                if (!mbar_wait(&s_wbar[warp], wpar)) fault = true;
+                wpar ^= 1u;
+                // derive this granule's records for the tiles
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int k = lane + 32 * h;
-                    float b = frac_dot3(ch, cl, s_off[q][k], s_lo[q][k]);
+                    float4 o = raw_off[k];
+                    const int2 ab = raw_ant[k];
+                    o.w = __int_as_float(ab.x << 16 | ab.y);   // the pair key (pair_gains)
+                    float b = frac_dot3(ch, cl, o, raw_lo[k]);
+                    const float4 va = vis_for_gauss(raw_hi[k]);
+                    const double2 rd = raw_r[k];
+                    const float2 rr = make_float2((float)rd.x, (float)rd.y);
                     if (gauss) {
-                        const float4 va = s_abs[q][k];
                         const GaussConst gc = gauss_const(va.x, va.y, -0.5f * va.z, sigma);
                         b = frac_turns(b + gc.cphase);
-                        const float2 rr = s_r[q][k];
-                        s_gw[q][k] = make_float4(gc.gamr, gc.coef, gc.id * fmaf(gc.beta, rr.y, rr.x),
-                                                 gc.id * fmaf(-gc.beta, rr.x, rr.y));
+                        s_gw[warp][k] = make_float4(gc.gamr, gc.coef, gc.id * fmaf(gc.beta, rr.y, rr.x),
+                                                    gc.id * fmaf(-gc.beta, rr.x, rr.y));
                     }
-                    s_B[q][k] = b * TWO_PI_F;                 // radians
+                    s_off[warp][k] = o;
+                    s_abs[warp][k] = va;
+                    s_r[warp][k] = rr;
+                    s_B[warp][k] = b * TWO_PI_F;              // radians
                 }
-                __syncwarp();
-                const bool exact = dot3(ext, s_cen[q][2]) > D_MAX;
+                const float4 yc_h = raw_cen[0], yc_l = raw_cen[1], yext = raw_cen[2];
+                __syncwarp();                                 // the slice is read: refill it
+                if (lane == 0 && g + BLK_GRAN < g1) adj_raw_load(raw, P, R, g + BLK_GRAN, &s_wbar[warp]);
+                const bool exact = dot3(ext, yext) > D_MAX;
                 float C[2];
 #pragma unroll
-                for (int r = 0; r < 2; ++r) C[r] = frac_dot3(xh[r], P.pix.lo[eidx[r]], s_cen[q][0], s_cen[q][1]);
+                for (int r = 0; r < 2; ++r) C[r] = frac_dot3(xh[r], P.pix.lo[eidx[r]], yc_h, yc_l);
                 const float Cr[2] = {C[0] * TWO_PI_F, C[1] * TWO_PI_F};
+                const float4* g_lo = P.vis.offlo + (size_t)g * G;   // exact tiles only (rare)
                 float acc[2] = {0.f, 0.f};
                 if (!gauss) {
                     if (exact) {
                         const float4 dxt[2] = {P.pix.off[eidx[0]], P.pix.off[eidx[1]]},
                                  dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
-                        adj_dirac_tile<true, true>(s_off[q], s_lo[q], s_r[q], s_B[q], sg, C, dxt, dxl, acc);
+                        adj_dirac_tile<true, true>(s_off[warp], g_lo, s_r[warp], s_B[warp], sg, C, dxt, dxl, acc);
                     } else {
-                        adj_dirac_tile<true, false>(s_off[q], s_lo[q], s_r[q], s_B[q], sg, Cr, dx, dx, acc);
+                        adj_dirac_tile<true, false>(s_off[warp], g_lo, s_r[warp], s_B[warp], sg, Cr, dx, dx, acc);
                     }
                 } else {
                     if (exact) {
                         const float4 dxt[2] = {P.pix.off[eidx[0]], P.pix.off[eidx[1]]},
                                  dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
-                        if (par) adj_gauss_tile<true, true, true>(s_off[q], s_lo[q], s_abs[q], s_B[q], s_gw[q], sg, C, dxt, dxl, pgd, acc);
-                        else adj_gauss_tile<true, true, false>(s_off[q], s_lo[q], s_abs[q], s_B[q], s_gw[q], sg, C, dxt, dxl, pgd, acc);
+                        if (par) adj_gauss_tile<true, true, true>(s_off[warp], g_lo, s_abs[warp], s_B[warp], s_gw[warp], sg, C, dxt, dxl, pgd, acc);
+                        else adj_gauss_tile<true, true, false>(s_off[warp], g_lo, s_abs[warp], s_B[warp], s_gw[warp], sg, C, dxt, dxl, pgd, acc);
                     } else {
-                        if (par) adj_gauss_tile<true, false, true>(s_off[q], s_lo[q], s_abs[q], s_B[q], s_gw[q], sg, Cr, dx, dx, pgd, acc);
-                        else adj_gauss_tile<true, false, false>(s_off[q], s_lo[q], s_abs[q], s_B[q], s_gw[q], sg, Cr, dx, dx, pgd, acc);
+                        if (par) adj_gauss_tile<true, false, true>(s_off[warp], g_lo, s_abs[warp], s_B[warp], s_gw[warp], sg, Cr, dx, dx, pgd, acc);
+                        else adj_gauss_tile<true, false, false>(s_off[warp], g_lo, s_abs[warp], s_B[warp], s_gw[warp], sg, Cr, dx, dx, pgd, acc);
                     }
                 }
 #pragma unroll
                 for (int r = 0; r < 2; ++r) tot[r] += (double)acc[r];
+                __syncwarp();                                 // s_off ... of this warp free again
             }
 #pragma unroll
             for (int r = 0; r < 2; ++r) s_red[warp][lane + 32 * r] = tot[r];
@@ -943,7 +973,7 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
         }
         u += g1 - g0;
     }
-    if (gfault) atomicOr(&g_wait_fault, 1u);
+    if (fault) atomicOr(&g_wait_fault, 1u);
 }
 
 // ------------------------------------------------------------- launchers
@@ -967,7 +997,7 @@ int fwd_smem_bytes(int n_ant, bool gains, int nst)
     const int t = gains_table_bytes(n_ant);
     return fwd_stage_bytes<1>() + (2 * t <= FWD_GAINS_DBL_MAX ? 2 * t : t);
 }
-int adj_gains_smem_bytes(int n_ant) { return gains_table_bytes(n_ant); }
+int adj_gains_smem_bytes(int n_ant) { return BLK_GRAN * AdjRaw::BYTES + gains_table_bytes(n_ant); }
 
 cudaError_t wait_fault_read(unsigned* host_flag, cudaStream_t st)
 {
