@@ -158,14 +158,18 @@ KERNEL_SOURCES = ("sl1m_mixed.cu", "sl1m_fp64.cu", "sl1m_devfn.cuh", "sl1m_dev.h
 
 
 def kernel_source_hash():
-    """First 12 hex digits of the SHA-1 of the operator kernels' sources: a
-    profile summary records it, so counters taken on other kernel code are
-    not reported as this code's."""
+    """First 12 hex digits of the SHA-1 of the operator kernels' sources with
+    comments removed and whitespace collapsed: a profile summary records it,
+    so counters taken on other kernel code are not reported as this code's
+    (an edit of a comment leaves the code, and the hash, unchanged)."""
     import hashlib
     h = hashlib.sha1()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1310_2078_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1310_2078_gb300", "csrc", f), encoding="utf-8") as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)     # block comments
+        src = re.sub(r"//[^\n]*", " ", src)                  # line comments
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:12]
 
 

@@ -27,9 +27,10 @@
 //
 // Work split: a CTA owns BLK_GRAN granules of one side (one per warp, 2
 // elements per lane) and streams granules of the other side through shared
-// memory; units = (owned block, streamed granule) are spread over a
-// persistent grid stream-K style (Plan); partials are summed by the finish
-// kernels in a fixed order.
+// memory -- in the forward and in the gains adjoint by bulk (TMA) copies that
+// complete on mbarriers, issued ahead of use; units = (owned block, streamed
+// granule) are spread over a persistent grid stream-K style (Plan); partials
+// are summed by the finish kernels in a fixed order.
 #include "sl1m_dev.h"
 #include "sl1m_devfn.cuh"
 #include "sl1m_kernels.h"
@@ -42,7 +43,7 @@ namespace sl1m {
 // address as a constant offset.
 
 // Set (never cleared here) by a CTA whose bounded wait for a bulk copy gave
-// up; the host reads and clears it (mixed_wait_fault_take).
+// up; the host reads and clears it (wait_fault_read, wait_fault_clear).
 __device__ unsigned int g_wait_fault;
 
 // ----------------------------------------------------------- forward tiles
