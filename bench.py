@@ -568,7 +568,7 @@ def main():
 
     e2e = None
     if not args.no_e2e and not args.ops_only:
-        e2e = run_e2e(ctx, w, V, lam, prec, args, sl1m, stream)
+        e2e = run_e2e(ctx, w, V, lam, prec, args, sl1m, stream, ws)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         xb, rb = baseline_inputs(w)
@@ -599,12 +599,16 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def run_e2e(ctx, w, V, lam, prec, args, sl1m, stream):
+def run_e2e(ctx, w, V, lam, prec, args, sl1m, stream, ws=1):
     """The same solve from host buffers through the C ABI: set inputs (host
-    layout + H2D), solve, read the image back (D2H) -- all timed."""
+    layout + H2D), solve, read the image back (D2H) -- all timed.  With
+    several ranks, each solves its own problem between two barriers and the
+    value is all ranks' pairs over the slowest rank's time."""
     import torch
     steps = max(1, min(args.steps, 3))
     ctx.counters_reset()
+    if ws > 1:
+        torch.distributed.barrier()
     t0 = time.perf_counter()
     pairs = 0.0
     for _ in range(steps):
@@ -618,6 +622,11 @@ def run_e2e(ctx, w, V, lam, prec, args, sl1m, stream):
         Q.close()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([dt, pairs], dtype=torch.float64, device=f"cuda:{torch.cuda.current_device()}")
+        torch.distributed.all_reduce(t[0:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t[1:2], op=torch.distributed.ReduceOp.SUM)
+        dt, pairs = float(t[0]), float(t[1])
     c = ctx.counters()
     return {"value": pairs / dt, "unit": "pairs/s", "steps": steps,
             "h2d_bytes_per_step": c["h2d_bytes"] // steps, "d2h_bytes_per_step": c["d2h_bytes"] // steps,
