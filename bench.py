@@ -157,15 +157,17 @@ class ClockSampler:
 KERNEL_SOURCES = ("sl1m_mixed.cu", "sl1m_fp64.cu", "sl1m_devfn.cuh", "sl1m_dev.h", "sl1m_sincos_poly.h")
 
 
-def kernel_source_hash():
+def kernel_source_hash(csrc=None):
     """First 12 hex digits of the SHA-1 of the operator kernels' sources with
     comments removed and whitespace collapsed: a profile summary records it,
     so counters taken on other kernel code are not reported as this code's
-    (an edit of a comment leaves the code, and the hash, unchanged)."""
+    (an edit of a comment leaves the code, and the hash, unchanged).  csrc:
+    the source directory (default: the package's)."""
     import hashlib
+    csrc = csrc or os.path.join(ROOT, "paper_1310_2078_gb300", "csrc")
     h = hashlib.sha1()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1310_2078_gb300", "csrc", f), encoding="utf-8") as fh:
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
             src = fh.read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)     # block comments
         src = re.sub(r"//[^\n]*", " ", src)                  # line comments

@@ -1,0 +1,60 @@
+"""The bench's roofline arithmetic and its bookkeeping of ncu counters (no GPU)."""
+import os
+import shutil
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+class W:
+    def __init__(self, kind):
+        self.kind = None if kind is None else np.asarray(kind)
+        self.n_pix = 100 if kind is None else len(kind)
+
+
+def test_sfu_peak_dirac_and_fma_sincos_bound():
+    peak, basis, alt = bench.sfu_peak(W(None))
+    # 152 SMs x 16 MUFU/clk x 2.07 GHz / 2 MUFU per pair
+    assert peak == pytest.approx(152 * 16 * 2.07 / 2 * 1e0, rel=1e-12)
+    # LP optimum: x = 1/16 SFU-path and y = (1 - 8/16)/21 FMA-path warp-pairs per clock
+    # and sub-partition, 4 x 32 pairs per warp-pair and SM
+    per_sm_clk = 4 * 32 * (1 / 16 + 0.5 / 21)
+    assert alt["peak"] == pytest.approx(152 * 2.07 * per_sm_clk, rel=1e-12)
+    assert alt["peak"] > peak
+
+
+def test_sfu_peak_of_a_kind_mix_adds_time_per_pair():
+    kinds = [0] * 25 + [2] * 75          # 25% Dirac (2 MUFU), 75% Gaussian (3 MUFU)
+    peak, basis, alt = bench.sfu_peak(W(kinds))
+    assert peak == pytest.approx(152 * 16 * 2.07 / 2.75, rel=1e-12)
+    assert alt is None
+
+
+def test_kernel_source_hash_ignores_comments_only(tmp_path):
+    src = os.path.join(ROOT, "paper_1310_2078_gb300", "csrc")
+    for f in bench.KERNEL_SOURCES:
+        shutil.copy(os.path.join(src, f), tmp_path / f)
+    h0 = bench.kernel_source_hash(str(tmp_path))
+    assert h0 == bench.kernel_source_hash()
+    p = tmp_path / "sl1m_mixed.cu"
+    text = p.read_text()
+    p.write_text("// a new comment\n/* and a\n block one */\n" + text.replace("\n", "\n  ", 3))
+    assert bench.kernel_source_hash(str(tmp_path)) == h0
+    assert "__launch_bounds__(NTHREADS, 3)" in text
+    p.write_text(text.replace("__launch_bounds__(NTHREADS, 3)", "__launch_bounds__(NTHREADS, 2)", 1))
+    assert bench.kernel_source_hash(str(tmp_path)) != h0
+
+
+def test_ncu_traffic_matches_kernel_shape_workload_and_source():
+    wl = "wide-field-dirac-256x256-40320vis"
+    got = bench.ncu_traffic("adj_mixed", 4, 1, 456, wl)
+    assert got is None or got > 0          # None once the kernels change after a capture
+    assert bench.ncu_traffic("adj_mixed", 8, 1, 456, wl) is None
+    assert bench.ncu_traffic("adj_mixed", 4, 2, 456, wl) is None
+    assert bench.ncu_traffic("adj_mixed", 4, 1, 304, wl) is None
+    assert bench.ncu_traffic("adj_mixed", 4, 1, 456, "another-workload") is None
