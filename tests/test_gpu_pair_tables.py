@@ -80,3 +80,26 @@ def test_pair_tables_solve_matches_oracle(ctx):
     img_o, _ = oracle.fista(O, V, lam, L, 12)
     assert np.max(np.abs(img - img_o)) <= 1e-4 * img_o.max()
     P.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_most_antennas_fit_and_match_oracle(ctx, gpu_lib, prec):
+    """300 antennas, the most the gains kernels' shared memory holds (one
+    pixel granule's table of 300 rows, the adjoint's per-warp slices and
+    records): forward and adjoint against the oracle; 301 is refused."""
+    d = synth.random_problem(31, 1500, 300, kinds=(DIRAC, WIDE), gains=True, n_ant=300, uv_max=300,
+                             w_max=100, extent=0.3, sigma_max=0.01)
+    P = ctx.problem()
+    P.set_visibilities(d["uvw"], None, None, d["ant_pair"])
+    P.set_pixels(d["lm"], d["sigma"], d["kind"])
+    P.set_gains(d["gains"])
+    O = oracle.Problem(d["uvw"], d["lm"], d["sigma"], d["kind"], None, d["ant_pair"], d["gains"])
+    rng = np.random.default_rng(6)
+    x = rng.normal(size=300)
+    assert nmax_err(P.forward(x, prec), oracle.forward(O, x)) <= TOL[prec]
+    r = rng.normal(size=1500) + 1j * rng.normal(size=1500)
+    assert nmax_err(P.adjoint(r, prec), oracle.adjoint(O, r)) <= TOL[prec]
+    with pytest.raises(gpu_lib.SL1MError) as e:
+        P.set_gains(np.ones((300, 301), complex))
+    assert e.value.status == gpu_lib.ERR_ARG
+    P.close()
