@@ -273,7 +273,7 @@ int sl1m_server_info(sl1m_ctx* ctx, sl1m_server_info_t* info);
 
 /* Autotuner of the operator kernels' tile shape: for the forward and the
  * adjoint of this problem it times, with CUDA events, every (streamed
- * granules per shared-memory stage: 2, 4 or 8) x (persistent grid: 1 .. occupancy CTAs per SM) of the mixed
+ * granules per shared-memory stage: 2, 4 or 8; the adjoint 2 or 4) x (persistent grid: 1 .. occupancy CTAs per SM) of the mixed
  * no-gains kernels, then at the fastest of those the share npoly (1 or 2 of
  * every 8 pairs) whose sincos runs on the FMA pipe instead of the SFU; with
  * gains or in FP64 only the grid is tuned.  The choice is kept in the context,
@@ -285,7 +285,7 @@ int sl1m_autotune(sl1m_problem* prob, int precision, int32_t* nst_out, int32_t* 
                   int32_t* npoly_out);
 
 /* Set the tile shape the autotuner would choose, for this problem's key
- * (op 0 forward, 1 adjoint): nst 2, 4 or 8,
+ * (op 0 forward, 1 adjoint): nst 2, 4 or 8 (the adjoint 2 or 4),
  * ctas_per_sm from 1 to the kernel's occupancy, npoly 0, 1 or 2.  With gains
  * or in FP64 only ctas_per_sm may differ from the defaults (nst 4, npoly 0).
  * SL1M_ERR_ARG for a shape that does not exist or does not fit. */

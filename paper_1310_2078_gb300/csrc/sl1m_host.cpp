@@ -422,6 +422,8 @@ sl1m_ctx::~sl1m_ctx()
 struct ProblemDev {
     DevSide vis, pix;
     DBuf<int2> ant;
+    DBuf<float4> vgabs;
+    DBuf<float2> r32;
     DBuf<int> vslot, gnb;
     DBuf<int2> gbl;
     DBuf<double2> V;
@@ -595,6 +597,14 @@ int sl1m_problem::rebuild(cudaStream_t st)
         }
         CK(D.ant.upload(a.data(), a.size(), st));
         CK(D.V.upload(Vs.data(), Vs.size(), st));
+        // {u, v, -2 w, u^2 + v^2} in FP32, as the adjoint's Gaussian terms take it
+        std::vector<float4> ga(H.n_pad);
+        for (int i = 0; i < H.n_pad; ++i) {
+            const float4 h = H.hi[i];
+            ga[i] = make_float4(h.x, h.y, -2.0f * h.z, std::fmaf(h.x, h.x, h.y * h.y));
+        }
+        CK(D.vgabs.upload(ga.data(), ga.size(), st));
+        CK(D.r32.upload(nullptr, H.n_pad, st, true));
         vis_orig = H.orig;
         if (n_ant > 0) {
             // each granule's distinct antenna pairs (adjacent after sort_baselines)
@@ -624,6 +634,8 @@ int sl1m_problem::rebuild(cudaStream_t st)
         }
     }
     hp.ant = D.ant.p;
+    hp.vgabs = D.vgabs.p;
+    hp.r32 = D.r32.p;
     hp.vslot = n_ant > 0 ? D.vslot.p : nullptr;
     hp.gbl = n_ant > 0 ? D.gbl.p : nullptr;
     hp.gnb = n_ant > 0 ? D.gnb.p : nullptr;
@@ -714,6 +726,7 @@ size_t sl1m_problem::estimate_bytes() const
         b += nv * 4 + (nv / G) * (NB_MAX * 8 + 4);                                     // pair lists
     }
     b += np * 8 * 4 + nv * 16 * 3;                 // solver vectors
+    b += nv * (16 + 8);                            // the adjoint's FP32 Gaussian terms and residual
     b += (nv + np) * 16 * 3;                       // operator scratch
     return b + (1 << 16);
 }
@@ -833,7 +846,7 @@ size_t sl1m_problem::dev_bytes() const
     };
     side(D.vis);
     side(D.pix);
-    b += D.ant.bytes() + D.vslot.bytes() + D.gbl.bytes() + D.gnb.bytes() + D.V.bytes() + D.pgauss.bytes() + D.pgauss64.bytes() + D.gsig.bytes() +
+    b += D.ant.bytes() + D.vgabs.bytes() + D.r32.bytes() + D.vslot.bytes() + D.gbl.bytes() + D.gnb.bytes() + D.V.bytes() + D.pgauss.bytes() + D.pgauss64.bytes() + D.gsig.bytes() +
          D.gsig64.bytes() + D.gkind.bytes() + D.pghdr.bytes() + D.gains32.bytes() + D.gains64.bytes();
     b += D.x_user.bytes() + D.x_sorted.bytes() + D.adj_sorted.bytes() + D.img_user.bytes() +
          D.r_user.bytes() + D.r_sorted.bytes() + D.fwd_sorted.bytes() + D.vis_user.bytes();
@@ -961,6 +974,11 @@ static int launch_op_class(sl1m_ctx* ctx, Batch& B, int op, int c)
                               ctx->partial_f.p, st));
         prof_end(ctx, tk, 0.0, B.fin_bytes[0]);
     } else {
+        if (B.precision != 0 && c == 0) {         // the mixed no-gains adjoint reads r in FP32
+            int vmax = 1;
+            for (const DevProblem& d : B.hdesc) vmax = std::max(vmax, d.vis.n_pad);
+            CKL(launch_r32(B.desc.p, (int)B.hdesc.size(), vmax, st));
+        }
         prof_begin(ctx, B.precision == 0 ? 1 : 3, tk);
         CKL(launch_adjoint(B.precision, c == 1, B.n_ant_max, B.desc.p, P.dpl.p, P.pl.C, ctx->partial_a.p, st,
                            B.nst[1][c]));
@@ -1542,7 +1560,7 @@ int sl1m_autotune(sl1m_problem* prob, int precision, int32_t* nst_out, int32_t* 
         // best of those, the share of pairs whose sincos runs on the FMA pipe
         std::vector<int> cands = {NST_DEFAULT};
         const bool mixed_plain = precision == SL1M_MIXED && !gains;
-        if (mixed_plain) cands = {2, 4, 8};
+        if (mixed_plain) cands = op == 0 ? std::vector<int>{2, 4, 8} : std::vector<int>{2, 4};
         float best = 1e30f;
         int bcode = NST_DEFAULT, bk = 0;
         const auto time_shape = [&](int code, int k) -> float {
@@ -1608,8 +1626,8 @@ int sl1m_set_tile_shape(sl1m_problem* prob, int precision, int op, int nst, int 
     const bool gains = prob->n_ant > 0;
     if (op < 0 || op > 1 || ctas_per_sm < 1 || npoly < 0 || npoly > 2)
         return sl1m_fail(ctx, SL1M_ERR_ARG, "bad tile shape (op %d, ctas/SM %d, npoly %d)", op, ctas_per_sm, npoly);
-    if (!(nst == 2 || nst == 4 || nst == 8))
-        return sl1m_fail(ctx, SL1M_ERR_ARG, "nst must be 2, 4 or 8");
+    if (!(nst == 2 || nst == 4 || (nst == 8 && op == 0)))
+        return sl1m_fail(ctx, SL1M_ERR_ARG, "nst must be 2, 4 or 8 (the adjoint: 2 or 4)");
     if ((gains || precision == SL1M_FP64) && (nst != NST_DEFAULT || npoly != 0))
         return sl1m_fail(ctx, SL1M_ERR_ARG, "with gains or in FP64 only the CTAs per SM can be set");
     RET(prob->rebuild(ctx->stream));

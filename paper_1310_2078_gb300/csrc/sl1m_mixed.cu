@@ -31,6 +31,8 @@
 // complete on mbarriers, issued ahead of use; units = (owned block, streamed
 // granule) are spread over a persistent grid stream-K style (Plan); partials
 // are summed by the finish kernels in a fixed order.
+#include <algorithm>
+
 #include "sl1m_dev.h"
 #include "sl1m_devfn.cuh"
 #include "sl1m_kernels.h"
@@ -643,26 +645,67 @@ __device__ __forceinline__ void adj_gauss_tile(const float4* __restrict__ s_off,
     }
 }
 
+// Adjoint stage buffers in dynamic shared memory: two of them, each holding
+// NSA streamed visibility granules as they sit in HBM -- offsets, offset
+// residuals, the Gaussian form {u, v, -2 w, u^2 + v^2}, the residual r in
+// FP32 (written by r32_kernel just before the launch) and the granule centres
+// and extents -- filled by bulk (TMA) copies on one mbarrier per buffer; the
+// copies of stage s + 1 are issued when stage s starts.
+template <int NSA>
+struct AdjStage {
+    static constexpr int OFF = 0;                      // float4 [NSA][G]
+    static constexpr int LO = OFF + NSA * G * 16;      // float4 [NSA][G]
+    static constexpr int GA = LO + NSA * G * 16;       // float4 [NSA][G]
+    static constexpr int R = GA + NSA * G * 16;        // float2 [NSA][G]
+    static constexpr int CEN = R + NSA * G * 8;        // float4 [3][NSA]: centre hi, centre lo, extent
+    static constexpr int BYTES = CEN + 48 * NSA;       // a multiple of 16
+};
+
+template <int NSA>
+__device__ __forceinline__ void adj_stage_load(unsigned char* buf, const DevProblem& P, int gs, int ns,
+                                               unsigned long long* bar)
+{
+    using S = AdjStage<NSA>;
+    const size_t e = (size_t)gs * G;
+    const unsigned n4 = (unsigned)(ns * G * 16), n2 = (unsigned)(ns * G * 8), nc = (unsigned)(ns * 16);
+    fence_proxy_async_smem();              // the buffer's last readers (generic proxy) are done
+    mbar_arrive_expect(bar, 3 * n4 + n2 + 3 * nc);
+    bulk_copy(buf + S::OFF, P.vis.off + e, n4, bar);
+    bulk_copy(buf + S::LO, P.vis.offlo + e, n4, bar);
+    bulk_copy(buf + S::GA, P.vgabs + e, n4, bar);
+    bulk_copy(buf + S::R, P.r32 + e, n2, bar);
+    bulk_copy(buf + S::CEN, P.vis.cen_hi + gs, nc, bar);
+    bulk_copy(buf + S::CEN + 16 * NSA, P.vis.cen_lo + gs, nc, bar);
+    bulk_copy(buf + S::CEN + 32 * NSA, P.vis.ext + gs, nc, bar);
+}
+
 // Owned: pixels (warp = one pixel granule, lane = 2 pixels).
-// Streamed: visibility granules through shared memory, NSA per stage.
+// Streamed: visibility granules through the two stage buffers, NSA per stage,
+// one CTA barrier per stage (it frees the buffer the next copies go to).
 template <int NSA, int NPOLY = 0>
 __global__ void __launch_bounds__(NTHREADS, 3)
 adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ plp, double* __restrict__ partial)
 {
-    __shared__ float4 s_off[NSA][G];            // {du, dv, dw, W}
-    __shared__ float4 s_lo[NSA][G];
-    __shared__ float4 s_abs[NSA][G];            // {u, v, -2 w, u^2 + v^2} (Gaussian owners)
-    __shared__ float2 s_r[NSA][G];
+    using S = AdjStage<NSA>;
+    extern __shared__ __align__(128) unsigned char s_dyn[];    // two stage buffers
     __shared__ float s_B[BLK_GRAN][NSA][G];
     __shared__ float4 s_gw[BLK_GRAN][NSA][G];   // Gaussian owners: {gamr, coef, r're, r'im}
-    __shared__ float4 s_cen[NSA][3];
+    __shared__ __align__(8) unsigned long long s_sbar[2];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Plan pl = *plp;
     const long long c = blockIdx.x;
     long long u, u_end;
     cta_range(pl, c, u, u_end);
-
+    int scur = 0;             // stage buffer of the current stage
+    unsigned spar = 0;        // parity of the next wait on stage buffer b (bit b)
+    bool fault = false;       // a bounded wait gave up
+    if (threadIdx.x == 0) {
+        mbar_init(&s_sbar[0], 1);
+        mbar_init(&s_sbar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
     while (u < u_end) {
         const int p = find_prob(pl, u);
         const DevProblem& P = probs[p];
@@ -676,6 +719,9 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
         const int blk = (int)(loc / upb);
         const int g0 = (int)(loc % upb);
         const int g1 = (int)min((long long)upb, (long long)g0 + (u_end - u));
+        // the range's first stage; its buffer's last readers finished before
+        // the barrier of the previous range's last stage
+        if (threadIdx.x == 0) adj_stage_load<NSA>(s_dyn + scur * S::BYTES, P, g0, min(NSA, g1 - g0), &s_sbar[scur]);
         const int pgi = blk * BLK_GRAN + warp;
         const bool pg_ok = pgi < P.pix.n_gran;
         const int e0 = (pg_ok ? pgi : 0) * G + lane;     // this lane's pixels: e0, e0 + 32
@@ -705,33 +751,29 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
 
         for (int gs = g0; gs < g1; gs += NSA) {
             const int ns = min(NSA, g1 - gs);
-            __syncthreads();
-            for (int t = threadIdx.x; t < ns * G; t += NTHREADS) {
-                const int q = t / G, i = t % G;
-                const int e = (gs + q) * G + i;
-                s_off[q][i] = P.vis.off[e];
-                s_lo[q][i] = P.vis.offlo[e];
-                s_abs[q][i] = vis_for_gauss(P.vis.hi[e]);
-                const double2 rr = R[e];
-                s_r[q][i] = make_float2((float)rr.x, (float)rr.y);
-            }
-            if (threadIdx.x < ns) {
-                const int g = gs + threadIdx.x;
-                s_cen[threadIdx.x][0] = P.vis.cen_hi[g];
-                s_cen[threadIdx.x][1] = P.vis.cen_lo[g];
-                s_cen[threadIdx.x][2] = P.vis.ext[g];
-            }
-            __syncthreads();
+            __syncthreads();                       // the previous stage is consumed
+            if (threadIdx.x == 0 && gs + NSA < g1)  // prefetch the next stage
+                adj_stage_load<NSA>(s_dyn + (scur ^ 1) * S::BYTES, P, gs + NSA, min(NSA, g1 - gs - NSA),
+                                    &s_sbar[scur ^ 1]);
+            if (!mbar_wait(&s_sbar[scur], (spar >> scur) & 1u)) fault = true;
+            spar ^= 1u << scur;
+            const unsigned char* sb = s_dyn + scur * S::BYTES;
+            scur ^= 1;
+            const float4* const b_off = reinterpret_cast<const float4*>(sb + S::OFF);
+            const float4* const b_lo = reinterpret_cast<const float4*>(sb + S::LO);
+            const float4* const b_ga = reinterpret_cast<const float4*>(sb + S::GA);
+            const float2* const b_r = reinterpret_cast<const float2*>(sb + S::R);
+            const float4* const b_cen = reinterpret_cast<const float4*>(sb + S::CEN);
             for (int q = 0; q < ns; ++q) {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int k = lane + 32 * h;
-                    float b = frac_dot3(ch, cl, s_off[q][k], s_lo[q][k]);
+                    float b = frac_dot3(ch, cl, b_off[q * G + k], b_lo[q * G + k]);
                     if (gauss) {
-                        const float4 va = s_abs[q][k];
+                        const float4 va = b_ga[q * G + k];
                         const GaussConst gc = gauss_const(va.x, va.y, -0.5f * va.z, sigma);
                         b = frac_turns(b + gc.cphase);
-                        const float2 rr = s_r[q][k];
+                        const float2 rr = b_r[q * G + k];
                         // r' = id (1 - i beta) r
                         s_gw[warp][q][k] = make_float4(gc.gamr, gc.coef, gc.id * fmaf(gc.beta, rr.y, rr.x),
                                                        gc.id * fmaf(-gc.beta, rr.x, rr.y));
@@ -741,8 +783,8 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
             }
             __syncwarp();
             for (int q = 0; q < ns; ++q) {
-                const float4 yc_h = s_cen[q][0], yc_l = s_cen[q][1];
-                const bool exact = dot3(ext, s_cen[q][2]) > D_MAX;
+                const float4 yc_h = b_cen[q], yc_l = b_cen[NSA + q];
+                const bool exact = dot3(ext, b_cen[2 * NSA + q]) > D_MAX;
                 float C[2];
 #pragma unroll
                 for (int r = 0; r < 2; ++r) C[r] = frac_dot3(xh[r], P.pix.lo[eidx[r]], yc_h, yc_l);
@@ -753,10 +795,10 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                     if (exact) {
                         const float4 dxt[2] = {P.pix.off[eidx[0]], P.pix.off[eidx[1]]},
                                  dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
-                        adj_dirac_tile<false, true>(s_off[q], s_lo[q], s_r[q], s_B[warp][q], ng, C, dxt,
+                        adj_dirac_tile<false, true>(b_off + q * G, b_lo + q * G, b_r + q * G, s_B[warp][q], ng, C, dxt,
                                                     dxl, acc);
                     } else {
-                        adj_dirac_tile<false, false, NoGain, NPOLY>(s_off[q], s_lo[q], s_r[q], s_B[warp][q],
+                        adj_dirac_tile<false, false, NoGain, NPOLY>(b_off + q * G, b_lo + q * G, b_r + q * G, s_B[warp][q],
                                                                     ng, Cr, dx,
                                                      dx, acc);
                     }
@@ -764,11 +806,11 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                     if (exact) {
                         const float4 dxt[2] = {P.pix.off[eidx[0]], P.pix.off[eidx[1]]},
                                  dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
-                        if (par) adj_gauss_tile<false, true, true>(s_off[q], s_lo[q], s_abs[q], s_B[warp][q], s_gw[warp][q], ng, C, dxt, dxl, pgd, acc);
-                        else adj_gauss_tile<false, true, false>(s_off[q], s_lo[q], s_abs[q], s_B[warp][q], s_gw[warp][q], ng, C, dxt, dxl, pgd, acc);
+                        if (par) adj_gauss_tile<false, true, true>(b_off + q * G, b_lo + q * G, b_ga + q * G, s_B[warp][q], s_gw[warp][q], ng, C, dxt, dxl, pgd, acc);
+                        else adj_gauss_tile<false, true, false>(b_off + q * G, b_lo + q * G, b_ga + q * G, s_B[warp][q], s_gw[warp][q], ng, C, dxt, dxl, pgd, acc);
                     } else {
-                        if (par) adj_gauss_tile<false, false, true>(s_off[q], s_lo[q], s_abs[q], s_B[warp][q], s_gw[warp][q], ng, Cr, dx, dx, pgd, acc);
-                        else adj_gauss_tile<false, false, false>(s_off[q], s_lo[q], s_abs[q], s_B[warp][q], s_gw[warp][q], ng, Cr, dx, dx, pgd, acc);
+                        if (par) adj_gauss_tile<false, false, true>(b_off + q * G, b_lo + q * G, b_ga + q * G, s_B[warp][q], s_gw[warp][q], ng, Cr, dx, dx, pgd, acc);
+                        else adj_gauss_tile<false, false, false>(b_off + q * G, b_lo + q * G, b_ga + q * G, s_B[warp][q], s_gw[warp][q], ng, Cr, dx, dx, pgd, acc);
                     }
                 }
 #pragma unroll
@@ -783,6 +825,7 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
         }
         u += g1 - g0;
     }
+    if (fault) atomicOr(&g_wait_fault, 1u);
 }
 
 // Adjoint with gains.  The CTA's 8 warps share one owned pixel granule at a
@@ -999,6 +1042,30 @@ int fwd_smem_bytes(int n_ant, bool gains, int nst)
     return fwd_stage_bytes<1>() + (2 * t <= FWD_GAINS_DBL_MAX ? 2 * t : t);
 }
 int adj_gains_smem_bytes(int n_ant) { return BLK_GRAN * AdjRaw::BYTES + gains_table_bytes(n_ant); }
+// the no-gains adjoint: two stage buffers
+static int adj_stage_bytes_of(int nst)
+{
+    return 2 * (nst <= 2 ? AdjStage<2>::BYTES : AdjStage<4>::BYTES);
+}
+
+// r32 = the adjoint's input residual in FP32, for every problem of the batch
+// that takes part in the coming adjoint (blockIdx.y = problem).
+__global__ void r32_kernel(const DevProblem* __restrict__ probs)
+{
+    const DevProblem& P = probs[blockIdx.y];
+    const double2* R;
+    if (!adj_role(P, R) || !P.r32) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.vis.n_pad; i += gridDim.x * blockDim.x) {
+        const double2 v = R[i];
+        P.r32[i] = make_float2((float)v.x, (float)v.y);
+    }
+}
+cudaError_t launch_r32(const DevProblem* probs, int n_probs, int max_vis_pad, cudaStream_t st)
+{
+    const dim3 grid((unsigned)std::max(1, std::min(1024, (max_vis_pad + 255) / 256)), (unsigned)n_probs);
+    r32_kernel<<<grid, 256, 0, st>>>(probs);
+    return cudaGetLastError();
+}
 
 cudaError_t wait_fault_read(unsigned* host_flag, cudaStream_t st)
 {
@@ -1038,10 +1105,12 @@ static FwdKernel fwd_kernel_of(int code)
     const int nst = shape_nst(code), np = shape_npoly(code);
     return nst <= 2 ? fwd_by_poly<2>(np) : nst <= 4 ? fwd_by_poly<4>(np) : fwd_by_poly<8>(np);
 }
+// The no-gains adjoint stages 2 or 4 granules (with 8, its stage buffers and
+// per-warp records would leave room for 1 CTA per SM).
 static AdjKernel adj_kernel_of(int code)
 {
     const int nst = shape_nst(code), np = shape_npoly(code);
-    return nst <= 2 ? adj_by_poly<2>(np) : nst <= 4 ? adj_by_poly<4>(np) : adj_by_poly<8>(np);
+    return nst <= 2 ? adj_by_poly<2>(np) : adj_by_poly<4>(np);
 }
 
 cudaError_t launch_forward_mixed(bool gains, int n_ant, int nst, const DevProblem* probs, const Plan* plp, int C,
@@ -1060,7 +1129,7 @@ cudaError_t launch_adjoint_mixed(bool gains, int n_ant, int nst, const DevProble
                                  double* partial, cudaStream_t st)
 {
     if (gains) adj_mixed_gains_kernel<<<C, NTHREADS, adj_gains_smem_bytes(n_ant), st>>>(probs, plp, partial);
-    else adj_kernel_of(nst)<<<C, NTHREADS, 0, st>>>(probs, plp, partial);
+    else adj_kernel_of(nst)<<<C, NTHREADS, adj_stage_bytes_of(shape_nst(nst)), st>>>(probs, plp, partial);
     return cudaGetLastError();
 }
 
@@ -1088,7 +1157,9 @@ int occupancy_mixed(int op, bool gains, int n_ant, int nst)
         }
         return occ_of(adj_mixed_gains_kernel, sm);
     }
-    return occ_of(adj_kernel_of(nst), 0);
+    const int sm = adj_stage_bytes_of(shape_nst(nst));   // fixed per tile shape
+    cudaFuncSetAttribute(adj_kernel_of(nst), cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    return occ_of(adj_kernel_of(nst), sm);
 }
 
 }  // namespace sl1m

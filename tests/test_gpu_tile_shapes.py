@@ -28,7 +28,8 @@ def case(gpu_lib):
     ctx.close()
 
 
-SHAPES = [(op, nst, npoly) for op in (0, 1) for nst in (2, 4, 8) for npoly in (0, 1, 2)]
+SHAPES = [(0, nst, npoly) for nst in (2, 4, 8) for npoly in (0, 1, 2)] + \
+         [(1, nst, npoly) for nst in (2, 4) for npoly in (0, 1, 2)]
 
 
 @pytest.mark.parametrize("op,nst,npoly", SHAPES)
@@ -54,7 +55,7 @@ def test_fma_sincos_changes_results_only_at_rounding_level(gpu_lib, case):
 
 def test_bad_shapes_are_refused(gpu_lib, case):
     ctx, P, *_ = case
-    for args in ((0, 3, 1, 0), (1, 0, 1, 0), (0, 4, 1, 3), (2, 4, 1, 0), (0, 4, 99, 0), (0, 0, 1, 0)):
+    for args in ((0, 3, 1, 0), (1, 0, 1, 0), (0, 4, 1, 3), (2, 4, 1, 0), (0, 4, 99, 0), (0, 0, 1, 0), (1, 8, 1, 0)):
         with pytest.raises(gpu_lib.SL1MError) as e:
             P.set_tile_shape(*args)
         assert e.value.status == gpu_lib.ERR_ARG
