@@ -79,9 +79,25 @@ def dist_init():
     if ws > 1:
         import torch.distributed as dist
         import torch
-        torch.cuda.set_device(local)
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return ws, rank, local
+
+
+def job_totals(seconds: float, units: float, ws: int, device="cpu"):
+    """(slowest rank's seconds, all ranks' units): the whole job's time and
+    work.  Every rank calls it (two all-reduces over the process group);
+    with one rank it returns its arguments."""
+    if ws <= 1:
+        return float(seconds), float(units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
 
 
 def workload(cfg: int, rank: int = 0, small: bool = False, args=None):
@@ -528,14 +544,7 @@ def main():
     counters = ctx.counters()
     prof = {k: ctx.profile_read(k) for k in sl1m.KERNEL_IDS}
     op_pairs = sum(prof[k]["pairs"] for k in ("fwd_fp64", "adj_fp64", "fwd_mixed", "adj_mixed"))
-    if ws > 1:
-        t = torch.tensor([T, op_pairs], dtype=torch.float64, device=f"cuda:{dev}")
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax[0:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t[1:2], op=torch.distributed.ReduceOp.SUM)
-        T_job, pairs_job = float(tmax[0]), float(t[1])
-    else:
-        T_job, pairs_job = T, op_pairs
+    T_job, pairs_job = job_totals(T, op_pairs, ws, f"cuda:{dev}")
     value = pairs_job / T_job
     solves_per_s = ws * args.steps / T_job
 
@@ -624,11 +633,7 @@ def run_e2e(ctx, w, V, lam, prec, args, sl1m, stream, ws=1):
         Q.close()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([dt, pairs], dtype=torch.float64, device=f"cuda:{torch.cuda.current_device()}")
-        torch.distributed.all_reduce(t[0:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t[1:2], op=torch.distributed.ReduceOp.SUM)
-        dt, pairs = float(t[0]), float(t[1])
+    dt, pairs = job_totals(dt, pairs, ws, f"cuda:{torch.cuda.current_device()}")
     c = ctx.counters()
     return {"value": pairs / dt, "unit": "pairs/s", "steps": steps,
             "h2d_bytes_per_step": c["h2d_bytes"] // steps, "d2h_bytes_per_step": c["d2h_bytes"] // steps,

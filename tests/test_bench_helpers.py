@@ -1,4 +1,5 @@
-"""The bench's roofline arithmetic and its bookkeeping of ncu counters (no GPU)."""
+"""The bench's roofline arithmetic, its bookkeeping of ncu counters and its
+multi-rank totals (no GPU; the totals over gloo ranks on CPU)."""
 import os
 import shutil
 import sys
@@ -58,3 +59,40 @@ def test_ncu_traffic_matches_kernel_shape_workload_and_source():
     assert bench.ncu_traffic("adj_mixed", 4, 2, 456, wl) is None
     assert bench.ncu_traffic("adj_mixed", 4, 1, 304, wl) is None
     assert bench.ncu_traffic("adj_mixed", 4, 1, 456, "another-workload") is None
+
+
+def _totals_worker(rank, world, port, results):
+    sys.path.insert(0, ROOT)
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    import torch.distributed as dist
+    import bench as b
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # rank r took 1.5 + r seconds for 10 * (r + 1) units
+    results[rank] = b.job_totals(1.5 + rank, 10.0 * (rank + 1), world)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_job_totals_take_the_slowest_rank_and_all_ranks_work():
+    """With several ranks the bench's figures are all ranks' units over the
+    slowest rank's time, the same on every rank; with one rank, its own."""
+    import socket
+    torch = pytest.importorskip("torch")
+    mp = torch.multiprocessing
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    ctx = mp.get_context("spawn")
+    results = ctx.Manager().dict()
+    world = 3
+    procs = [ctx.Process(target=_totals_worker, args=(r, world, port, results)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    assert all(p.exitcode == 0 for p in procs), [p.exitcode for p in procs]
+    for r in range(world):
+        assert results[r] == (3.5, 60.0)
+    assert bench.job_totals(2.0, 7.0, 1) == (2.0, 7.0)

@@ -1,12 +1,19 @@
 """Multi-process sharding arithmetic on CPU (gloo, world_size 2).
 
-A single SL1M solve shards by visibilities: each rank holds N_v/P
-visibilities and a replica of the image; the forward is local, the adjoint
-yields partial images that are all-reduced (one exchange of N_p reals per
-iteration), and the FISTA update is replicated.  These tests run the FP64
-oracle on each rank's shard and check the all-reduced results against the
-unsharded oracle.  (Every box this build runs on has one GPU, so the sharded
-path is exercised here, on CPU ranks.)
+A single SL1M solve shards two ways, each with one exchange per iteration:
+
+* by visibilities: each rank holds N_v/P visibilities and a replica of the
+  image; the forward is local, the adjoint yields partial images that are
+  all-reduced (N_p reals), and the FISTA update is replicated;
+* by pixels: each rank holds N_p/P pixels and their image entries; the
+  forward yields partial visibilities that are all-reduced (2 N_v reals),
+  the residual is replicated, and the adjoint and the threshold step are
+  local.
+
+The cheaper split exchanges min(N_p, 2 N_v) reals per iteration.  These tests
+run the FP64 oracle on each rank's shard and check the all-reduced results
+against the unsharded oracle.  (Every box this build runs on has one GPU, so
+the sharded paths are exercised here, on CPU ranks.)
 """
 import os
 import socket
@@ -89,16 +96,92 @@ def _worker(rank, world, port, results):
     dist.destroy_process_group()
 
 
-def test_visibility_split_allreduce_matches_unsharded_oracle():
+def _worker_pix(rank, world, port, results):
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import oracle
+    d, x, rng = _problem()
+    Ofull = oracle.Problem(d["uvw"], d["lm"], d["sigma"], d["kind"], d["weights"], d["ant_pair"],
+                           d["gains"])
+    V = oracle.forward(Ofull, x) + 0.01 * (rng.normal(size=301) + 1j * rng.normal(size=301))
+    n_pix = d["lm"].shape[0]
+    idx = np.array_split(np.arange(n_pix), world)[rank]
+    O = oracle.Problem(d["uvw"], d["lm"][idx], d["sigma"][idx], d["kind"][idx], d["weights"],
+                       d["ant_pair"], d["gains"][idx])
+    W = d["weights"]
+    exchanged = [0]
+
+    def forward_sum(xl):
+        # partial visibilities of the local pixels, all-reduced as 2 N_v reals
+        v = oracle.forward(O, xl)
+        t = torch.from_numpy(np.stack([v.real, v.imag], axis=-1))
+        dist.all_reduce(t)
+        exchanged[0] += t.numel()
+        return t[:, 0].numpy() + 1j * t[:, 1].numpy()
+
+    Ax = forward_sum(x[idx])
+    g = oracle.adjoint(O, W * (Ax - V))       # local columns of the gradient
+    L, _ = oracle.power(Ofull, max_iter=500, tol=1e-13)
+    lam = 0.05
+    I_prev = np.zeros(len(idx))
+    y = I_prev.copy()
+    t = 1.0
+    exchanged[0] = 0
+    for _ in range(30):
+        gl = oracle.adjoint(O, W * (forward_sum(y) - V))
+        v = y - gl / L
+        I = np.where(v > lam / L, v - lam / L, 0.0)
+        tn = 0.5 * (1 + np.sqrt(1 + 4 * t * t))
+        y = I + (t - 1) / tn * (I - I_prev)
+        I_prev, t = I, tn
+    img_parts = torch.zeros(n_pix, dtype=torch.float64)
+    img_parts[idx] = torch.from_numpy(I)
+    dist.all_reduce(img_parts)                 # gather: disjoint supports
+    g_parts = torch.zeros(n_pix, dtype=torch.float64)
+    g_parts[idx] = torch.from_numpy(g)
+    dist.all_reduce(g_parts)
+    if rank == 0:
+        full_V = oracle.forward(Ofull, x)
+        full_g = oracle.adjoint(Ofull, W * (full_V - V))
+        img, _ = oracle.fista(Ofull, V, lam, L, 30)
+        results["fwd_err"] = float(np.max(np.abs(Ax - full_V)) / np.max(np.abs(full_V)))
+        results["grad_err"] = float(np.max(np.abs(g_parts.numpy() - full_g)) / np.max(np.abs(full_g)))
+        results["img_err"] = float(np.max(np.abs(img_parts.numpy() - img)) / max(img.max(), 1e-300))
+        results["reals_per_iter"] = exchanged[0] / 30
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def _run(target, world=2):
     ctx = mp.get_context("spawn")
     mgr = ctx.Manager()
     results = mgr.dict()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, results)) for r in range(2)]
+    procs = [ctx.Process(target=target, args=(r, world, port, results)) for r in range(world)]
     for p in procs:
         p.start()
     for p in procs:
         p.join(timeout=300)
     assert all(p.exitcode == 0 for p in procs), [p.exitcode for p in procs]
+    return dict(results)
+
+
+def test_visibility_split_allreduce_matches_unsharded_oracle():
+    results = _run(_worker)
     assert results["grad_err"] < 1e-12
     assert results["img_err"] < 1e-10
+
+
+def test_pixel_split_allreduce_matches_unsharded_oracle():
+    """The forward's partial sums over each rank's pixels, all-reduced, are
+    the full forward; the local adjoint columns and threshold steps then give
+    the unsharded gradient and FISTA image; one exchange of 2 N_v reals per
+    iteration."""
+    results = _run(_worker_pix)
+    assert results["fwd_err"] < 1e-12
+    assert results["grad_err"] < 1e-12
+    assert results["img_err"] < 1e-10
+    assert results["reals_per_iter"] == 2 * 301
