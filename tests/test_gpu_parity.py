@@ -253,6 +253,13 @@ def test_invalid_arguments_rejected(ctx, gpu_lib):
         P.set_pixels(np.array([[0.1, 0.1]]), sigma=np.array([0.0]), kind=np.array([2]))
     with pytest.raises(gpu_lib.SL1MError):
         P.set_visibilities(np.array([[np.nan, 0.0, 0.0]]))
+    # empty inputs: a problem needs at least one visibility and one pixel
+    with pytest.raises(gpu_lib.SL1MError) as e:
+        P.set_visibilities(np.zeros((0, 3)))
+    assert e.value.status == gpu_lib.ERR_ARG
+    with pytest.raises(gpu_lib.SL1MError) as e:
+        P.set_pixels(np.zeros((0, 2)))
+    assert e.value.status == gpu_lib.ERR_ARG
     with pytest.raises(gpu_lib.SL1MError) as e:
         P.forward(np.zeros(1))
     assert e.value.status == gpu_lib.ERR_STATE
