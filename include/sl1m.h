@@ -82,7 +82,8 @@ int sl1m_create(sl1m_ctx** out, int device, void* cuda_stream);
 /* Destroy a context and every problem created in it. */
 int sl1m_destroy(sl1m_ctx* ctx);
 
-/* Last error message of the context ("" if none).  Valid until the next call. */
+/* Last error message of the context ("" if none).  The text is a copy held
+ * per calling thread, valid until that thread calls this function again. */
 const char* sl1m_last_error(const sl1m_ctx* ctx);
 
 /* Create / destroy an (empty) deconvolution problem. */

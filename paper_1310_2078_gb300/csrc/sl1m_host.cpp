@@ -30,6 +30,7 @@ int sl1m_fail(sl1m_ctx* ctx, int code, const char* fmt, ...)
         va_start(ap, fmt);
         vsnprintf(buf, sizeof buf, fmt, ap);
         va_end(ap);
+        std::lock_guard<std::mutex> lk(ctx->err_mu);
         ctx->err = buf;
     }
     return code;
@@ -1193,7 +1194,16 @@ int sl1m_destroy(sl1m_ctx* ctx)
     return SL1M_OK;
 }
 
-const char* sl1m_last_error(const sl1m_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+// A copy per calling thread, so that a message the server thread writes
+// meanwhile cannot invalidate the pointer returned here.
+const char* sl1m_last_error(const sl1m_ctx* ctx)
+{
+    if (!ctx) return "null context";
+    thread_local std::string copy;
+    std::lock_guard<std::mutex> lk(ctx->err_mu);
+    copy = ctx->err;
+    return copy.c_str();
+}
 
 #define NOT_WHILE_SERVING(ctx)                                                                   \
     do {                                                                                         \

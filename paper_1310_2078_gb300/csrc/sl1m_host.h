@@ -4,6 +4,7 @@
 
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -136,7 +137,8 @@ struct sl1m_ctx {
     cudaStream_t upstream = nullptr;     // uploads of problems joining a running server
     bool own_stream = false;
     int num_sms = 1;
-    std::string err;
+    std::string err;                     // last error message, guarded by err_mu: a running
+    mutable std::mutex err_mu;           // server thread reports failures here too
     DBuf<double2> partial_f;
     DBuf<double> partial_a;
     std::vector<sl1m_problem*> problems;

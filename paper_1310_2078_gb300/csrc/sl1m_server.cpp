@@ -7,6 +7,10 @@
 // `ticks_per_round` times, reads the phase of every solve, and retires the
 // finished ones (image to the caller's order, stats, latency).  Every solve
 // keeps its own state on the device (phase machine of the scalars kernel).
+//
+// Only the request loop changes `active` and the counters, and it does so
+// under `mu`, which the caller-side calls (submit, poll, wait, info) take to
+// read them; the loop reads its own list without the lock.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -59,7 +63,6 @@ struct Server {
     double max_pairs = 4e9;
     bool stop = false, running = false;
     long long finished = 0, max_active = 0, ticks = 0, rounds = 0;
-    std::string err;
     Batch batch;
 };
 
@@ -129,8 +132,10 @@ static void server_loop(Server* Sp)
             const int rc = batch_ticks(ctx, S.batch, S.ticks_per_round);
             if (rc != SL1M_OK) {
                 for (Request* r : S.active) retire(S, r, rc);
+                std::lock_guard<std::mutex> lk(S.mu);
                 S.active.clear();
             } else {
+                std::lock_guard<std::mutex> lk(S.mu);
                 S.ticks += S.ticks_per_round;
             }
         }
@@ -155,9 +160,13 @@ static void server_loop(Server* Sp)
                     keep.push_back(S.active[i]);
                 }
             }
+            std::lock_guard<std::mutex> lk(S.mu);
             S.active.swap(keep);
         }
-        S.rounds += 1;
+        {
+            std::lock_guard<std::mutex> lk(S.mu);
+            S.rounds += 1;
+        }
         if (changed) {
             {
                 std::lock_guard<std::mutex> lk(S.mu);
@@ -174,6 +183,7 @@ static void server_loop(Server* Sp)
                 const int rc = batch_set(ctx, S.batch, probs, descs, S.precision, true);
                 if (rc != SL1M_OK) {
                     for (Request* r : S.active) retire(S, r, rc);
+                    std::lock_guard<std::mutex> lk(S.mu);
                     S.active.clear();
                 }
             }
@@ -238,7 +248,7 @@ int sl1m_server_submit(sl1m_ctx* ctx, sl1m_problem* prob, const sl1m_solve_opts*
 {
     if (!ctx || !prob || !o || !ticket) return sl1m_fail(ctx, SL1M_ERR_ARG, "null argument");
     Server* S = ctx->server;
-    if (!S || !S->running || S->stop) return sl1m_fail(ctx, SL1M_ERR_STATE, "no server running");
+    if (!S) return sl1m_fail(ctx, SL1M_ERR_STATE, "no server running");
     if (prob->ctx != ctx) return sl1m_fail(ctx, SL1M_ERR_ARG, "problem belongs to another context");
     if (prob->in_server) return sl1m_fail(ctx, SL1M_ERR_BUSY, "problem already queued");
     if (prob->n_vis <= 0 || prob->n_pix <= 0) return sl1m_fail(ctx, SL1M_ERR_STATE, "problem incomplete");
@@ -256,6 +266,7 @@ int sl1m_server_submit(sl1m_ctx* ctx, sl1m_problem* prob, const sl1m_solve_opts*
     }
     r->t_submit = now_s();
     std::lock_guard<std::mutex> lk(S->mu);
+    if (!S->running || S->stop) return sl1m_fail(ctx, SL1M_ERR_STATE, "no server running");
     r->ticket = S->next_ticket++;
     *ticket = r->ticket;
     prob->in_server = true;
