@@ -6,6 +6,11 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+# A directory holding another copy of the `oracle` package, imported in its
+# place (tests/test_oracle_mutants.py runs the pins against planted mistakes).
+_ORACLE_UNDER_TEST = os.environ.get("SL1M_ORACLE_UNDER_TEST")
+if _ORACLE_UNDER_TEST:
+    sys.path.insert(0, _ORACLE_UNDER_TEST)
 
 
 def pytest_configure(config):

@@ -271,6 +271,22 @@ def test_power_iteration_single_pixel_is_exact():
     assert abs(L - np.sum(d["weights"] * np.abs(A) ** 2)) < 1e-12 * L
 
 
+def test_power_iteration_from_the_unit_start_vector():
+    """N_p Dirac pixels all at the phase centre: every entry is exactly 1, so
+    Re(A^H W A) = (sum_k W_k) J, whose top eigenvector is the start vector
+    1/sqrt(N_p) (reading R8).  One step gives L = N_p sum W exactly, and the
+    second step, which changes nothing, ends the iteration."""
+    rng = np.random.default_rng(44)
+    n_vis, n_pix = 37, 9
+    W = rng.uniform(0.5, 2.0, n_vis)
+    P = oracle.Problem(rng.uniform(-50, 50, size=(n_vis, 3)), np.zeros((n_pix, 2)), weights=W)
+    want = n_pix * W.sum()
+    L1, it1 = oracle.power(P, max_iter=1)
+    assert it1 == 1 and abs(L1 - want) <= 1e-12 * want
+    L, it = oracle.power(P, max_iter=50, tol=1e-6)
+    assert it == 2 and abs(L - want) <= 1e-12 * want
+
+
 @pytest.mark.parametrize("kw", [dict(), dict(kinds=(DIRAC, PAR), weights=True, gains=True)])
 def test_power_iteration_matches_dense_eigensolver(kw):
     P, d = _problem(43, 80, 40, **kw)
@@ -369,6 +385,33 @@ def test_fista_matches_brute_force_and_rate_bound(seed):
     assert abs(st["E"] - Fs) < 1e-10 * Fs
 
 
+@pytest.mark.parametrize("solver", ["fista", "mfista"])
+def test_warm_start_at_the_minimiser_is_a_fixed_point(solver):
+    """Started at the enumerated minimiser x*, which the proximal gradient
+    step T(x - grad/L) leaves in place (its optimality conditions), the
+    first step returns x*: FISTA's I_1 and MFISTA's proximal point z_1.
+    Started at zero, the same step lands elsewhere."""
+    P, d = _problem(62, 30, 6, kinds=(DIRAC, PAR), weights=True, uv_max=40, w_max=10,
+                    extent=0.2, sigma_max=0.02)
+    A = _dense(P)
+    W = d["weights"]
+    rng = np.random.default_rng(62)
+    xt = np.abs(rng.normal(size=6)) * (rng.random(6) < 0.5)
+    V = A @ xt + 0.05 * (rng.normal(size=30) + 1j * rng.normal(size=30))
+    lam = 0.5
+    xs, _ = brute_force_l1(A, W, V, lam)
+    B, _ = _normal_eqs(A, W, V)
+    L = np.linalg.eigvalsh(B)[-1]
+    if solver == "fista":
+        warm, _ = oracle.fista(P, V, lam, L, max_iter=1, x0=xs)
+        cold, _ = oracle.fista(P, V, lam, L, max_iter=1)
+    else:
+        warm = oracle.mfista(P, V, lam, L, 1, x0=xs, trace=True)[2]["z"][0]
+        cold = oracle.mfista(P, V, lam, L, 1, trace=True)[2]["z"][0]
+    assert np.max(np.abs(warm - xs)) < 1e-9 * max(1.0, xs.max())
+    assert np.max(np.abs(cold - xs)) > 1e-3 * xs.max()
+
+
 def test_fista_kkt_at_convergence():
     """I_j > 0 => Re(A^H W(AI - V))_j = -lam;  I_j = 0 => >= -lam."""
     P, d = _problem(71, 120, 40, kinds=(DIRAC, WIDE), gains=True, uv_max=60, w_max=20,
@@ -418,6 +461,10 @@ def test_stopping_rule_relative_change_of_E():
     # one more step changes E by no more than the tolerance's order
     img2, st2 = oracle.fista(P, V, 0.2, L, max_iter=st["iters"] - 1)
     assert abs(st["E"] - st2["E"]) <= 1e-6 * st2["E"] * (1 + 1e-9)
+    # and it is the first step that does: the one before changed E by more
+    assert st["iters"] >= 3
+    _, st1 = oracle.fista(P, V, 0.2, L, max_iter=st["iters"] - 2)
+    assert abs(st2["E"] - st1["E"]) > 1e-6 * st1["E"]
     assert st["E_paper"] == pytest.approx(st["resid2"] + 0.2 * st["l1"])
 
 
