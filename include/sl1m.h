@@ -18,7 +18,9 @@
  *   - Every call returns an SL1M_* status.  On failure nothing that the call
  *     was to produce is valid; sl1m_last_error() gives a one-line reason.
  *   - Thread safety: a context and its problems must be used from one host
- *     thread at a time.
+ *     thread at a time.  A running solve server (sl1m_server_start) works on
+ *     a host thread of its own; the caller's sl1m_server_* calls and
+ *     sl1m_last_error may run meanwhile.
  *   - Precision: SL1M_FP64 evaluates every step in FP64 ("plain" path);
  *     SL1M_MIXED evaluates sincos/exp and the complex multiply-accumulates in
  *     FP32 after an exact FP32 reduction of the phase to fractional turns;
@@ -57,13 +59,13 @@ extern "C" {
  * Eq. gaus has unit integral, so x_j is the pixel's total flux; and the
  * wide-field residual phase is w (n - 1 + (l^2+m^2)/2), the form whose
  * Taylor expansion is Eq. taylorexp.) */
-/* Solvers (sl1m_solve_opts.algorithm). */
-#define SL1M_FISTA 0          /* the algorithm box of Sect. 3                  */
-#define SL1M_MFISTA 1         /* its monotone variant, Beck & Teboulle (2009b) */
-
 #define SL1M_DIRAC 0
 #define SL1M_GAUSS_PARAXIAL 1
 #define SL1M_GAUSS_WIDE 2
+
+/* Solvers (sl1m_solve_opts.algorithm). */
+#define SL1M_FISTA 0          /* the algorithm box of Sect. 3                  */
+#define SL1M_MFISTA 1         /* its monotone variant, Beck & Teboulle (2009b) */
 
 typedef struct sl1m_ctx sl1m_ctx;
 typedef struct sl1m_problem sl1m_problem;
@@ -274,8 +276,9 @@ int sl1m_server_info(sl1m_ctx* ctx, sl1m_server_info_t* info);
 
 /* Autotuner of the operator kernels' tile shape: for the forward and the
  * adjoint of this problem it times, with CUDA events, every (streamed
- * granules per shared-memory stage: 2, 4 or 8; the adjoint 2 or 4) x (persistent grid: 1 .. occupancy CTAs per SM) of the mixed
- * no-gains kernels, then at the fastest of those the share npoly (1 or 2 of
+ * granules per shared-memory stage: 2, 4 or 8; the adjoint 2 or 4) x
+ * (persistent grid: 1 .. occupancy CTAs per SM) of the mixed no-gains
+ * kernels, then at the fastest of those the share npoly (1 or 2 of
  * every 8 pairs) whose sincos runs on the FMA pipe instead of the SFU; with
  * gains or in FP64 only the grid is tuned.  The choice is kept in the context,
  * keyed by (precision, operator, gains, Gaussian pixels, log2 of the work
