@@ -329,9 +329,10 @@ def cpu_threaded(O, x, r, rows, cols, fo, ao, pairs):
 
 
 def run_reference(args):
-    """--impl reference: the FP64 oracle on the host cores (bounded samples)."""
-    ws, rank, _ = dist_init()
-    if rank != 0:
+    """--impl reference: the FP64 oracle on the host cores (bounded samples).
+    Under torchrun only rank 0 runs it (no process group is needed); the
+    other ranks exit at once."""
+    if int(os.environ.get("RANK", "0")) != 0:
         return
     import oracle
     w = workload(args.config, 0, args.small, args)
