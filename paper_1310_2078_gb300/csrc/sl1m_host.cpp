@@ -1,6 +1,6 @@
 // sl1m_host.cpp -- host side of libsl1m: contexts, problem layout in HBM,
 // stream-K launch plans, the operator calls, the power iteration for L and
-// the FISTA driver (Hardy 2013, Sect. 2-3).  See include/sl1m.h for the ABI.
+// the FISTA loop (Hardy 2013, Sect. 2-3).  See include/sl1m.h for the ABI.
 #include "sl1m.h"
 
 #include <algorithm>
