@@ -94,11 +94,14 @@ def test_phase_centre_source_constant_on_gpu(ctx):
 
 @pytest.mark.parametrize("cfg", [2, 3])
 def test_full_size_config_sampled(ctx, cfg):
-    """Full-size configs in the launch configuration the benchmark uses,
-    checked on sampled outputs that the oracle computes one by one."""
+    """Full-size configs in the launch configuration the benchmark uses (the
+    autotuner's tile shapes, chosen first as bench.py does), checked on
+    sampled outputs that the oracle computes one by one."""
     w = synth.CONFIGS[cfg]()
     P, O = make_pair(ctx, dict(uvw=w.uvw, lm=w.lm, sigma=w.sigma, kind=w.kind,
                                ant_pair=w.ant_pair, gains=w.gains))
+    tuned = P.autotune(1)
+    assert all(k >= 1 for k in tuned["ctas_per_sm"])
     rng = np.random.default_rng(cfg)
     x = np.abs(rng.normal(size=w.n_pix))
     f = P.forward(x, 1)
