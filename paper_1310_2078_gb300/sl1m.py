@@ -180,6 +180,26 @@ def _ptr(a):
     return None if a is None else a.ctypes.data
 
 
+def _need(a, n, what):
+    """The library reads host and device arrays without a size argument, so
+    an array of the wrong length would be read past its end: refuse it here.
+    n == 0 (the problem's side not set yet) leaves the check to the library,
+    which reports the missing data."""
+    if a is None or not n:
+        return
+    size = a.numel() if hasattr(a, "numel") else a.size
+    if size != n:
+        raise ValueError(f"{what}: expected {n} values, got {size}")
+
+
+def _dev_f64(t, n, what):
+    """Device pointer of a contiguous float64 CUDA tensor of n values."""
+    if str(getattr(t, "dtype", "")) != "torch.float64":
+        raise ValueError(f"{what}: expected a float64 tensor")
+    _need(t, n, what)
+    return _tptr(t)
+
+
 def _tptr(t):
     """Device pointer of a contiguous torch CUDA tensor."""
     if not t.is_cuda or not t.is_contiguous():
@@ -278,6 +298,7 @@ class Context:
     def server_submit(self, problem, lam, L=0.0, max_iter=200, rel_tol=0.0, x0=None,
                       power_max_iter=0, power_tol=0.0, algorithm="fista"):
         x0a = _f64(x0)
+        _need(x0a, problem.n_pix, "x0")
         o = SolveOpts(float(lam), float(L), float(rel_tol), int(max_iter), MIXED,
                       int(power_max_iter), float(power_tol), _ptr(x0a), _ALGOS[algorithm])
         t = C.c_uint64()
@@ -333,17 +354,23 @@ class Problem:
         v = _cplx_interleaved(vis)
         w = _f64(weights)
         ap = None if ant_pair is None else np.ascontiguousarray(np.asarray(ant_pair, np.int32).reshape(-1, 2))
+        _need(v, 2 * n, "vis")
+        _need(w, n, "weights")
+        _need(ap, 2 * n, "ant_pair")
         self.ctx.check(self.lib.sl1m_set_visibilities(self.h, n, _ptr(uvw), _ptr(v), _ptr(w), _ptr(ap)))
         self.n_vis = n
 
     def set_vis_data(self, vis):
         v = _cplx_interleaved(vis)
+        _need(v, 2 * self.n_vis, "vis")
         self.ctx.check(self.lib.sl1m_set_vis_data(self.h, _ptr(v)))
 
     def set_pixels(self, lm, sigma=None, kind=None):
         lm = _f64(lm, (-1, 2))
         s = _f64(sigma)
         k = None if kind is None else np.ascontiguousarray(np.asarray(kind, np.int32))
+        _need(s, lm.shape[0], "sigma")
+        _need(k, lm.shape[0], "kind")
         self.ctx.check(self.lib.sl1m_set_pixels(self.h, lm.shape[0], _ptr(lm), _ptr(s), _ptr(k)))
         self.n_pix = lm.shape[0]
 
@@ -352,32 +379,39 @@ class Problem:
             self.ctx.check(self.lib.sl1m_set_gains(self.h, 0, None))
             return
         g = np.asarray(gains, dtype=np.complex128)
+        if g.ndim != 2 or (self.n_pix and g.shape[0] != self.n_pix):
+            raise ValueError(f"gains: expected an array [n_pix = {self.n_pix}, n_ant], got {g.shape}")
         gi = _cplx_interleaved(g)
         self.ctx.check(self.lib.sl1m_set_gains(self.h, g.shape[1], _ptr(gi)))
 
     def forward(self, x, precision=MIXED):
         x = _f64(x)
+        _need(x, self.n_pix, "x")
         out = np.zeros((self.n_vis, 2))
         self.ctx.check(self.lib.sl1m_forward(self.h, _ptr(x), _ptr(out), int(precision)))
         return out[:, 0] + 1j * out[:, 1]
 
     def adjoint(self, r, precision=MIXED):
         rr = _cplx_interleaved(np.asarray(r, dtype=np.complex128))
+        _need(rr, 2 * self.n_vis, "r")
         out = np.zeros(self.n_pix)
         self.ctx.check(self.lib.sl1m_adjoint(self.h, _ptr(rr), _ptr(out), int(precision)))
         return out
 
     def forward_dev(self, x_t, out_t, precision=MIXED):
         """x_t: float64 CUDA tensor [n_pix]; out_t: float64 CUDA tensor [n_vis, 2]."""
-        self.ctx.check(self.lib.sl1m_forward_dev(self.h, _tptr(x_t), _tptr(out_t), int(precision)))
+        self.ctx.check(self.lib.sl1m_forward_dev(self.h, _dev_f64(x_t, self.n_pix, "x"),
+                                                 _dev_f64(out_t, 2 * self.n_vis, "out"), int(precision)))
 
     def forward_noalloc(self, x_t, out_t, precision=MIXED):
         """sl1m_forward_noalloc: like forward_dev, scratch in a static device array."""
-        self.ctx.check(self.lib.sl1m_forward_noalloc(self.h, _tptr(x_t), _tptr(out_t), int(precision)))
+        self.ctx.check(self.lib.sl1m_forward_noalloc(self.h, _dev_f64(x_t, self.n_pix, "x"),
+                                                     _dev_f64(out_t, 2 * self.n_vis, "out"), int(precision)))
 
     def adjoint_dev(self, r_t, out_t, precision=MIXED):
         """r_t: float64 CUDA tensor [n_vis, 2]; out_t: float64 CUDA tensor [n_pix]."""
-        self.ctx.check(self.lib.sl1m_adjoint_dev(self.h, _tptr(r_t), _tptr(out_t), int(precision)))
+        self.ctx.check(self.lib.sl1m_adjoint_dev(self.h, _dev_f64(r_t, 2 * self.n_vis, "r"),
+                                                 _dev_f64(out_t, self.n_pix, "out"), int(precision)))
 
     def dirty_image(self, precision=MIXED):
         """sl1m_dirty_image: (Re A^H W V, lambda_max)."""
@@ -395,6 +429,7 @@ class Problem:
     def solve(self, lam, L=0.0, max_iter=200, rel_tol=0.0, precision=MIXED, x0=None,
               power_max_iter=0, power_tol=0.0, algorithm="fista"):
         x0a = _f64(x0)
+        _need(x0a, self.n_pix, "x0")
         o = SolveOpts(float(lam), float(L), float(rel_tol), int(max_iter), int(precision),
                       int(power_max_iter), float(power_tol), _ptr(x0a), _ALGOS[algorithm])
         img = np.zeros(self.n_pix)
