@@ -1,5 +1,7 @@
 """C ABI checks that need no GPU: the library builds, loads and exports every
-function include/sl1m.h declares; the binding declares the same set."""
+function include/sl1m.h declares; the binding declares the same set, raises
+without the library, and refuses arrays of the wrong length; the package and
+the oracle share no code."""
 import ctypes
 import os
 import re
