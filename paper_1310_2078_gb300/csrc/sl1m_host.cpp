@@ -1040,15 +1040,20 @@ int batch_ticks(sl1m_ctx* ctx, Batch& B, int n)
             cudaGraphExecDestroy(B.gexec);
             B.gexec = nullptr;
         }
-        cudaGraph_t g;
+        cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
         const long long l0 = ctx->n_launch;
         const int rc = enqueue_tick(ctx, B);
         const cudaError_t ec = cudaStreamEndCapture(ctx->stream, &g);
-        if (rc != SL1M_OK) return rc;
-        CK(ec);
-        CK(cudaGraphInstantiate(&B.gexec, g, 0));
+        if (rc != SL1M_OK || ec != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            if (rc != SL1M_OK) return rc;
+            CK(ec);
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&B.gexec, g, 0);
         cudaGraphDestroy(g);
+        if (ei != cudaSuccess) B.gexec = nullptr;
+        CK(ei);
         B.graph_ok = true;
         B.tick_launches = ctx->n_launch - l0;
         ctx->n_launch = l0;
