@@ -667,10 +667,11 @@ int sl1m_problem::rebuild(cudaStream_t st)
 double sl1m_problem::pairs() const { return (double)n_vis * (double)n_pix; }
 
 // Relative cost of the units (owned block x streamed granule) of one operator:
-// a Gaussian pixel granule costs 1.6 (three SFU ops per pair and the extra
-// FMAs, against two), a tile taking the exact phase path 3x, and gains 1.4x.
-// A block's 8 warps meet at each shared-memory stage, so a unit costs what
-// its slowest warp costs.  Uniform problems return a constant.
+// a Gaussian pixel granule costs 1.34 to 1.60 times a Dirac one (measured, see
+// below), a tile taking the exact phase path 3x, and gains 2x (gains problems
+// run in launches of their own, so that factor only orders work across the
+// two classes).  A block's 8 warps meet at each shared-memory stage, so a unit
+// costs what its slowest warp costs.  Uniform problems return a constant.
 const UnitCost& sl1m_problem::unit_cost(int precision, int op)
 {
     UnitCost& uc = ucost[precision][op];
