@@ -1036,6 +1036,12 @@ int batch_ticks(sl1m_ctx* ctx, Batch& B, int n)
         for (int i = 0; i < n; ++i) RET(enqueue_tick(ctx, B));
         return SL1M_OK;
     }
+    // The captured tick bakes in the context's partial-sum scratch, which a
+    // larger batch (another problem's solve or operator call, the autotuner)
+    // may have reallocated since: capture again rather than replay with a
+    // freed buffer.  The scratch only grows, so it still fits this batch.
+    if (B.graph_ok && (B.cap_partial[0] != ctx->partial_f.p || B.cap_partial[1] != ctx->partial_a.p))
+        B.graph_ok = false;
     if (!B.graph_ok) {
         if (B.gexec) {
             cudaGraphExecDestroy(B.gexec);
@@ -1056,6 +1062,8 @@ int batch_ticks(sl1m_ctx* ctx, Batch& B, int n)
         if (ei != cudaSuccess) B.gexec = nullptr;
         CK(ei);
         B.graph_ok = true;
+        B.cap_partial[0] = ctx->partial_f.p;
+        B.cap_partial[1] = ctx->partial_a.p;
         B.tick_launches = ctx->n_launch - l0;
         ctx->n_launch = l0;
     }

@@ -128,6 +128,7 @@ struct Batch {
     cudaGraphExec_t gexec = nullptr;
     bool graph_ok = false;
     long long tick_launches = 0;
+    const void* cap_partial[2] = {nullptr, nullptr};   // the context's scratch the capture baked in
     ~Batch();
 };
 

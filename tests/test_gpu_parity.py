@@ -154,6 +154,33 @@ def test_deterministic_repeat(ctx):
         assert np.array_equal(a, b)
 
 
+def test_solve_again_after_another_problem_grew_the_scratch(gpu_lib):
+    """A solve's captured step bakes in the context's partial-sum scratch. A
+    larger problem solved in between reallocates that scratch; solving the
+    first problem again captures anew and gives the same image, bit for bit,
+    still matching the oracle."""
+    c = gpu_lib.Context(0)                     # fresh: the scratch starts small
+    small = synth.random_problem(301, 400, 200, uv_max=150, w_max=40, extent=0.15)
+    big = synth.random_problem(302, 6000, 5000, uv_max=150, w_max=40, extent=0.15)
+    rng = np.random.default_rng(301)
+    x = np.zeros(200)
+    x[rng.choice(200, 4, replace=False)] = 1.0
+    P, O = make_pair(c, small)
+    V = oracle.forward(O, x)
+    P.set_vis_data(V)
+    L = oracle.power(O)[0]
+    lam = 0.05 * oracle.adjoint(O, V).max()
+    img1, st1 = P.solve(lam, L=L, max_iter=30)
+    Q, _ = make_pair(c, big)
+    Q.set_vis_data(np.ones(6000, complex))
+    Q.solve(1.0, L=1e9, max_iter=3)            # 456 CTAs' partial slots: the scratch grows
+    img2, st2 = P.solve(lam, L=L, max_iter=30)
+    assert np.array_equal(img1, img2) and st1["E"] == st2["E"]
+    img_o, _ = oracle.fista(O, V, lam, L, 30)
+    assert np.max(np.abs(img2 - img_o)) <= 1e-4 * img_o.max()
+    c.close()
+
+
 def test_power_iteration_matches_oracle(ctx):
     d = synth.random_problem(13, 900, 400, kinds=(DIRAC, PAR), weights=True, uv_max=300,
                              w_max=50)
