@@ -109,8 +109,8 @@ int sl1m_set_vis_data(sl1m_problem* prob, const double* vis);
 int sl1m_set_pixels(sl1m_problem* prob, int64_t n_pix, const double* lm,
                     const double* sigma, const int32_t* kind);
 
-/* Direction-dependent gains (Sect. 2: A(l,m; Z_j, chi_j), "arbitrary gains
- * between each pixel and each antenna element"): G [n_pix][n_ant][2],
+/* Direction-dependent gains (Sect. 2: A(l,m; Z_j, chi_j); the method allows
+ * a different gain for every pixel and every antenna): G [n_pix][n_ant][2],
  * per pixel and antenna; the entry for visibility k is multiplied by
  * g_jk = G[j][a_k] * conj(G[j][b_k]).  G == NULL or n_ant == 0 removes the
  * gains.  The mixed-precision kernels hold one pixel granule's gains for all
@@ -164,8 +164,8 @@ int sl1m_forward_noalloc(sl1m_problem* prob, const double* x_dev, double* vis_ou
 int sl1m_dirty_image(sl1m_problem* prob, int precision, double* img_out, double* lambda_max_out);
 
 /* Step constant of FISTA (Sect. 3, algorithm box: L = largest eigenvalue of
- * M*M; the paper uses "an algorithm to calculate the largest eigenvalue",
- * Sect. 3.1).  Power iteration on B = Re(A^H W A) from x = 1/sqrt(n_pix):
+ * M*M; Sect. 3.1 computes it with a routine whose method it does not give).
+ * Power iteration on B = Re(A^H W A) from x = 1/sqrt(n_pix):
  * z = B x, mu = ||z||, x = z/mu, stopping when |mu_i - mu_{i-1}| <= tol*mu_i
  * or after max_iter steps; L = the last mu.  Synchronous. */
 int sl1m_max_eig(sl1m_problem* prob, int max_iter, double tol, int precision,

@@ -1,7 +1,8 @@
 // sl1m_refine.cpp -- adaptive quadtree refinement of the pixel set
-// (Hardy 2013, Sect. 4.4: "solved at a low resolution, and pixels where
-// emission is detected are then subdivided"; in the paper's example every
-// pixel above 1% of the maximum is split, level by level, from 64" to 2").
+// (Hardy 2013, Sect. 4.4: solve on a coarse grid first, then split the
+// pixels that hold emission and solve again, repeatedly; in the paper's
+// example every pixel above 1% of the maximum is split, level by level, from
+// 64" to 2").
 //
 // Each level is an ordinary solve on the GPU (power iteration for L, FISTA);
 // between levels the host splits every pixel above refine_frac * peak into
