@@ -121,3 +121,24 @@ def test_reference_arm_under_torchrun_prints_one_line_from_rank_0():
     out = json.loads(lines[0])
     assert out["impl"] == "reference" and out["n_gpus"] == 2 and out["value"] > 0
     assert out["cpu_baseline"]["kind"] == "oracle" and out["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_cpu_baseline_leg_times_the_oracle_and_measures_the_error():
+    """The bench's CPU-baseline leg on a small workload: the single-threaded
+    and the threaded oracle runs agree bit for bit, and the error it reports
+    for given operator outputs is max |diff| / max |oracle| over its sample."""
+    import oracle
+    from paper_1310_2078_gb300 import synth
+    w = synth.config1(scale=0.5)
+    x, r = bench.baseline_inputs(w)
+    O = oracle.Problem(w.uvw, w.lm)
+    fwd, adj = oracle.forward(O, x), oracle.adjoint(O, r)
+    out = bench.cpu_baseline(w, fwd * (1 + 3e-7), adj, budget_s=0.2)
+    assert out["kind"] == "oracle" and out["cores"] == 1 and out["value"] > 0
+    assert out["unit"] == "pairs/s" and w.name in out["sample"]
+    th = out["threaded"]
+    assert th["bitwise_identical_to_single_thread"] is True
+    assert th["cores"] == (os.cpu_count() or 1) and th["value"] > 0
+    err = out["gpu_error_vs_oracle"]
+    assert err["forward"] == pytest.approx(3e-7, rel=1e-6)
+    assert err["adjoint"] == 0.0
