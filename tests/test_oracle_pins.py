@@ -431,6 +431,30 @@ def test_fista_kkt_at_convergence():
     assert np.min(g[~on]) > -lam * (1 + 1e-6)
 
 
+def test_lambda_sweep_has_the_shape_of_table1():
+    """Table 1 (Sect. 4.1, noise-free point sources) for its shape only (its
+    values need the ASKAP layout): at the minimiser, the flux sum never
+    exceeds the true one (the true image is feasible, so F(x*) <= F(x_true)),
+    falls as lambda grows while the residual grows (both monotone along the
+    L1 path), and tends to the true flux as lambda -> 0; convergence to a
+    1e-6 relative change of E takes fewer steps at large lambda."""
+    w = synth.config1(scale=0.25)              # 8x8 grid, 2,208 visibilities, 10 sources
+    P = oracle.Problem(w.uvw, w.lm)
+    V = oracle.forward(P, w.x_true)
+    L, _ = oracle.power(P)
+    lmax = oracle.adjoint(P, V).max()
+    true_l1 = w.x_true.sum()
+    runs = [oracle.fista(P, V, f * lmax, L, 6000, tol=1e-6)[1] for f in (1e-4, 1e-3, 1e-2, 1e-1, 3e-1)]
+    l1 = np.array([st["l1"] for st in runs])
+    r2 = np.array([st["resid2"] for st in runs])
+    its = np.array([st["iters"] for st in runs])
+    assert all(st["converged"] for st in runs)
+    assert np.all(l1 <= true_l1 * (1 + 1e-6))
+    assert np.all(np.diff(l1) < 0) and np.all(np.diff(r2) > 0)
+    assert l1[0] > 0.999 * true_l1
+    assert its[-1] < its[0]
+
+
 def test_noise_free_isolated_sources_are_recovered():
     """Noise-free, isolated point sources on pixel centres, small lam: the
     recovered fluxes sit within the L1 bias (~lam/||a_j||^2) of the truth."""
