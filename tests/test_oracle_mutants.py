@@ -73,6 +73,21 @@ MUTANTS = [
      "for (long j = 0; j < np; ++j) { l1 += Ik[j]; nnz += Ik[j] >= 0.0; }"),
     ("mfista_ignores_x0", "        memcpy(x, x0, sizeof(double) * np);\n        memcpy(y, x0, sizeof(double) * np);",
      "        memcpy(x, x0, sizeof(double) * np);"),
+    ("gauss_exponent_without_q", "double complex a = q * cexp(q * c) / n;", "double complex a = q * cexp(c) / n;"),
+    ("n_sign_inside_root", "double n = sqrt(1.0 - r2);", "double n = sqrt(1.0 + r2);"),
+    ("gain_index_transposed", "const double *ga = P->gains + 2 * ((size_t)j * P->n_ant + aa);",
+     "const double *ga = P->gains + 2 * ((size_t)aa * P->n_pix + j);"),
+    ("fista_t_update_constant", "double t_next = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));\n        double beta",
+     "double t_next = 0.5 * (1.0 + sqrt(1.0 + 2.0 * t * t));\n        double beta"),
+    ("power_absolute_tolerance", "if (it > 1 && fabs(mu - mu_prev) <= tol * mu) break;",
+     "if (it > 1 && fabs(mu - mu_prev) <= tol) break;"),
+    ("power_returns_previous_mu", "    *L_out = mu;\n", "    *L_out = mu_prev > 0.0 ? mu_prev : mu;\n"),
+    ("fista_stop_before_the_step_is_kept", "            if (fabs(E - E_prev) <= tol * E_prev) { converged = 1; break; }",
+     "            if (fabs(E - E_prev) <= tol) { converged = 1; break; }"),
+    ("mfista_momentum_uses_t_next_minus_one", "y[j] = xk + (t / t_next) * (z[j] - xk) + ((t - 1.0) / t_next) * (xk - x[j]);",
+     "y[j] = xk + ((t - 1.0) / t_next) * (z[j] - xk) + ((t - 1.0) / t_next) * (xk - x[j]);"),
+    ("stats_E_paper_halved", "            stats->E_paper = r2 + lambda * l1;\n            stats->t_final = t;\n        }\n    }\n    free(Ik);",
+     "            stats->E_paper = 0.5 * r2 + lambda * l1;\n            stats->t_final = t;\n        }\n    }\n    free(Ik);"),
     ("mfista_drops_z_term", "y[j] = xk + (t / t_next) * (z[j] - xk) + ((t - 1.0) / t_next) * (xk - x[j]);",
      "y[j] = xk + ((t - 1.0) / t_next) * (xk - x[j]);"),
     ("mfista_always_takes_z", "const int take = Fz <= Fx;", "const int take = 1;"),

@@ -287,6 +287,28 @@ def test_power_iteration_from_the_unit_start_vector():
     assert it == 2 and abs(L - want) <= 1e-12 * want
 
 
+def test_power_iteration_rises_each_step_and_is_scale_free():
+    """For the symmetric positive semidefinite B = Re(A^H W A), each power
+    step raises ||B x|| / ||x|| strictly until x is an eigenvector, and never
+    above lambda_max.  The stopping rule is relative (reading R8): weights
+    scaled by 1024 scale B, and every mu, exactly in binary floating point,
+    so the iteration stops at the same step with L scaled by 1024; and L is
+    the last step's estimate, the one a run of that many steps returns."""
+    P, d = _problem(45, 70, 30, kinds=(DIRAC, PAR), weights=True, uv_max=120, w_max=30, sigma_max=0.02)
+    A = _dense(P)
+    W = d["weights"]
+    lam = np.linalg.eigvalsh((A.conj().T @ (W[:, None] * A)).real)[-1]
+    Lk = [oracle.power(P, max_iter=k, tol=0.0)[0] for k in range(1, 7)]
+    assert np.all(np.diff(Lk) > 1e-9 * lam) and Lk[-1] <= lam * (1 + 1e-12)
+    P2 = oracle.Problem(d["uvw"], d["lm"], d["sigma"], d["kind"], 1024.0 * W)
+    for tol in (1e-3, 1e-6):
+        L1, it1 = oracle.power(P, max_iter=500, tol=tol)
+        L2, it2 = oracle.power(P2, max_iter=500, tol=tol)
+        assert it1 == it2 < 500 and L2 == 1024.0 * L1
+        # L is the estimate of the last step taken: the rule only decides when to stop
+        assert oracle.power(P, max_iter=it1, tol=0.0)[0] == L1
+
+
 @pytest.mark.parametrize("kw", [dict(), dict(kinds=(DIRAC, PAR), weights=True, gains=True)])
 def test_power_iteration_matches_dense_eigensolver(kw):
     P, d = _problem(43, 80, 40, **kw)
@@ -489,6 +511,10 @@ def test_stopping_rule_relative_change_of_E():
     assert st["iters"] >= 3
     _, st1 = oracle.fista(P, V, 0.2, L, max_iter=st["iters"] - 2)
     assert abs(st2["E"] - st1["E"]) > 1e-6 * st1["E"]
+    # the rule is relative: V and lambda scaled by 1024 scale every iterate
+    # and E (by 2^20) exactly, so the solve stops at the same step
+    img3, st3 = oracle.fista(P, 1024.0 * V, 0.2 * 1024.0, L, max_iter=5000, tol=1e-6)
+    assert st3["iters"] == st["iters"] and np.array_equal(img3, 1024.0 * img)
     assert st["E_paper"] == pytest.approx(st["resid2"] + 0.2 * st["l1"])
 
 
