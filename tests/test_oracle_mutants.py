@@ -88,6 +88,10 @@ MUTANTS = [
      "y[j] = xk + ((t - 1.0) / t_next) * (z[j] - xk) + ((t - 1.0) / t_next) * (xk - x[j]);"),
     ("stats_E_paper_halved", "            stats->E_paper = r2 + lambda * l1;\n            stats->t_final = t;\n        }\n    }\n    free(Ik);",
      "            stats->E_paper = 0.5 * r2 + lambda * l1;\n            stats->t_final = t;\n        }\n    }\n    free(Ik);"),
+    ("mfista_absolute_stop", "if (tol > 0.0 && fabs(Fz - Fx_prev) <= tol * Fx_prev) { converged = 1; break; }",
+     "if (tol > 0.0 && fabs(Fz - Fx_prev) <= tol) { converged = 1; break; }"),
+    ("entry_accepts_pixels_off_the_sky", "    if (!(l * l + m * m < 1.0) || !out) return ORC_ERR_ARG;",
+     "    if (!out) return ORC_ERR_ARG;"),
     ("mfista_drops_z_term", "y[j] = xk + (t / t_next) * (z[j] - xk) + ((t - 1.0) / t_next) * (xk - x[j]);",
      "y[j] = xk + ((t - 1.0) / t_next) * (xk - x[j]);"),
     ("mfista_always_takes_z", "const int take = Fz <= Fx;", "const int take = 1;"),

@@ -62,6 +62,9 @@ def test_dirac_hand_worked_values():
     for l, m, u, v, w, re, im in rows:
         a = oracle.entry(DIRAC, l, m, 0.0, u, v, w)
         assert abs(a - complex(re, im)) < 1e-13, (l, m, u, v, w, a)
+    # the fixture's case 5: l^2 + m^2 = 1 is off the sky (n would be 0), refused
+    with pytest.raises(ValueError):
+        oracle.entry(DIRAC, -0.28, 0.96, 0.0, 1.0, 1.0, 1.0)
 
 
 def test_phase_centre_source_gives_constant_visibilities():
@@ -636,3 +639,6 @@ def test_mfista_stopping_rule():
     img, st = oracle.mfista(P, V, lam, L, 3000, tol=1e-6)
     assert st["converged"] == 1 and st["iters"] == hit[0] + 1
     assert np.array_equal(img, tr["x"][hit[0]])
+    # the rule is relative: V and lambda times 1024 scale every iterate and F exactly
+    img2, st2 = oracle.mfista(P, 1024.0 * V, 1024.0 * lam, L, 3000, tol=1e-6)
+    assert st2["iters"] == st["iters"] and np.array_equal(img2, 1024.0 * img)
