@@ -115,6 +115,13 @@ def workload(cfg: int, rank: int = 0, small: bool = False, args=None):
     return w
 
 
+def smi_id(index: int) -> str:
+    """nvidia-smi's name for CUDA device `index`: CUDA numbers only the devices
+    CUDA_VISIBLE_DEVICES lists (by index or UUID), nvidia-smi numbers them all."""
+    vis = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    return vis[index] if index < len(vis) else str(index)
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -129,7 +136,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                ["nvidia-smi", f"--id={smi_id(self.index)}", f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)

@@ -142,3 +142,12 @@ def test_cpu_baseline_leg_times_the_oracle_and_measures_the_error():
     err = out["gpu_error_vs_oracle"]
     assert err["forward"] == pytest.approx(3e-7, rel=1e-6)
     assert err["adjoint"] == 0.0
+
+
+def test_clock_sampler_names_the_gpu_as_nvidia_smi_does(monkeypatch):
+    monkeypatch.delenv("CUDA_VISIBLE_DEVICES", raising=False)
+    assert bench.smi_id(0) == "0"
+    monkeypatch.setenv("CUDA_VISIBLE_DEVICES", "3,5")
+    assert bench.smi_id(0) == "3" and bench.smi_id(1) == "5"
+    monkeypatch.setenv("CUDA_VISIBLE_DEVICES", "GPU-1234abcd")
+    assert bench.smi_id(0) == "GPU-1234abcd"
