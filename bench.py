@@ -303,6 +303,20 @@ def cpu_baseline(w, gpu_fwd=None, gpu_adj=None, budget_s: float = 12.0):
     return out
 
 
+def oracle_stream_estimate(reqs, picks, stream_pairs, budget_s: float = 6.0):
+    """The FP64 oracle, single-threaded, timed on bounded samples of the
+    requests `picks` of a serving stream; the mean of their pair rates,
+    applied to the pairs the whole stream evaluated, estimates a serial
+    oracle run of every request (solves/s)."""
+    samples = [dict(request=int(i), **cpu_baseline(reqs[i], budget_s=budget_s)) for i in picks]
+    rate = float(np.mean([smp["value"] for smp in samples]))
+    wall = stream_pairs / rate
+    return {"value": len(reqs) / wall, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle forward rows + adjoint columns of requests {[int(i) for i in picks]}, "
+                      "single thread; their mean pair rate applied to all requests' pairs (serial)",
+            "pairs_per_s": rate, "est_wall_s": wall, "samples": samples}
+
+
 def cpu_threaded(O, x, r, rows, cols, fo, ao, pairs):
     """The same oracle sample with the outer loop (forward rows, adjoint
     columns) split over every host core: each output is still one
@@ -452,6 +466,10 @@ def run_serve(args):
                     "method": "FP64 single solves, pair rate measured on the sample, "
                               "applied to all requests' pairs (serial, no overlap)"}
                    if fp64_rate else None)
+    # the FP64 oracle on the host cores: the smallest and the median request sampled
+    cpu = None
+    if not args.no_cpu:
+        cpu = oracle_stream_estimate(reqs, [by_work[0], by_work[len(by_work) // 2]], pairs)
     out = {"metric": "solves/s (continuous batching, mixed precision)", "value": args.requests / T,
            "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32+f64",
            "data": "synthetic",
@@ -466,7 +484,8 @@ def run_serve(args):
            "iters_mean": float(np.mean([st["iters"] for _, st in results])),
            "server": info, "clocks": clk, "gpu_launches": ctx.counters()["launches"],
            "fp64_plain_single_solve": {"sample": cmp, "solves_per_s_on_sample": fp64_solves_per_s,
-                                       "serial_whole_stream": fp64_serial}}
+                                       "serial_whole_stream": fp64_serial},
+           "cpu_baseline": cpu}
     print(json.dumps(out))
     ctx.close()
 

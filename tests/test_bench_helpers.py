@@ -151,3 +151,17 @@ def test_clock_sampler_names_the_gpu_as_nvidia_smi_does(monkeypatch):
     assert bench.smi_id(0) == "3" and bench.smi_id(1) == "5"
     monkeypatch.setenv("CUDA_VISIBLE_DEVICES", "GPU-1234abcd")
     assert bench.smi_id(0) == "GPU-1234abcd"
+
+
+def test_oracle_stream_estimate_scales_the_sampled_rate_to_the_stream():
+    from paper_1310_2078_gb300 import synth
+    reqs = [synth.config1(scale=0.25), synth.config1(scale=0.5), synth.config1(scale=0.25)]
+    stream_pairs = 1e9
+    est = bench.oracle_stream_estimate(reqs, [0, 1], stream_pairs, budget_s=0.1)
+    assert est["kind"] == "oracle" and est["cores"] == 1 and est["unit"] == "solves/s"
+    assert [s["request"] for s in est["samples"]] == [0, 1]
+    assert all(s["threaded"]["bitwise_identical_to_single_thread"] for s in est["samples"])
+    rate = np.mean([s["value"] for s in est["samples"]])
+    assert est["pairs_per_s"] == pytest.approx(rate)
+    assert est["est_wall_s"] == pytest.approx(stream_pairs / rate)
+    assert est["value"] == pytest.approx(3 / (stream_pairs / rate))
