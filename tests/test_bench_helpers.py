@@ -165,3 +165,17 @@ def test_oracle_stream_estimate_scales_the_sampled_rate_to_the_stream():
     assert est["pairs_per_s"] == pytest.approx(rate)
     assert est["est_wall_s"] == pytest.approx(stream_pairs / rate)
     assert est["value"] == pytest.approx(3 / (stream_pairs / rate))
+
+
+def test_default_workload_matches_the_profiles_and_ranks_share_its_shape():
+    """The bench's default workload is the one the committed ncu traffic lines
+    name; under several ranks each rank solves the same geometry with its own
+    noise (weak scaling)."""
+    w = bench.workload(2)
+    assert w.name == "wide-field-dirac-256x256-40320vis" and (w.n_pix, w.n_vis) == (65536, 40320)
+    prof = open(os.path.join(ROOT, "profiles", "launch_list_wide_field_dirac_256x256_40320vis.md")).read()
+    assert f"workload={w.name}" in prof
+    w1 = bench.workload(2, rank=1)
+    assert (w1.n_pix, w1.n_vis) == (w.n_pix, w.n_vis)
+    np.testing.assert_array_equal(w1.uvw, w.uvw)
+    assert not np.array_equal(w1.noise, w.noise)
