@@ -5,7 +5,8 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``libsl1m`` and its binding ``paper_1310_2078_gb300``) never imports, links or
 calls it, and this package imports nothing from the product.
 
-The arithmetic lives in ``sl1m_oracle.c`` (plain C99, FP64, single-threaded);
+The arithmetic lives in ``sl1m_oracle.c`` (plain C99, FP64, single-threaded
+unless a Problem asks for threads over its outer loops);
 this module only compiles it with gcc and marshals numpy arrays through
 ctypes.  Every function cites the passage of Hardy (2013) it follows:
 
@@ -39,7 +40,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(
-            ["gcc", "-std=c99", "-O2", "-fno-fast-math", "-ffp-contract=off",
+            ["gcc", "-std=c99", "-O2", "-fno-fast-math", "-ffp-contract=off", "-pthread",
              "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -51,7 +52,7 @@ class _Problem(C.Structure):
         ("ant_pair", C.c_void_p),
         ("n_pix", C.c_long), ("lm", C.c_void_p), ("sigma", C.c_void_p),
         ("kind", C.c_void_p),
-        ("n_ant", C.c_int), ("gains", C.c_void_p),
+        ("n_ant", C.c_int), ("gains", C.c_void_p), ("n_threads", C.c_int),
     ]
 
 
@@ -123,11 +124,14 @@ class Problem:
     ant_pair[n_vis, 2] int or None;  lm [n_pix, 2] direction cosines;
     sigma   [n_pix] or None;         kind [n_pix] int (0 Dirac, 1 paraxial
     Gaussian, 2 wide-field Gaussian) or None;  gains [n_pix, n_ant] complex or
-    None (unit gains).
+    None (unit gains).  threads: threads for the outer loops of the forward
+    (rows) and adjoint (columns), also inside power / fista / mfista; every
+    output is still one sum in the single-threaded order, so results are
+    bitwise the same for any count (1 = single-threaded, the default).
     """
 
     def __init__(self, uvw, lm, sigma=None, kind=None, weights=None,
-                 ant_pair=None, gains=None):
+                 ant_pair=None, gains=None, threads=1):
         self.uvw = _f64(uvw, (-1, 3))
         self.lm = _f64(lm, (-1, 2))
         self.sigma = _f64(sigma)
@@ -147,7 +151,7 @@ class Problem:
         self._c = _Problem(self.n_vis, _ptr(self.uvw), _ptr(self.weights),
                            _ptr(self.ant_pair), self.n_pix, _ptr(self.lm),
                            _ptr(self.sigma), _ptr(self.kind), self.n_ant,
-                           _ptr(self.gains))
+                           _ptr(self.gains), int(threads))
 
     @property
     def c(self):

@@ -44,9 +44,16 @@
  * sums visibilities in index order k = 0..n_vis-1, with plain FP64 "+=".
  * A pixel with x_j == 0 contributes an exact zero and is skipped; that leaves
  * every partial sum unchanged.
+ *
+ * Threads: single-threaded unless the problem's n_threads is above 1.  Then
+ * the outer loop of a forward (its rows) or an adjoint (its columns) is cut
+ * into contiguous ranges, one per thread; every output element is still one
+ * sum, in the order above, by one thread, so the results are bit for bit
+ * those of the single-threaded run.  Nothing else is threaded.
  */
 #include <complex.h>
 #include <math.h>
+#include <pthread.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -71,6 +78,7 @@ typedef struct {
     const int *kind;        /* [n_pix] or NULL (= Dirac)                      */
     int n_ant;
     const double *gains;    /* [n_pix][n_ant][2] or NULL (= unit gains)      */
+    int n_threads;          /* threads for the outer loops; <= 1: one        */
 } orc_problem;
 
 typedef struct {
@@ -170,6 +178,79 @@ int orc_entry_kj(const orc_problem *P, long k, long j, double *out)
     return ORC_OK;
 }
 
+/* One row of the forward product, Eq. sme: sum_j A_kj x_j in pixel order. */
+static void forward_row(const orc_problem *P, const double *x, long k, double *out)
+{
+    double complex acc = 0.0;
+    for (long j = 0; j < P->n_pix; ++j) {
+        if (x[j] == 0.0) continue;
+        acc += entry_kj(P, k, j) * x[j];
+    }
+    out[0] = creal(acc);
+    out[1] = cimag(acc);
+}
+
+/* One column of the adjoint: sum_k Re(conj(A_kj) r_k) in visibility order. */
+static void adjoint_col(const orc_problem *P, const double *r, long j, double *out)
+{
+    double acc = 0.0;
+    for (long k = 0; k < P->n_vis; ++k) {
+        double complex rk = r[2 * k] + _Complex_I * r[2 * k + 1];
+        acc += creal(conj(entry_kj(P, k, j)) * rk);
+    }
+    *out = acc;
+}
+
+/* A contiguous range [t0, t1) of the outputs of a forward (rows) or an
+ * adjoint (columns); idx == NULL: output t is row / column t. */
+typedef struct {
+    const orc_problem *P;
+    const double *in;
+    const long *idx;
+    long t0, t1;
+    double *out;
+    int adjoint;
+} orc_range;
+
+static void *run_range(void *arg)
+{
+    const orc_range *R = (const orc_range *)arg;
+    for (long t = R->t0; t < R->t1; ++t) {
+        long e = R->idx ? R->idx[t] : t;
+        if (R->adjoint) adjoint_col(R->P, R->in, e, R->out + t);
+        else forward_row(R->P, R->in, e, R->out + 2 * t);
+    }
+    return NULL;
+}
+
+/* All n outputs: in one thread, or cut into P->n_threads contiguous ranges. */
+static int run_outputs(const orc_problem *P, const double *in, long n, const long *idx,
+                       double *out, int adjoint)
+{
+    long nt = P->n_threads > 1 ? P->n_threads : 1;
+    if (nt > n) nt = n;
+    if (nt <= 1) {
+        orc_range R = {P, in, idx, 0, n, out, adjoint};
+        run_range(&R);
+        return ORC_OK;
+    }
+    orc_range *R = malloc(sizeof(orc_range) * nt);
+    pthread_t *th = malloc(sizeof(pthread_t) * nt);
+    if (!R || !th) { free(R); free(th); return ORC_ERR_OOM; }
+    for (long q = 0; q < nt; ++q) {
+        orc_range r = {P, in, idx, n * q / nt, n * (q + 1) / nt, out, adjoint};
+        R[q] = r;
+    }
+    long started = 1;
+    while (started < nt && pthread_create(&th[started], NULL, run_range, &R[started]) == 0) ++started;
+    run_range(&R[0]);
+    for (long q = 1; q < started; ++q) pthread_join(th[q], NULL);
+    for (long q = started; q < nt; ++q) run_range(&R[q]);   /* threads that could not start */
+    free(R);
+    free(th);
+    return ORC_OK;
+}
+
 /* Forward product, Eq. sme: out_k = sum_j A_kj x_j, for the visibilities
  * listed in rows[0..n_rows) (rows == NULL: all, in order).  out is
  * [n_rows][2]. */
@@ -178,18 +259,9 @@ int orc_forward_rows(const orc_problem *P, const double *x, long n_rows,
 {
     if (check_problem(P) || (!x && P->n_pix) || !out) return ORC_ERR_ARG;
     long nr = rows ? n_rows : P->n_vis;
-    for (long t = 0; t < nr; ++t) {
-        long k = rows ? rows[t] : t;
-        if (k < 0 || k >= P->n_vis) return ORC_ERR_ARG;
-        double complex acc = 0.0;
-        for (long j = 0; j < P->n_pix; ++j) {
-            if (x[j] == 0.0) continue;
-            acc += entry_kj(P, k, j) * x[j];
-        }
-        out[2 * t] = creal(acc);
-        out[2 * t + 1] = cimag(acc);
-    }
-    return ORC_OK;
+    for (long t = 0; rows && t < nr; ++t)
+        if (rows[t] < 0 || rows[t] >= P->n_vis) return ORC_ERR_ARG;
+    return run_outputs(P, x, nr, rows, out, 0);
 }
 
 int orc_forward(const orc_problem *P, const double *x, double *out)
@@ -204,17 +276,9 @@ int orc_adjoint_cols(const orc_problem *P, const double *r, long n_cols,
 {
     if (check_problem(P) || (!r && P->n_vis) || !out) return ORC_ERR_ARG;
     long nc = cols ? n_cols : P->n_pix;
-    for (long t = 0; t < nc; ++t) {
-        long j = cols ? cols[t] : t;
-        if (j < 0 || j >= P->n_pix) return ORC_ERR_ARG;
-        double acc = 0.0;
-        for (long k = 0; k < P->n_vis; ++k) {
-            double complex rk = r[2 * k] + _Complex_I * r[2 * k + 1];
-            acc += creal(conj(entry_kj(P, k, j)) * rk);
-        }
-        out[t] = acc;
-    }
-    return ORC_OK;
+    for (long t = 0; cols && t < nc; ++t)
+        if (cols[t] < 0 || cols[t] >= P->n_pix) return ORC_ERR_ARG;
+    return run_outputs(P, r, nc, cols, out, 1);
 }
 
 int orc_adjoint(const orc_problem *P, const double *r, double *out)

@@ -112,7 +112,7 @@ def _copy_oracle(dst, mutant=None):
         f.write(src)
     # build here, so that a mutant that does not compile fails this test and
     # not the pin run
-    subprocess.check_call(["gcc", "-std=c99", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fPIC",
+    subprocess.check_call(["gcc", "-std=c99", "-O2", "-fno-fast-math", "-ffp-contract=off", "-pthread", "-fPIC",
                            "-shared", "-o", os.path.join(pkg, "libsl1m_oracle.so"),
                            os.path.join(pkg, "sl1m_oracle.c"), "-lm"])
     return dst
