@@ -153,7 +153,13 @@ int sl1m_adjoint_dev(sl1m_problem* prob, const double* r_dev, double* img_out_de
  *     whose work overlaps on the GPU (other streams, other contexts, other
  *     host threads) race and must be serialised by the caller.
  *   - x_dev [n_pix] and vis_out_dev [n_vis][2] are device pointers in the
- *     caller's order; asynchronous on the context's stream. */
+ *     caller's order; asynchronous on the context's stream: the call enqueues
+ *     its kernels (its per-call tables travel in kernel parameters, not in
+ *     copies from host memory) and returns without waiting for the stream.
+ *   - With gains in mixed precision, a kernel whose bounded wait for a bulk
+ *     copy gives up sets the context's device fault flag; this call does not
+ *     read it (that would wait for the stream).  The next synchronous call on
+ *     the context reads it and returns SL1M_ERR_CUDA. */
 int sl1m_forward_noalloc(sl1m_problem* prob, const double* x_dev, double* vis_out_dev, int precision);
 
 /* Dirty image: the back-projection of the measured data, Re(A^H W V)
@@ -369,6 +375,38 @@ int sl1m_granule_order(int64_t n, const double* xy, int32_t* order, int64_t* n_p
 
 /* Device bytes the problem holds (inputs, layout and solver workspace). */
 int sl1m_problem_bytes(const sl1m_problem* prob, int64_t* bytes);
+
+/* Measured issue rate of the special-function unit (MUFU), which bounds the
+ * mixed-precision operator kernels: per pixel-visibility pair they take sin
+ * and cos of the phase of Eq. deltam, and exp2 of the Gaussian amplitude of
+ * Eq. samlm5.  A kernel of 8 independent dependency chains per thread, over
+ * 4 CTAs of 256 threads per SM, times sin.approx/cos.approx (alternating)
+ * and ex2.approx with CUDA events on the context's stream (best of 3 after a
+ * warm-up).  sincos_per_s_out: sin or cos results per second over the whole
+ * device; ex2_per_s_out: exp2 results per second.  Synchronous. */
+int sl1m_measure_sfu(sl1m_ctx* ctx, double* sincos_per_s_out, double* ex2_per_s_out);
+
+/* Self-test of the kernels' bounded waits.  The mixed kernels wait on
+ * mbarriers for their bulk copies into shared memory; each wait gives up
+ * after a fixed time on the GPU's global timer (limit_ns_out), records a
+ * device flag and lets its kernel run to its end, so no CTA barrier is left
+ * waiting and the context stays usable; the next synchronous call reads the
+ * flag and fails with SL1M_ERR_CUDA.  This call runs a kernel whose threads
+ * wait on an mbarrier nobody arrives on (no copy is in flight), so the wait
+ * must give up: it returns SL1M_ERR_CUDA, and waited_ns_out (may be NULL)
+ * receives how long the wait lasted.  Any other status means the bounded wait
+ * is broken.  Synchronous. */
+int sl1m_selftest_bounded_wait(sl1m_ctx* ctx, int64_t* waited_ns_out, int64_t* limit_ns_out);
+
+/* Share of the operator's tiles (visibility granule of 64 x pixel granule of
+ * 64) that the mixed-precision kernels evaluate on the exact phase path: the
+ * phase u l + v m + w (n-1) of Eq. deltam is split into granule-centre and
+ * offset terms, and a tile whose granule extents could make the product of
+ * the two offsets exceed 6 turns reduces that term exactly too (wide fields,
+ * long baselines).  share_out in [0, 1]; n_tiles_out (may be NULL) the number
+ * of tiles.  The problem must have been laid out by an operator or solve call
+ * (SL1M_ERR_STATE otherwise).  Host-only, synchronous. */
+int sl1m_exact_tile_share(const sl1m_problem* prob, double* share_out, int64_t* n_tiles_out);
 
 #ifdef __cplusplus
 }

@@ -116,25 +116,51 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
     mbar_arrive_expect(bar, bytes);
     bulk_copy(dst, src, bytes, bar);
 }
-// Wait until the phase of bar with this parity has completed.  Bounded: after
-// 2^20 unsuccessful tries (each may suspend the thread for a while) it gives
-// up and returns false; the caller records the fault and carries on, so no
-// barrier of the CTA is left waiting.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity)
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ unsigned long long global_ns()
 {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// How long a wait for a bulk copy may take before it gives up: a copy of a
+// stage (a few to 40 KB) lands in microseconds, so 20 ms is far beyond any
+// wait that will still end.
+constexpr unsigned long long WAIT_LIMIT_NS = 20ull * 1000 * 1000;
+
+__device__ __forceinline__ bool mbar_try(unsigned a, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait until the phase of bar with this parity has completed, bounded by
+// elapsed time: after WAIT_LIMIT_NS on the global timer it gives up and sets
+// `fault`.  A thread whose `fault` is already set does not wait at all, so a
+// kernel whose copies stopped completing gives up once per thread, records
+// the fault (the caller) and runs to its end; no barrier of the CTA is left
+// waiting.
+__device__ __forceinline__ void mbar_wait(unsigned long long* bar, unsigned parity, bool& fault)
+{
+    if (fault) return;
     const unsigned a = smem_u32(bar);
-    for (int i = 0; i < (1 << 20); ++i) {
-        unsigned ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (ok) return true;
+    for (int i = 0; i < 8; ++i)                 // the usual case: done at once or soon
+        if (mbar_try(a, parity)) return;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try(a, parity)) {
+        if (global_ns() - t0 > WAIT_LIMIT_NS) {
+            fault = true;
+            return;
+        }
     }
-    return false;
 }
 // Dynamic shared memory of this launch, in bytes.
 __device__ __forceinline__ unsigned dyn_smem_bytes()

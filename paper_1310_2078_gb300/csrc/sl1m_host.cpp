@@ -395,6 +395,17 @@ cudaEvent_t sl1m_ctx::get_event()
 
 void sl1m_ctx::drain_profile()
 {
+    if (evals_dev.p) {                 // solver ticks: the pairs counted on the device
+        double ev[4] = {0, 0, 0, 0};
+        if (cudaMemcpyAsync(ev, evals_dev.p, sizeof ev, cudaMemcpyDeviceToHost, stream) == cudaSuccess &&
+            cudaStreamSynchronize(stream) == cudaSuccess) {
+            prof_pairs[0] += ev[0];    // forward FP64, adjoint FP64, forward mixed, adjoint mixed
+            prof_pairs[1] += ev[1];
+            prof_pairs[2] += ev[2];
+            prof_pairs[3] += ev[3];
+            cudaMemsetAsync(evals_dev.p, 0, sizeof ev, stream);
+        }
+    }
     for (auto& r : pending) {
         cudaEventSynchronize(r.ev1);
         float ms = 0.f;
@@ -970,7 +981,7 @@ static int launch_op_class(sl1m_ctx* ctx, Batch& B, int op, int c)
         prof_begin(ctx, B.precision == 0 ? 0 : 2, tk);
         CKL(launch_forward(B.precision, c == 1, B.n_ant_max, B.desc.p, P.dpl.p, P.pl.C, ctx->partial_f.p, st,
                            B.nst[0][c]));
-        prof_end(ctx, tk, B.pairs_class[c], 0.0);
+        prof_end(ctx, tk, B.solver ? 0.0 : B.pairs_class[c], 0.0);   // solver ticks: counted on the device
         prof_begin(ctx, 4, tk);
         CKL(launch_fwd_finish(B.desc.p, P.dpl.p, std::min(B.fin_grid, std::max(1, P.pl.n_blocks)),
                               ctx->partial_f.p, st));
@@ -984,7 +995,7 @@ static int launch_op_class(sl1m_ctx* ctx, Batch& B, int op, int c)
         prof_begin(ctx, B.precision == 0 ? 1 : 3, tk);
         CKL(launch_adjoint(B.precision, c == 1, B.n_ant_max, B.desc.p, P.dpl.p, P.pl.C, ctx->partial_a.p, st,
                            B.nst[1][c]));
-        prof_end(ctx, tk, B.pairs_class[c], 0.0);
+        prof_end(ctx, tk, B.solver ? 0.0 : B.pairs_class[c], 0.0);
         prof_begin(ctx, 5, tk);
         CKL(launch_adj_finish(B.desc.p, P.dpl.p, std::min(B.fin_grid, std::max(1, P.pl.n_blocks)),
                               ctx->partial_a.p, st));
@@ -1006,7 +1017,10 @@ static int enqueue_tick(sl1m_ctx* ctx, Batch& B)
 {
     for (int c = 0; c < 2; ++c) RET(launch_op_class(ctx, B, 1, c));
     for (int c = 0; c < 2; ++c) RET(launch_op_class(ctx, B, 0, c));
-    CKL(launch_scalars(B.desc.p, B.n_probs_dev.p, B.sc_grid, ctx->stream));
+    // while profiling (ticks are launched directly then, never captured) the
+    // scalars kernel counts the pairs the tick evaluated
+    double* ev = (ctx->prof && B.solver && ctx->evals_dev.p) ? ctx->evals_dev.p + 2 * (B.precision != 0) : nullptr;
+    CKL(launch_scalars(B.desc.p, B.n_probs_dev.p, B.sc_grid, ev, ctx->stream));
     if (B.has_mfista) {
         ProfTok tk;
         prof_begin(ctx, 6, tk);
@@ -1670,6 +1684,11 @@ int sl1m_set_tile_shape(sl1m_problem* prob, int precision, int op, int nst, int 
 int sl1m_profile_enable(sl1m_ctx* ctx, int on)
 {
     if (!ctx) return SL1M_ERR_ARG;
+    if (on && !ctx->evals_dev.p) {
+        CK(cudaSetDevice(ctx->device));
+        CK(ctx->evals_dev.alloc(4));
+        CK(cudaMemsetAsync(ctx->evals_dev.p, 0, 4 * sizeof(double), ctx->stream));
+    }
     ctx->prof = on != 0;
     return SL1M_OK;
 }
@@ -1773,6 +1792,42 @@ int sl1m_problem_bytes(const sl1m_problem* prob, int64_t* bytes)
 {
     if (!prob || !bytes) return SL1M_ERR_ARG;
     *bytes = prob->dev ? (int64_t)prob->dev_bytes() : 0;
+    return SL1M_OK;
+}
+
+int sl1m_selftest_bounded_wait(sl1m_ctx* ctx, int64_t* waited_ns, int64_t* limit_ns)
+{
+    if (!ctx) return SL1M_ERR_ARG;
+    NOT_WHILE_SERVING(ctx);
+    CK(cudaSetDevice(ctx->device));
+    constexpr int NB = 2;
+    DBuf<unsigned long long> w;
+    CK(w.alloc(NB));
+    CK(cudaMemsetAsync(w.p, 0, sizeof(unsigned long long) * NB, ctx->stream));
+    CKL(launch_wait_selftest(w.p, NB, ctx->stream));
+    unsigned long long hw[NB] = {0, 0};
+    CK(cudaMemcpyAsync(hw, w.p, sizeof hw, cudaMemcpyDeviceToHost, ctx->stream));
+    unsigned fault = 0;
+    CK(wait_fault_read(&fault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (waited_ns) *waited_ns = (int64_t)std::min(hw[0], hw[1]);
+    if (limit_ns) *limit_ns = (int64_t)wait_limit_ns();
+    return check_wait_fault(ctx, fault);
+}
+
+int sl1m_exact_tile_share(const sl1m_problem* prob, double* share, int64_t* n_tiles)
+{
+    if (!prob || !share) return SL1M_ERR_ARG;
+    if (prob->dirty || !prob->dev)
+        return sl1m_fail(prob->ctx, SL1M_ERR_STATE, "problem not laid out on the device yet");
+    // the test the mixed kernels make per tile: the granules' extents bound
+    // the FP32 product term D = (X - Xc).(Y - Yc) above D_MAX turns
+    long long n_ex = 0;
+    for (const float4& v : prob->gext_vis)
+        for (const float4& p : prob->gext_pix) n_ex += v.x * p.x + v.y * p.y + v.z * p.z > D_MAX;
+    const long long n = (long long)prob->gext_vis.size() * (long long)prob->gext_pix.size();
+    *share = n > 0 ? (double)n_ex / (double)n : 0.0;
+    if (n_tiles) *n_tiles = n;
     return SL1M_OK;
 }
 

@@ -154,6 +154,9 @@ struct sl1m_ctx {
     std::vector<ProfRec> pending;
     std::vector<cudaEvent_t> ev_pool;
     double prof_ms[NPROF] = {0}, prof_pairs[NPROF] = {0}, prof_bytes[NPROF] = {0};
+    // pairs evaluated by the operator kernels of solver ticks, counted on the
+    // device by the scalars kernel while profiling: [precision][0 fwd, 1 adj]
+    DBuf<double> evals_dev;
     long long prof_n[NPROF] = {0};
     long long n_launch = 0, h2d = 0, d2h = 0;
     cudaEvent_t get_event();

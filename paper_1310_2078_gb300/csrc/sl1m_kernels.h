@@ -31,6 +31,11 @@ cudaError_t launch_r32(const DevProblem* probs, int n_probs, int max_vis_pad, cu
 // after the stream is synchronised) and clear it.
 cudaError_t wait_fault_read(unsigned* host_flag, cudaStream_t st);
 cudaError_t wait_fault_clear(cudaStream_t st);
+// Self-test: n_blocks CTAs each wait on an mbarrier nobody arrives on; the
+// waits give up after wait_limit_ns() and set the flag above; waited_ns
+// [n_blocks] (device) receives how long each CTA's thread 0 waited.
+cudaError_t launch_wait_selftest(unsigned long long* waited_ns, int n_blocks, cudaStream_t st);
+unsigned long long wait_limit_ns();
 
 // solver kernels (sl1m_solver.cu)
 cudaError_t launch_gather_real(const double* src, double* dst, const int* orig, int n_pad,
@@ -49,7 +54,9 @@ cudaError_t launch_adj_finish(const DevProblem* probs, const Plan* plp, int grid
                               cudaStream_t st);
 cudaError_t launch_mfista_mix(const DevProblem* probs, const Plan* fplp, const Plan* aplp, int grid,
                               cudaStream_t st);
-cudaError_t launch_scalars(const DevProblem* probs, const int* n_probs, int grid, cudaStream_t st);
+// evals (may be null): [0] += pairs the forward and [1] += pairs the adjoint
+// evaluated in this tick, summed over the problems that took part.
+cudaError_t launch_scalars(const DevProblem* probs, const int* n_probs, int grid, double* evals, cudaStream_t st);
 cudaError_t launch_phases(const DevProblem* probs, const int* n_probs, int grid, int* out, cudaStream_t st);
 
 }  // namespace sl1m

@@ -399,7 +399,7 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                                   &s_gbar[b ^ 1]);
                 }
             }
-            if (!mbar_wait(&s_sbar[scur], (spar >> scur) & 1u)) fault = true;
+            mbar_wait(&s_sbar[scur], (spar >> scur) & 1u, fault);
             spar ^= 1u << scur;
             const unsigned char* sb = s_dyn + scur * S::BYTES;
             const float4* s_off = reinterpret_cast<const float4*>(sb + S::OFF);
@@ -411,7 +411,7 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
             const float2* gtab = s_gain;
             if (GAINS) {
                 const int b = gdbl ? gcur : 0;
-                if (!mbar_wait(&s_gbar[b], (gpar >> b) & 1u)) fault = true;
+                mbar_wait(&s_gbar[b], (gpar >> b) & 1u, fault);
                 gpar ^= 1u << b;
                 gtab = s_gain + b * gtab_n;
                 if (gdbl) gcur ^= 1;
@@ -755,7 +755,7 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
             if (threadIdx.x == 0 && gs + NSA < g1)  // prefetch the next stage
                 adj_stage_load<NSA>(s_dyn + (scur ^ 1) * S::BYTES, P, gs + NSA, min(NSA, g1 - gs - NSA),
                                     &s_sbar[scur ^ 1]);
-            if (!mbar_wait(&s_sbar[scur], (spar >> scur) & 1u)) fault = true;
+            mbar_wait(&s_sbar[scur], (spar >> scur) & 1u, fault);
             spar ^= 1u << scur;
             const unsigned char* sb = s_dyn + scur * S::BYTES;
             scur ^= 1;
@@ -942,11 +942,11 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
                 if (gauss) pgd[r] = pix_for_gauss(P.pgauss[eidx[r]]);
             }
             const SmemGain sg{s_gain, lane};
-            if (!mbar_wait(&s_gbar, gpar)) fault = true;
+            mbar_wait(&s_gbar, gpar, fault);
             gpar ^= 1u;
             double tot[2] = {0.0, 0.0};
             for (int g = g0 + warp; g < g1; g += BLK_GRAN) {
-                if (!mbar_wait(&s_wbar[warp], wpar)) fault = true;
+                mbar_wait(&s_wbar[warp], wpar, fault);
                 wpar ^= 1u;
                 // derive this granule's records for the tiles
 #pragma unroll
@@ -1071,6 +1071,33 @@ cudaError_t wait_fault_read(unsigned* host_flag, cudaStream_t st)
 {
     return cudaMemcpyFromSymbolAsync(host_flag, g_wait_fault, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, st);
 }
+// Self-test of the bounded wait: every thread waits on an mbarrier that
+// expects one arrival which nobody makes (no copy is issued, so nothing is in
+// flight).  The wait gives up after WAIT_LIMIT_NS, the CTA sets the fault flag
+// as the operator kernels do, records how long thread 0 waited, and returns.
+__global__ void __launch_bounds__(64) wait_selftest_kernel(unsigned long long* waited_ns)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    bool fault = false;
+    const unsigned long long t0 = global_ns();
+    mbar_wait(&bar, 0u, fault);
+    const unsigned long long t1 = global_ns();
+    if (threadIdx.x == 0) {
+        waited_ns[blockIdx.x] = t1 - t0;
+        if (fault) atomicOr(&g_wait_fault, 1u);
+    }
+}
+cudaError_t launch_wait_selftest(unsigned long long* waited_ns, int n_blocks, cudaStream_t st)
+{
+    wait_selftest_kernel<<<n_blocks, 64, 0, st>>>(waited_ns);
+    return cudaGetLastError();
+}
+unsigned long long wait_limit_ns() { return WAIT_LIMIT_NS; }
 cudaError_t wait_fault_clear(cudaStream_t st)
 {
     static const unsigned zero = 0;

@@ -360,7 +360,8 @@ __device__ long long warp_sum_fixed_i(const int* a, int n)
 }
 
 // The phase machine of every solve in the batch (end of a tick).
-__global__ void scalars_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ n_probs)
+__global__ void scalars_kernel(const DevProblem* __restrict__ probs, const int* __restrict__ n_probs,
+                               double* __restrict__ evals)
 {
     const int np = *n_probs;
     for (int p = blockIdx.x; p < np; p += gridDim.x) {
@@ -370,6 +371,13 @@ __global__ void scalars_kernel(const DevProblem* __restrict__ probs, const int* 
         const SolveBufs& B = P.b;
         const int nvb = P.vis.n_blk, npb = P.pix.n_blk;
         const int ph = S.phase;
+        // pairs the operator kernels of this tick evaluated for this problem
+        // (the roles of fwd_role / adj_role in the tick's phase)
+        if (evals && threadIdx.x == 0) {
+            const double pairs = (double)P.vis.n * (double)P.pix.n;
+            if (ph == PH_PINIT || ph == PH_POWER || ph == PH_SINIT || ph == PH_SOLVE) atomicAdd(&evals[0], pairs);
+            if (ph == PH_POWER || ph == PH_SOLVE) atomicAdd(&evals[1], pairs);
+        }
         // the mix kernel of the previous tick has run (stream order)
         if (threadIdx.x == 0) S.mix_pending = 0;
         if (ph == PH_PINIT) {
@@ -547,9 +555,9 @@ cudaError_t launch_mfista_mix(const DevProblem* probs, const Plan* fplp, const P
     return cudaGetLastError();
 }
 
-cudaError_t launch_scalars(const DevProblem* probs, const int* n_probs, int grid, cudaStream_t st)
+cudaError_t launch_scalars(const DevProblem* probs, const int* n_probs, int grid, double* evals, cudaStream_t st)
 {
-    scalars_kernel<<<grid, 32, 0, st>>>(probs, n_probs);
+    scalars_kernel<<<grid, 32, 0, st>>>(probs, n_probs, evals);
     return cudaGetLastError();
 }
 

@@ -38,6 +38,7 @@ EXPORTS = [
     "sl1m_server_start", "sl1m_server_submit", "sl1m_server_poll", "sl1m_server_wait",
     "sl1m_server_stop", "sl1m_server_info", "sl1m_forward_noalloc", "sl1m_autotune",
     "sl1m_dirty_image", "sl1m_solve_refine", "sl1m_get_solution", "sl1m_set_tile_shape",
+    "sl1m_exact_tile_share", "sl1m_selftest_bounded_wait", "sl1m_measure_sfu",
 ]
 
 
@@ -140,6 +141,9 @@ def load():
             "sl1m_profile_read": ([vp, C.c_int, C.POINTER(d), C.POINTER(i64), C.POINTER(d),
                                    C.POINTER(d)], C.c_int),
             "sl1m_problem_bytes": ([vp, C.POINTER(i64)], C.c_int),
+            "sl1m_exact_tile_share": ([vp, C.POINTER(d), C.POINTER(i64)], C.c_int),
+            "sl1m_selftest_bounded_wait": ([vp, C.POINTER(i64), C.POINTER(i64)], C.c_int),
+            "sl1m_measure_sfu": ([vp, C.POINTER(d), C.POINTER(d)], C.c_int),
             "sl1m_counters": ([vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)], C.c_int),
             "sl1m_counters_reset": ([vp], C.c_int),
             "sl1m_plan_preview": ([i32, vp, vp, i32, vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32),
@@ -287,6 +291,19 @@ class Context:
 
     def counters_reset(self):
         self.check(self.lib.sl1m_counters_reset(self.h))
+
+    def measure_sfu(self):
+        """sl1m_measure_sfu: {"sincos_per_s": ..., "ex2_per_s": ...} (results/s, device)."""
+        a, b = C.c_double(), C.c_double()
+        self.check(self.lib.sl1m_measure_sfu(self.h, C.byref(a), C.byref(b)))
+        return {"sincos_per_s": a.value, "ex2_per_s": b.value}
+
+    def selftest_bounded_wait(self):
+        """sl1m_selftest_bounded_wait: (status, waited_ns, limit_ns); status
+        SL1M_ERR_CUDA is the expected outcome (the wait gave up)."""
+        w, lim = C.c_int64(), C.c_int64()
+        st = self.lib.sl1m_selftest_bounded_wait(self.h, C.byref(w), C.byref(lim))
+        return st, w.value, lim.value
 
     # ---- continuous-batching server (sl1m_server_*)
     def server_start(self, mem_budget_bytes=0, max_slots=0, ticks_per_round=0, precision=MIXED,
@@ -471,6 +488,12 @@ class Problem:
         b = C.c_int64()
         self.ctx.check(self.lib.sl1m_problem_bytes(self.h, C.byref(b)))
         return b.value
+
+    def exact_tile_share(self):
+        """sl1m_exact_tile_share: (share of tiles on the exact phase path, tiles)."""
+        sh, n = C.c_double(), C.c_int64()
+        self.ctx.check(self.lib.sl1m_exact_tile_share(self.h, C.byref(sh), C.byref(n)))
+        return sh.value, n.value
 
     def close(self):
         if getattr(self, "h", None) and self.ctx.h:

@@ -1,0 +1,76 @@
+"""Image parity where the mixed-precision path is stressed.
+
+The other image-parity tests iterate on narrow fields.  Here the solver runs
+on the wide-field geometry -- l, m over +/-0.5, where the w-term of
+Eq. deltam (n - 1 up to -0.13) is significant, 64 antennas in a 2 km disk
+with 50 m height scatter, 20 snapshots: all 40,320 visibilities -- at 64x64
+pixels, so that some tiles take the exact phase path (asserted), and on a
+reduced gains + multiscale geometry (jittered grid at Dirac and wide-field
+Gaussian scales, per-antenna beam x phase-ramp gains, Eq. samlm5).  Both
+precisions are held, after the same FISTA steps with the same L and lambda
+(Sect. 3 algorithm box), to 1e-4 of the peak of the oracle's image and to
+1e-6 relative in E.  The oracle runs with its outer loops threaded over the
+host cores (bitwise the single-threaded result).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1310_2078_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+THREADS = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def ctx(gpu_lib):
+    c = gpu_lib.Context(0)
+    yield c
+    c.close()
+
+
+def _solve_both(ctx, w, iters, exact_share_min=None):
+    O = oracle.Problem(w.uvw, w.lm, w.sigma, w.kind, w.weights, w.ant_pair, w.gains, threads=THREADS)
+    V = oracle.forward(O, w.x_true) + w.noise
+    L, _ = oracle.power(O, max_iter=20)            # the same L for both sides
+    lam = w.lambda_frac * oracle.adjoint(O, V).max()
+    img_o, st_o = oracle.fista(O, V, lam, L, iters)
+    P = ctx.problem()
+    P.set_visibilities(w.uvw, V, w.weights, w.ant_pair)
+    P.set_pixels(w.lm, w.sigma, w.kind)
+    if w.gains is not None:
+        P.set_gains(w.gains)
+    out = {}
+    for prec in (0, 1):
+        img, st = P.solve(lam, L=L, max_iter=iters, precision=prec)
+        assert st["iters"] == iters
+        err = np.max(np.abs(img - img_o)) / img_o.max()
+        assert err <= 1e-4, (prec, err)
+        assert st["E"] == pytest.approx(st_o["E"], rel=1e-6), prec
+        assert st["nnz"] == pytest.approx(st_o["nnz"], abs=max(2, 0.01 * st_o["nnz"]))
+        out[prec] = err
+    share, n_tiles = P.exact_tile_share()
+    P.close()
+    return share, n_tiles, out
+
+
+def test_wide_field_64x64_all_visibilities_50_steps(ctx):
+    """Wide field, 64^2 pixels x 40,320 visibilities, 50 FISTA steps."""
+    w = synth.config2(n_side=64)
+    assert (w.n_pix, w.n_vis) == (4096, 40320)
+    share, n_tiles, _ = _solve_both(ctx, w, 50)
+    assert n_tiles == 64 * 630 and share > 0.0     # the exact phase path is exercised
+
+
+def test_gains_multiscale_reduced_50_steps(ctx):
+    """The gains + multiscale geometry at a quarter of its grid side: a 32^2
+    jittered grid at Dirac and wide-field Gaussian sigma = 1, 2, 4 pixels
+    (4,096 pixels), beam x phase-ramp gains on 64 antennas, 4 snapshots
+    (8,000 visibilities), 50 FISTA steps."""
+    w = synth.config3(n_side=32, n_times=4, max_vis=8000)
+    assert (w.n_pix, w.n_vis) == (4096, 8000) and w.gains is not None
+    assert set(np.unique(w.kind)) == {0, 2}
+    _solve_both(ctx, w, 50)
