@@ -12,6 +12,14 @@
 // SCRATCH_BYTES, that every GPU loading this library holds until the process
 // exits.  The call makes no cudaMalloc / cudaFree and calls no allocating
 // library routine.  The paper has no counterpart: this is plumbing.
+//
+// The per-call host data (descriptor, plan header and work-split tables) is
+// built on the host and written into the array by small kernels that carry
+// it in their parameters: a launch snapshots its parameters, so the call
+// enqueues work and returns without waiting for the stream (a copy from
+// pageable host memory would wait for it), and the host data may go out of
+// scope at once.
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -33,6 +41,39 @@ void* g_scratch_dev[MAX_DEVICES] = {nullptr};
 std::mutex g_scratch_mu;
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Up to STAGE_WORDS 32-bit words of host data, carried by value in a kernel's
+// parameters (16 KB, inside the 32 KB parameter space of sm_70 and later).
+constexpr int STAGE_WORDS = 4096;
+struct StageChunk {
+    unsigned* dst;
+    int n_words;
+    unsigned w[STAGE_WORDS];
+};
+
+__global__ void __launch_bounds__(256) stage_words_kernel(const StageChunk c)
+{
+    for (int i = threadIdx.x; i < c.n_words; i += blockDim.x) c.dst[i] = c.w[i];
+}
+
+// Write n_bytes (a multiple of 4) of host data to dst on stream st, in
+// chunks of STAGE_WORDS words; returns the launches made through *n_launch.
+cudaError_t stage_to_device(unsigned char* dst, const unsigned char* src, size_t n_bytes, cudaStream_t st,
+                            long long* n_launch)
+{
+    StageChunk c;
+    for (size_t at = 0; at < n_bytes; at += sizeof(c.w)) {
+        const size_t nb = std::min(sizeof(c.w), n_bytes - at);
+        c.dst = (unsigned*)(dst + at);
+        c.n_words = (int)(nb / 4);
+        std::memcpy(c.w, src + at, nb);
+        stage_words_kernel<<<1, 256, 0, st>>>(c);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        ++*n_launch;
+    }
+    return cudaSuccess;
+}
 
 }  // namespace
 
@@ -91,7 +132,8 @@ extern "C" int sl1m_forward_noalloc(sl1m_problem* prob, const double* x_dev, dou
         return sl1m_fail(ctx, SL1M_ERR_ARG,
                          "problem needs %zu bytes of scratch; sl1m_forward_noalloc holds %zu (32 MiB)", off,
                          SCRATCH_BYTES);
-    // fill descriptor and plan (pageable host sources are staged before the calls return)
+    // descriptor, plan header and tables: laid out on the host exactly as the
+    // scratch is carved above, then written by kernels carrying them by value
     DevProblem d = lay;
     d.st = nullptr;
     d.x = d_x;
@@ -109,24 +151,30 @@ extern "C" int sl1m_forward_noalloc(sl1m_problem* prob, const double* x_dev, dou
     pl.blk_ncon = d_ncon;
     pl.n_blocks = H.n_blocks;
     pl.n_slots = H.n_slots;
-    cudaStream_t st = ctx->stream;
+    const size_t head = (size_t)((unsigned char*)d_x - base);     // descriptor .. tables
+    std::vector<unsigned char> img(head, 0);
+    auto put = [&](void* at, const void* src, size_t bytes) {
+        if (bytes) std::memcpy(img.data() + ((unsigned char*)at - base), src, bytes);
+    };
     const int zero = 0;
+    put(d_desc, &d, sizeof d);
+    put(d_plan, &pl, sizeof pl);
+    put(d_u0, H.u0.data(), sizeof(long long) * H.u0.size());
+    put(d_b0, H.b0.data(), sizeof(int) * H.b0.size());
+    if (!H.poff.empty()) {
+        put(d_poff, H.poff.data(), sizeof(int) * H.poff.size());
+        put(d_clo, H.clo.data(), sizeof(int) * H.clo.size());
+        put(d_ncon, H.ncon.data(), sizeof(int) * H.ncon.size());
+    } else {
+        put(d_ncon, &zero, sizeof(int));
+    }
+    cudaStream_t st = ctx->stream;
 #define CKN(call)                                                                                     \
     do {                                                                                              \
         cudaError_t e_ = (call);                                                                      \
         if (e_ != cudaSuccess) return sl1m_fail(ctx, SL1M_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
-    CKN(cudaMemcpyAsync(d_desc, &d, sizeof d, cudaMemcpyHostToDevice, st));
-    CKN(cudaMemcpyAsync(d_plan, &pl, sizeof pl, cudaMemcpyHostToDevice, st));
-    CKN(cudaMemcpyAsync(d_u0, H.u0.data(), sizeof(long long) * H.u0.size(), cudaMemcpyHostToDevice, st));
-    CKN(cudaMemcpyAsync(d_b0, H.b0.data(), sizeof(int) * H.b0.size(), cudaMemcpyHostToDevice, st));
-    if (!H.poff.empty()) {
-        CKN(cudaMemcpyAsync(d_poff, H.poff.data(), sizeof(int) * H.poff.size(), cudaMemcpyHostToDevice, st));
-        CKN(cudaMemcpyAsync(d_clo, H.clo.data(), sizeof(int) * H.clo.size(), cudaMemcpyHostToDevice, st));
-        CKN(cudaMemcpyAsync(d_ncon, H.ncon.data(), sizeof(int) * H.ncon.size(), cudaMemcpyHostToDevice, st));
-    } else {
-        CKN(cudaMemcpyAsync(d_ncon, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
-    }
+    CKN(stage_to_device(base, img.data(), head, st, &ctx->n_launch));
     // every partial slot the finish reads is written by exactly one CTA of this
     // launch, so nothing in the scratch needs clearing
     CKN(launch_gather_real(x_dev, d_x, lay.pix.orig, lay.pix.n_pad, 1.0, st));
