@@ -1,18 +1,25 @@
 """Benchmark of the SL1M hot path on GB300.
 
-Workload (default): the wide-field w-term configuration -- 256x256 = 65,536
-Dirac pixels over l,m in +/-0.5, 64 antennas (R = 2 km, 50 m height scatter),
-20 snapshots -> 40,320 visibilities, 200 point sources + noise, mixed
-precision.  One step = one complete solve through the C ABI: L by power
-iteration (<= 50 steps, tol 1e-6), then 200 FISTA steps with
-lambda = 0.02 * max Re(A^H V).  Metric: pixel-visibility pairs evaluated per
-second by the forward and adjoint kernels (pairs/s), whole job.
+Workload (default): the paper-scale configuration -- 1024x1024 = 1,048,576
+Dirac pixels over l,m in +/-0.3, 128 antennas (R = 1 km, 30 m height
+scatter) x 50 snapshots -> 406,400 visibilities, 2,000 power-law sources +
+noise, mixed precision (FP32 operator, FP64 solver scalars).  L is computed
+once by power iteration (untimed); one step = `--iters` FISTA steps (default
+5) at that L through the C ABI's solve call, each one forward and one
+adjoint over all 4.26e11 pixel-visibility pairs, plus the forward of I_0.
+Metric: pixel-visibility pairs evaluated per second by the forward and
+adjoint kernels (pairs/s), whole job.
 
-value : inputs resident in HBM when the timed region starts; each step timed
-        with CUDA events on the library's stream, L2 flushed between steps.
-e2e   : the same solve through the C ABI from HOST buffers: setting the
-        visibilities and pixels (layout + H2D) and reading the image back are
-        inside the timed region.
+value   : inputs resident in HBM when the timed region starts; each step
+          timed with CUDA events on the library's stream, L2 flushed between
+          steps.
+e2e     : the same steps through the C ABI from HOST buffers: setting the
+          visibilities and pixels (layout + H2D) and reading the image back
+          are inside the timed region.
+serving : a shortened serving stream (independent solves of uneven sizes
+          arriving as a Poisson process) through the continuous-batching
+          server: solves/s, p50/p99 latency, and the FP64 plain single-solve
+          path on the same requests.
 --impl reference : the FP64 CPU oracle on the host cores, bounded sample.
 """
 from __future__ import annotations
@@ -39,19 +46,22 @@ SM_MAX_MHZ = 2070.0
 L2_BYTES = 129 * 2 ** 20
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--config", type=int, default=4)
     ap.add_argument("--small", action="store_true",
                     help="config 2 at 128x128 pixels (a small case for ncu captures)")
     ap.add_argument("--n-side", type=int, default=0, help="override: pixel grid side")
     ap.add_argument("--n-ant", type=int, default=0, help="override: antennas")
     ap.add_argument("--n-times", type=int, default=0, help="override: snapshots")
-    ap.add_argument("--iters", type=int, default=200)
+    ap.add_argument("--iters", type=int, default=0,
+                    help="FISTA steps per bench step (default 5; 200 with --full-solve)")
+    ap.add_argument("--full-solve", action="store_true",
+                    help="a step is one whole solve: power iteration for L, then --iters FISTA steps")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="skip the (untimed) tile-shape autotuner")
@@ -63,13 +73,36 @@ def parse():
     ap.add_argument("--ops-only", action="store_true",
                     help="a step is one forward + one adjoint through the C ABI (device pointers)")
     ap.add_argument("--serve", action="store_true",
-                    help="serving workload: Poisson stream of independent solves through the server")
-    ap.add_argument("--requests", type=int, default=256)
-    ap.add_argument("--rate", type=float, default=20.0)
+                    help="serving workload alone: Poisson stream of independent solves through the server")
+    ap.add_argument("--requests", type=int, default=0,
+                    help="serving requests (default 256 with --serve, 48 in the default line)")
+    ap.add_argument("--rate", type=float, default=0.0,
+                    help="serving arrival rate, 1/s (default 20 with --serve, 2 in the default line)")
+    ap.add_argument("--no-serve", action="store_true", help="leave the serving object out of the line")
     ap.add_argument("--fp64-sample", type=int, default=3)
     ap.add_argument("--ticks", type=int, default=4, help="serving: ticks per round")
     ap.add_argument("--max-pairs", type=float, default=4e9, help="serving: work in flight per tick")
-    return ap.parse_args()
+    args = ap.parse_args(argv)
+    if not args.iters:
+        args.iters = 200 if args.full_solve else 5
+    return args
+
+
+def step_text(args) -> str:
+    """What one timed step is (the config's `step`)."""
+    if args.ops_only:
+        return "one forward + one adjoint (device pointers)"
+    if args.full_solve:
+        return f"one solve: power iteration (<=50) + {args.iters} FISTA steps"
+    return (f"{args.iters} FISTA steps at a fixed L (power iteration once, untimed), each one "
+            "forward + one adjoint, plus the forward of I_0, through sl1m_solve")
+
+
+def bench_config(args, w) -> dict:
+    """The line's `config`, the same for both arms."""
+    return {"workload": w.name, "n_pix": w.n_pix, "n_vis": w.n_vis, "step": step_text(args),
+            "precision": args.precision, "l2": "flushed between steps (268 MB write)",
+            "parallelism": f"replicas{args.gpus}" if args.gpus > 1 else "1 GPU"}
 
 
 def dist_init():
@@ -259,6 +292,21 @@ def sfu_peak(w):
     return peak, basis, alt
 
 
+def sfu_peak_measured(w, sfu):
+    """The SFU bound of workload w from the measured MUFU rates (Gpairs/s):
+    a pair takes a sin and a cos, and an exp2 when its pixel is Gaussian, so
+    its time on the unit is 2 / (sin-or-cos rate) + f_gauss / (exp2 rate)."""
+    kinds = np.zeros(w.n_pix, np.int32) if w.kind is None else np.asarray(w.kind)
+    f_gauss = float(np.mean(kinds != 0))
+    t_pair = 2.0 / sfu["sincos_per_s"] + f_gauss / sfu["ex2_per_s"]
+    per_clk_sm = {k: v / (N_SM * SM_MAX_MHZ * 1e6) for k, v in sfu.items()}
+    return {"peak": 1.0 / t_pair / 1e9,
+            "basis": "sl1m_measure_sfu: sin/cos and exp2 results per second on this GPU; "
+                     f"2 sin/cos + {f_gauss:.3g} exp2 per pair",
+            "measured_per_s": sfu,
+            "per_clk_per_sm_at_max_clock": per_clk_sm}
+
+
 def baseline_inputs(w):
     """The seeded x [n_pix] and r [n_vis] the CPU-baseline sample runs on."""
     rng = np.random.default_rng(0)
@@ -267,7 +315,7 @@ def baseline_inputs(w):
     return x, r
 
 
-def cpu_baseline(w, gpu_fwd=None, gpu_adj=None, budget_s: float = 12.0):
+def cpu_baseline(w, gpu_fwd=None, gpu_adj=None, budget_s: float = 12.0, threaded: bool = True):
     """The FP64 oracle as it stands, single-threaded, on a bounded sample of
     the same workload: forward rows and adjoint columns; pairs/s.  Given the
     library's forward A x and adjoint Re A^H r of the same inputs, the sampled
@@ -283,8 +331,13 @@ def cpu_baseline(w, gpu_fwd=None, gpu_adj=None, budget_s: float = 12.0):
     n_rows = max(8, int(0.5 * budget_s / per_row))
     n_cols = max(8, int(0.5 * budget_s / (per_row * w.n_vis / w.n_pix)))
     # prefixes of fixed permutations: a run that samples more rows or columns
-    # keeps every row and column of a smaller sample, so errors compare across runs
-    rows = np.random.default_rng(1).permutation(w.n_vis)[:min(n_rows, w.n_vis)]
+    # keeps every row and column of a smaller sample, so errors compare across
+    # runs.  The rows also hold the 8 shortest baselines: for the positive x
+    # below |V_k| peaks there, so the sample's max |V| is the vector's and the
+    # error is normwise over the whole output, as defined.
+    short = np.argsort(np.sum(np.asarray(w.uvw)[:, :2] ** 2, axis=1))[:8]
+    perm = np.random.default_rng(1).permutation(w.n_vis)
+    rows = np.concatenate([short, perm[~np.isin(perm, short)][:max(0, min(n_rows, w.n_vis) - 8)]])
     cols = np.random.default_rng(2).permutation(w.n_pix)[:min(n_cols, w.n_pix)]
     t0 = time.perf_counter()
     fo = oracle.forward(O, x, rows=rows)
@@ -292,9 +345,11 @@ def cpu_baseline(w, gpu_fwd=None, gpu_adj=None, budget_s: float = 12.0):
     dt = time.perf_counter() - t0
     pairs = len(rows) * w.n_pix + len(cols) * w.n_vis
     out = {"value": pairs / dt, "unit": "pairs/s", "cores": 1, "kind": "oracle",
-           "sample": f"{len(rows)} forward rows x {w.n_pix} px + {len(cols)} adjoint "
-                     f"columns x {w.n_vis} vis of {w.name}, FP64, single thread, {dt:.1f} s"}
-    out["threaded"] = cpu_threaded(O, x, r, rows, cols, fo, ao, pairs)
+           "sample": f"{len(rows)} forward rows (the 8 shortest baselines + a random sample) x {w.n_pix} px "
+                     f"+ {len(cols)} adjoint columns x {w.n_vis} vis of {w.name}, FP64, single thread, {dt:.1f} s",
+           "pairs": float(pairs), "seconds": dt}
+    if threaded:
+        out["threaded"] = cpu_threaded(O, x, r, rows, cols, fo, ao, pairs)
     if gpu_fwd is not None and gpu_adj is not None:
         out["gpu_error_vs_oracle"] = {
             "forward": float(np.max(np.abs(gpu_fwd[rows] - fo)) / np.max(np.abs(fo))),
@@ -305,15 +360,17 @@ def cpu_baseline(w, gpu_fwd=None, gpu_adj=None, budget_s: float = 12.0):
 
 def oracle_stream_estimate(reqs, picks, stream_pairs, budget_s: float = 6.0):
     """The FP64 oracle, single-threaded, timed on bounded samples of the
-    requests `picks` of a serving stream; the mean of their pair rates,
-    applied to the pairs the whole stream evaluated, estimates a serial
+    requests `picks` of a serving stream; their total pairs over their total
+    time, applied to the pairs the whole stream evaluated, estimates a serial
     oracle run of every request (solves/s)."""
-    samples = [dict(request=int(i), **cpu_baseline(reqs[i], budget_s=budget_s)) for i in picks]
-    rate = float(np.mean([smp["value"] for smp in samples]))
+    samples = [dict(request=int(i), **cpu_baseline(reqs[i], budget_s=budget_s, threaded=False))
+               for i in picks]
+    rate = sum(smp["pairs"] for smp in samples) / sum(smp["seconds"] for smp in samples)
     wall = stream_pairs / rate
     return {"value": len(reqs) / wall, "unit": "solves/s", "cores": 1, "kind": "oracle",
             "sample": f"FP64 oracle forward rows + adjoint columns of requests {[int(i) for i in picks]}, "
-                      "single thread; their mean pair rate applied to all requests' pairs (serial)",
+                      "single thread; their pair rate (total pairs / total time) applied to all "
+                      "requests' pairs (serial)",
             "pairs_per_s": rate, "est_wall_s": wall, "samples": samples}
 
 
@@ -385,7 +442,7 @@ def run_reference(args):
            "unit": "pairs/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * T / len(times), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": w.name, "n_pix": w.n_pix, "n_vis": w.n_vis},
+           "config": bench_config(args, w),
            "cpu_baseline": {"value": val, "unit": "pairs/s", "cores": 1, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": val, "unit": "pairs/s", "h2d_bytes_per_step": 0,
@@ -393,21 +450,22 @@ def run_reference(args):
     print(json.dumps(out))
 
 
-def run_serve(args):
-    """Continuous batching: `requests` independent solves arriving as a
+def serving_measure(n_requests, rate, ticks=4, max_pairs=4e9, fp64_sample=3, with_cpu=True, dev=0):
+    """Continuous batching: `n_requests` independent solves arriving as a
     Poisson stream (`rate` per second), each an independently generated
     array/sky with 4k-256k pixels and 2k-100k visibilities, Dirac or wide
     Gaussian pixels, gains on half of them; 200 FISTA steps or relative change
-    of E below 1e-6, L by power iteration.  Reports solves/s, p50/p99 latency
-    (submit to result), pairs/s, and the FP64 plain single-solve path on the
-    smallest requests (serial, same iterations) for comparison."""
+    of E below 1e-6, L by power iteration.  Returns solves/s, latency
+    percentiles (submit to result), pairs/s, and the FP64 plain single-solve
+    path on a sample of the same requests (same L and iterations, serial):
+    its time, its final objective against the mixed path's, and its pair
+    rate applied to the whole stream."""
     import torch
     from paper_1310_2078_gb300 import sl1m, synth
     sl1m.load()
-    dev = 0
     torch.cuda.set_device(dev)
-    reqs = [synth.serving_request(i) for i in range(args.requests)]
-    arrive = synth.arrivals(args.requests, args.rate)
+    reqs = [synth.serving_request(i) for i in range(n_requests)]
+    arrive = synth.arrivals(n_requests, rate)
     ctx = sl1m.Context(dev)
     # data: V = A x_true + noise through the library's forward (mixed), lambda from the dirty image
     probs, lams = [], []
@@ -419,7 +477,7 @@ def run_serve(args):
         probs.append((P, V))
     torch.cuda.synchronize()
     ctx.counters_reset()
-    ctx.server_start(max_slots=64, ticks_per_round=args.ticks, max_pairs_per_tick=args.max_pairs)
+    ctx.server_start(max_slots=64, ticks_per_round=ticks, max_pairs_per_tick=max_pairs)
     clocks = ClockSampler(dev)
     clocks.start()
     t0 = time.perf_counter()
@@ -434,16 +492,23 @@ def run_serve(args):
     clk = clocks.stop()
     info = ctx.server_info()
     ctx.server_stop()
+    launches = ctx.counters()["launches"]
     lat = np.array([st["seconds"] for _, st in results])
-    pairs = sum((2 * st["power_iters"] + 2 * st["iters"] + 2) * float(w.n_vis) * w.n_pix
-                for (_, st), w in zip(results, reqs))
-    # FP64 plain single-solve path on the smallest requests (serial, same iterations)
-    # FP64 sample: requests spread over the lower half of the work distribution
+    req_pairs = [(2 * st["power_iters"] + 2 * st["iters"] + 2) * float(w.n_vis) * w.n_pix
+                 for (_, st), w in zip(results, reqs)]
+    pairs = sum(req_pairs)
+    # the slowest requests: their size and their work at the stream's pair rate
+    slowest = [{"request": int(i), "n_pix": reqs[i].n_pix, "n_vis": reqs[i].n_vis,
+                "iters": results[i][1]["iters"], "latency_s": float(lat[i]),
+                "own_work_s_at_stream_rate": req_pairs[i] / (pairs / T)}
+               for i in np.argsort(-lat)[:5]]
+    # FP64 plain single-solve path: requests spread over the lower half of the
+    # work distribution, each solved alone with the served solve's L and
+    # iterations, and the mixed path alone on the same request beside it
     by_work = np.argsort([w.pairs for w in reqs])
-    ranks = np.unique(np.linspace(0, len(reqs) // 2, max(1, args.fp64_sample)).astype(int))
-    order = by_work[ranks]
+    ranks = np.unique(np.linspace(0, len(reqs) // 2, max(1, fp64_sample)).astype(int))
     cmp = []
-    for i in order:
+    for i in by_work[ranks]:
         P, V = probs[i]
         st_m = results[i][1]
         t1 = time.perf_counter()
@@ -455,39 +520,47 @@ def run_serve(args):
         cmp.append({"request": int(i), "n_pix": reqs[i].n_pix, "n_vis": reqs[i].n_vis,
                     "iters": st_m["iters"], "fp64_s": t64, "mixed_alone_s": tm,
                     "E_rel_diff": abs(stm["E"] - st64["E"]) / st64["E"],
+                    "served_E_rel_diff": abs(st_m["E"] - st64["E"]) / st64["E"],
                     "img_err_of_peak": float(np.max(np.abs(imgm - img64)) / max(img64.max(), 1e-300))})
     fp64_solves_per_s = len(cmp) / sum(c["fp64_s"] for c in cmp) if cmp else None
     # the FP64 plain path solving every request serially: its pair rate on the
     # sample (same iterations, L given) applied to the whole stream's pairs
-    fp64_pairs = sum((2 * c["iters"] + 2) * float(c["n_vis"]) * c["n_pix"] for c in cmp)
+    fp64_pairs = sum((2 * c["iters"] + 1) * float(c["n_vis"]) * c["n_pix"] for c in cmp)
     fp64_rate = fp64_pairs / sum(c["fp64_s"] for c in cmp) if cmp else None
-    fp64_serial = ({"pairs_per_s": fp64_rate, "est_wall_s": pairs / fp64_rate,
-                    "est_solves_per_s": args.requests / (pairs / fp64_rate),
-                    "method": "FP64 single solves, pair rate measured on the sample, "
-                              "applied to all requests' pairs (serial, no overlap)"}
-                   if fp64_rate else None)
-    # the FP64 oracle on the host cores: the smallest and the median request sampled
+    fp64_serial = None
+    if fp64_rate:
+        est = n_requests / (pairs / fp64_rate)
+        fp64_serial = {"pairs_per_s": fp64_rate, "est_wall_s": pairs / fp64_rate, "est_solves_per_s": est,
+                       "served_over_fp64": (n_requests / T) / est,
+                       "method": "FP64 single solves, pair rate measured on the sample, "
+                                 "applied to all requests' pairs (serial, no overlap)"}
     cpu = None
-    if not args.no_cpu:
+    if with_cpu:
         cpu = oracle_stream_estimate(reqs, [by_work[0], by_work[len(by_work) // 2]], pairs)
-    out = {"metric": "solves/s (continuous batching, mixed precision)", "value": args.requests / T,
+    out = {"metric": "solves/s (continuous batching, mixed precision)", "value": n_requests / T,
            "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32+f64",
            "data": "synthetic",
-           "config": {"workload": f"serving: {args.requests} requests, Poisson {args.rate}/s, "
+           "config": {"workload": f"serving: {n_requests} requests, Poisson {rate:g}/s, "
                                   "pixels logU(4k,256k), visibilities logU(2k,100k), "
                                   "Dirac/wide-Gaussian 50/50, gains on 50%",
-                      "max_slots": 64, "ticks_per_round": args.ticks,
-                      "max_pairs_per_tick": args.max_pairs},
+                      "max_slots": 64, "ticks_per_round": ticks, "max_pairs_per_tick": max_pairs},
            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                          "mean": float(lat.mean()), "max": float(lat.max())},
-           "pairs_per_s": pairs / T, "wall_s": T,
+           "pairs_per_s": pairs / T, "wall_s": T, "slowest": slowest,
            "iters_mean": float(np.mean([st["iters"] for _, st in results])),
-           "server": info, "clocks": clk, "gpu_launches": ctx.counters()["launches"],
+           "server": info, "clocks": clk, "gpu_launches": launches,
            "fp64_plain_single_solve": {"sample": cmp, "solves_per_s_on_sample": fp64_solves_per_s,
                                        "serial_whole_stream": fp64_serial},
            "cpu_baseline": cpu}
-    print(json.dumps(out))
     ctx.close()
+    return out
+
+
+def run_serve(args):
+    """--serve: the serving stream alone, as its own line."""
+    out = serving_measure(args.requests or 256, args.rate or 20.0, args.ticks, args.max_pairs,
+                          args.fp64_sample, not args.no_cpu)
+    print(json.dumps(out))
 
 
 def main():
@@ -523,6 +596,7 @@ def main():
                  "npoly": [sh[0][2], sh[1][2]], "source": "--shape"}
     else:
         tuned = None if args.no_autotune else P.autotune(prec)
+    sfu = ctx.measure_sfu()                                      # untimed: the measured MUFU rate
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
 
     if args.ops_only:
@@ -534,9 +608,14 @@ def main():
             P.forward_dev(xs, vs, prec)
             P.adjoint_dev(vs, img_d, prec)
             return None, {"iters": 0, "power_iters": 0, "E": 0.0, "resid2": 0.0, "nnz": 0, "L": 0.0}
-    else:
+    elif args.full_solve:
         def one_step():
             return P.solve(lam, L=0.0, max_iter=args.iters, precision=prec)
+    else:
+        L_fixed, _ = P.max_eig(50, 1e-6, prec)                 # once, untimed
+
+        def one_step():
+            return P.solve(lam, L=L_fixed, max_iter=args.iters, precision=prec)
 
     for _ in range(args.warmup):
         one_step()
@@ -573,7 +652,8 @@ def main():
     op_pairs = sum(prof[k]["pairs"] for k in ("fwd_fp64", "adj_fp64", "fwd_mixed", "adj_mixed"))
     T_job, pairs_job = job_totals(T, op_pairs, ws, f"cuda:{dev}")
     value = pairs_job / T_job
-    solves_per_s = ws * args.steps / T_job
+    rate_key, rate_val = (("solves_per_s", ws * args.steps / T_job) if args.full_solve else
+                          ("fista_steps_per_s", ws * args.steps * args.iters / T_job))
 
     # roofline of the dominant kernel
     keys = ("fwd_mixed", "adj_mixed") if prec == sl1m.MIXED else ("fwd_fp64", "adj_fp64")
@@ -593,6 +673,9 @@ def main():
     if alt:
         roofline["peak_sfu_plus_fma_sincos"] = alt
         roofline["frac_of_sfu_plus_fma_sincos"] = achieved / alt["peak"]
+    meas = sfu_peak_measured(w, sfu)
+    roofline["peak_measured_sfu"] = meas
+    roofline["frac_of_measured_sfu"] = achieved / meas["peak"]
     per_kernel = {k: {"launches": prof[k]["launches"],
                       "avg_launch_ms": prof[k]["ms"] / max(1, prof[k]["launches"]),
                       "Gpairs_per_s": prof[k]["pairs"] / (prof[k]["ms"] / 1e3) / 1e9,
@@ -606,65 +689,71 @@ def main():
 
     e2e = None
     if not args.no_e2e and not args.ops_only:
-        e2e = run_e2e(ctx, w, V, lam, prec, args, sl1m, stream, ws)
+        e2e = run_e2e(ctx, w, V, lam, 0.0 if args.full_solve else L_fixed, prec, args, sl1m, stream, ws)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         xb, rb = baseline_inputs(w)
         cpu = cpu_baseline(w, P.forward(xb, prec), P.adjoint(rb, prec))
+    ctx.close()
+    serving = None
+    if rank == 0 and ws == 1 and not args.no_serve and not args.ops_only:
+        del flush
+        torch.cuda.empty_cache()
+        serving = serving_measure(args.requests or 48, args.rate or 2.0, args.ticks, args.max_pairs,
+                                  args.fp64_sample, not args.no_cpu, dev)
     if rank == 0:
         out = {"metric": "pixel-visibility pairs/s (fwd+adj)", "value": value, "unit": "pairs/s",
                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": 1e3 * T_job / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None,
                "dtype": "f32+f64" if prec == sl1m.MIXED else "f64", "data": "synthetic",
-               "config": {"workload": w.name, "n_pix": w.n_pix, "n_vis": w.n_vis,
-                          "step": ("one forward + one adjoint (device pointers)" if args.ops_only else
-                                   f"one solve: power iteration (<=50) + {args.iters} FISTA steps"),
-                          "precision": args.precision, "lambda": lam,
-                          "l2": "flushed between steps (268 MB write)",
-                          "tile_shape": tuned,
-                          "parallelism": f"replicas{ws}" if ws > 1 else "1 GPU"},
-               "solves_per_s": solves_per_s,
+               "config": bench_config(args, w), "lambda": lam, "tile_shape": tuned,
+               rate_key: rate_val,
                "iters": [s["iters"] for s in stats], "power_iters": stats[-1]["power_iters"],
                "final": {"E": stats[-1]["E"], "resid2": stats[-1]["resid2"],
                          "nnz": stats[-1]["nnz"], "L": stats[-1]["L"]},
                "roofline": roofline, "operator_kernels": per_kernel, "vector_updates": vec,
                "clocks": clk, "gpu_launches": counters["launches"],
-               "e2e": e2e, "cpu_baseline": cpu}
+               "e2e": e2e, "cpu_baseline": cpu, "serving": serving}
         print(json.dumps(out))
-    ctx.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
 
 
-def run_e2e(ctx, w, V, lam, prec, args, sl1m, stream, ws=1):
-    """The same solve from host buffers through the C ABI: set inputs (host
-    layout + H2D), solve, read the image back (D2H) -- all timed.  With
-    several ranks, each solves its own problem between two barriers and the
-    value is all ranks' pairs over the slowest rank's time."""
+def run_e2e(ctx, w, V, lam, L, prec, args, sl1m, stream, ws=1):
+    """The same steps from host buffers through the C ABI, every step: set the
+    inputs (host layout + H2D), solve (L given, or computed when 0), read the
+    image back (D2H) -- all timed, over as many steps as the device-timed
+    figure.  With several ranks, each solves its own problem between two
+    barriers and the value is all ranks' pairs over the slowest rank's time."""
     import torch
-    steps = max(1, min(args.steps, 3))
+    steps = max(1, args.steps)
     ctx.counters_reset()
+    ctx.profile_reset()
+    ctx.profile_enable(True)
     if ws > 1:
         torch.distributed.barrier()
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    pairs = 0.0
     for _ in range(steps):
         Q = ctx.problem()
         Q.set_visibilities(w.uvw, V, w.weights, w.ant_pair)
         Q.set_pixels(w.lm, w.sigma, w.kind)
         if w.gains is not None:
             Q.set_gains(w.gains)
-        img, st = Q.solve(lam, L=0.0, max_iter=args.iters, precision=prec)
-        pairs += (2 * st["power_iters"] + 2 * st["iters"] + 1) * float(w.n_vis) * w.n_pix
+        img, st = Q.solve(lam, L=L, max_iter=args.iters, precision=prec)
         Q.close()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    ctx.profile_enable(False)
+    pairs = sum(ctx.profile_read(k)["pairs"] for k in ("fwd_fp64", "adj_fp64", "fwd_mixed", "adj_mixed"))
     dt, pairs = job_totals(dt, pairs, ws, f"cuda:{torch.cuda.current_device()}")
     c = ctx.counters()
     return {"value": pairs / dt, "unit": "pairs/s", "steps": steps,
             "h2d_bytes_per_step": c["h2d_bytes"] // steps, "d2h_bytes_per_step": c["d2h_bytes"] // steps,
-            "ms_per_step": 1e3 * dt / steps}
+            "ms_per_step": 1e3 * dt / steps,
+            "timed": "host wall clock around every step (layout, H2D, solve, image D2H), "
+                     "device synchronised on both sides"}
 
 
 if __name__ == "__main__":

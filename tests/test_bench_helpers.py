@@ -121,6 +121,8 @@ def test_reference_arm_under_torchrun_prints_one_line_from_rank_0():
     out = json.loads(lines[0])
     assert out["impl"] == "reference" and out["n_gpus"] == 2 and out["value"] > 0
     assert out["cpu_baseline"]["kind"] == "oracle" and out["e2e"]["h2d_bytes_per_step"] == 0
+    args = bench.parse(["--gpus", "2"])
+    assert out["config"] == bench.bench_config(args, bench.workload(args.config))
 
 
 def test_cpu_baseline_leg_times_the_oracle_and_measures_the_error():
@@ -154,28 +156,61 @@ def test_clock_sampler_names_the_gpu_as_nvidia_smi_does(monkeypatch):
 
 
 def test_oracle_stream_estimate_scales_the_sampled_rate_to_the_stream():
+    """The serving line's oracle estimate: the samples' total pairs over their
+    total time (not a mean of rates of requests of very different sizes),
+    applied to the whole stream; the samples run single-threaded only."""
     from paper_1310_2078_gb300 import synth
     reqs = [synth.config1(scale=0.25), synth.config1(scale=0.5), synth.config1(scale=0.25)]
     stream_pairs = 1e9
     est = bench.oracle_stream_estimate(reqs, [0, 1], stream_pairs, budget_s=0.1)
     assert est["kind"] == "oracle" and est["cores"] == 1 and est["unit"] == "solves/s"
     assert [s["request"] for s in est["samples"]] == [0, 1]
-    assert all(s["threaded"]["bitwise_identical_to_single_thread"] for s in est["samples"])
-    rate = np.mean([s["value"] for s in est["samples"]])
+    assert all("threaded" not in s for s in est["samples"])
+    rate = sum(s["pairs"] for s in est["samples"]) / sum(s["seconds"] for s in est["samples"])
     assert est["pairs_per_s"] == pytest.approx(rate)
     assert est["est_wall_s"] == pytest.approx(stream_pairs / rate)
     assert est["value"] == pytest.approx(3 / (stream_pairs / rate))
 
 
-def test_default_workload_matches_the_profiles_and_ranks_share_its_shape():
-    """The bench's default workload is the one the committed ncu traffic lines
-    name; under several ranks each rank solves the same geometry with its own
+def test_default_workload_is_paper_scale_and_ranks_share_its_shape():
+    """The bench's default workload is the paper-scale one (1024^2 Dirac
+    pixels x 406,400 visibilities) with a step of 5 FISTA steps at a fixed L;
+    under several ranks each rank solves the same geometry with its own
     noise (weak scaling)."""
-    w = bench.workload(2)
-    assert w.name == "wide-field-dirac-256x256-40320vis" and (w.n_pix, w.n_vis) == (65536, 40320)
-    prof = open(os.path.join(ROOT, "profiles", "launch_list_wide_field_dirac_256x256_40320vis.md")).read()
-    assert f"workload={w.name}" in prof
-    w1 = bench.workload(2, rank=1)
+    args = bench.parse([])
+    assert args.config == 4 and args.iters == 5 and not args.full_solve
+    assert bench.parse(["--full-solve"]).iters == 200
+    w = bench.workload(args.config)
+    assert w.name == "paper-scale-dirac-1024x1024-406400vis" and (w.n_pix, w.n_vis) == (1048576, 406400)
+    w1 = bench.workload(args.config, rank=1)
     assert (w1.n_pix, w1.n_vis) == (w.n_pix, w.n_vis)
     np.testing.assert_array_equal(w1.uvw, w.uvw)
     assert not np.array_equal(w1.noise, w.noise)
+
+
+def test_both_arms_print_the_same_config():
+    """The reference arm's `config` is the one the GPU arm prints."""
+    args = bench.parse(["--gpus", "2"])
+    w = bench.workload(args.config)
+    c = bench.bench_config(args, w)
+    assert c["workload"] == w.name and c["parallelism"] == "replicas2"
+    assert "5 FISTA steps at a fixed L" in c["step"] and c["precision"] == "mixed"
+    assert bench.bench_config(bench.parse(["--ops-only"]), w)["step"].startswith("one forward")
+
+
+def test_measured_sfu_peak_weighs_the_pixel_kinds():
+    """With the measured rates at the table's 16 per clock per SM, the
+    measured bound equals the table bound for Dirac and for a Dirac/Gaussian
+    mix (exp2 at the same rate)."""
+    class W:
+        def __init__(self, kind):
+            self.kind = kind
+            self.n_pix = 4 if kind is None else len(kind)
+    r = 16 * bench.N_SM * bench.SM_MAX_MHZ * 1e6
+    sfu = {"sincos_per_s": r, "ex2_per_s": r}
+    for kinds in (None, np.array([0, 2, 2, 2])):
+        m = bench.sfu_peak_measured(W(kinds), sfu)
+        assert m["peak"] == pytest.approx(bench.sfu_peak(W(kinds))[0])
+        assert m["per_clk_per_sm_at_max_clock"]["sincos_per_s"] == pytest.approx(16.0)
+    m = bench.sfu_peak_measured(W(None), {"sincos_per_s": r / 2, "ex2_per_s": r})
+    assert m["peak"] == pytest.approx(bench.sfu_peak(W(None))[0] / 2)
