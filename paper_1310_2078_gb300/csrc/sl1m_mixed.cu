@@ -828,6 +828,124 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
     if (fault) atomicOr(&g_wait_fault, 1u);
 }
 
+// ---- adjoint tiles with gains
+// A streamed visibility granule's members are sorted by antenna pair, so for
+// an owned pixel j each pair s = (a, b) is one run of visibilities k.  Their
+// contribution is  Re( conj(g_js) e^{2 pi i C} sum_{k in s} e^{i theta_jk} r_k )
+// with g_js = G_ja conj(G_jb), C the tile's centre term and theta = 2 pi (B + D)
+// (+ the Gaussian terms): the run is summed as a complex number z, and at the
+// run's end acc += Re(w z) with w = conj(g) e^{2 pi i C} formed once per run.
+// Per record k: off = {du, dv, dw, B in radians}, rk = {r (or the Gaussian
+// r' = id (1 - i beta) r), pair key a << 16 | b, 0}; Gaussian owners also read
+// va = {u, v, -2 w, gam in radians} and kk = {k1, k0}, the amplitude being
+// 2^(k1 t + k0) with t = u l + v m - w r^2/2.
+
+// Add the run held in (zr, zi) with weight w into acc: acc += Re(w z).
+__device__ __forceinline__ void adjg_flush(const float2 (&w)[2], float (&zr)[2], float (&zi)[2], float (&acc)[2])
+{
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        acc[r] = fmaf(w[r].x, zr[r], fmaf(-w[r].y, zi[r], acc[r]));
+        zr[r] = 0.f;
+        zi[r] = 0.f;
+    }
+}
+
+// At a new pair `key` (antenna indices a = key >> 16, b = key & 0xffff, both
+// valid): flush the run so far, then w = conj(G_ja conj(G_jb)) (cC + i sC) for
+// the lane's two pixels.
+template <class GF>
+__device__ __forceinline__ void adjg_next_run(int key, int& cur, const GF& gain, const float (&cC)[2],
+                                              const float (&sC)[2], float2 (&w)[2], float (&zr)[2],
+                                              float (&zi)[2], float (&acc)[2])
+{
+    if (key == cur) return;                       // warp-uniform: every lane has the same k
+    adjg_flush(w, zr, zi, acc);
+    cur = key;
+    const int a = key >> 16, b = key & 0xffff;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const float2 ga = gain(a, r), gb = gain(b, r);
+        const float gr = fmaf(ga.x, gb.x, ga.y * gb.y), gi = fmaf(ga.y, gb.x, -ga.x * gb.y);   // G_a conj(G_b)
+        w[r] = make_float2(fmaf(gr, cC[r], gi * sC[r]), fmaf(gr, sC[r], -gi * cC[r]));         // conj(g) e^{iC}
+    }
+}
+
+template <bool EXACT, class GF>
+__device__ __forceinline__ void adjg_dirac_tile(const float4* __restrict__ s_off, const float4* __restrict__ g_lo,
+                                                const float4* __restrict__ s_rk, const GF& gain,
+                                                const float (&cC)[2], const float (&sC)[2],
+                                                const float4 (&dx)[2], const float4 (&dxl)[2], float (&acc)[2])
+{
+    int cur = -1;
+    float2 w[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    float zr[2] = {0.f, 0.f}, zi[2] = {0.f, 0.f};
+#pragma unroll 1
+    for (int k0 = 0; k0 < G; k0 += 4)
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const int k = k0 + kk;
+        const float4 o = s_off[k];
+        const float4 rk = s_rk[k];
+        adjg_next_run(__float_as_int(rk.z), cur, gain, cC, sC, w, zr, zi, acc);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            float ph;                              // radians
+            if (EXACT) ph = frac_turns(o.w * INV_TWO_PI_F + frac_dot3(dx[r], dxl[r], o, g_lo[k])) * TWO_PI_F;
+            else ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, o.w)));
+            float sn, cs;
+            __sincosf(ph, &sn, &cs);               // e^{i ph} = cs + i sn
+            zr[r] = fmaf(cs, rk.x, fmaf(-sn, rk.y, zr[r]));
+            zi[r] = fmaf(cs, rk.y, fmaf(sn, rk.x, zi[r]));
+        }
+    }
+    adjg_flush(w, zr, zi, acc);                 // the last run
+}
+
+template <bool EXACT, bool PAR, class GF>
+__device__ __forceinline__ void adjg_gauss_tile(const float4* __restrict__ s_off, const float4* __restrict__ g_lo,
+                                                const float4* __restrict__ s_va, const float2* __restrict__ s_kk,
+                                                const float4* __restrict__ s_rk, const GF& gain,
+                                                const float (&cC)[2], const float (&sC)[2],
+                                                const float4 (&dx)[2], const float4 (&dxl)[2],
+                                                const float4 (&pgd)[2], float (&acc)[2])
+{
+    int cur = -1;
+    float2 w[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    float zr[2] = {0.f, 0.f}, zi[2] = {0.f, 0.f};
+#pragma unroll 2
+    for (int k = 0; k < G; ++k) {
+        const float4 o = s_off[k];
+        const float4 va = s_va[k];                 // {u, v, -2 w, gam (radians)}
+        const float2 ka = s_kk[k];                 // {k1, k0}
+        const float4 rk = s_rk[k];                 // {r', key, 0}
+        adjg_next_run(__float_as_int(rk.z), cur, gain, cC, sC, w, zr, zi, acc);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            // pgd = {l, m, r^2/4, pi nu}: t = u l + v m - w r^2/2
+            const float t = fmaf(va.x, pgd[r].x, fmaf(va.y, pgd[r].y, va.z * pgd[r].z));
+            float ph;                              // radians
+            if (EXACT) {
+                ph = o.w * INV_TWO_PI_F + frac_dot3(dx[r], dxl[r], o, g_lo[k]);
+                ph = fmaf(-va.w * INV_TWO_PI_F, t, ph);
+                if (PAR) ph = fmaf(va.z, pgd[r].w * INV_TWO_PI_F, ph);   // -w nu, turns
+                ph = frac_turns(ph) * TWO_PI_F;
+            } else {
+                ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, o.w)));
+                ph = fmaf(-va.w, t, ph);
+                if (PAR) ph = fmaf(va.z, pgd[r].w, ph);                  // -2 pi w nu
+            }
+            float sn, cs;
+            __sincosf(ph, &sn, &cs);
+            const float amp = ex2_approx(fmaf(ka.x, t, ka.y));        // e^{Re(qc)}
+            const float ca = amp * cs, sa = amp * sn;
+            zr[r] = fmaf(ca, rk.x, fmaf(-sa, rk.y, zr[r]));
+            zi[r] = fmaf(ca, rk.y, fmaf(sa, rk.x, zi[r]));
+        }
+    }
+    adjg_flush(w, zr, zi, acc);                 // the last run
+}
+
 // Adjoint with gains.  The CTA's 8 warps share one owned pixel granule at a
 // time -- its gains for all antennas in shared memory as [antenna][pixel], so
 // a lane's loads never conflict -- and split the streamed visibility granules
@@ -866,11 +984,10 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
                        double* __restrict__ partial)
 {
     // per warp, what its tiles read for its current granule
-    __shared__ float4 s_off[BLK_GRAN][G];       // {du, dv, dw, pair key}
-    __shared__ float4 s_abs[BLK_GRAN][G];       // {u, v, -2 w, u^2 + v^2}
-    __shared__ float2 s_r[BLK_GRAN][G];
-    __shared__ float s_B[BLK_GRAN][G];
-    __shared__ float4 s_gw[BLK_GRAN][G];        // Gaussian owners: {gamr, coef, r're, r'im}
+    __shared__ float4 s_off[BLK_GRAN][G];       // {du, dv, dw, B (radians)}
+    __shared__ float4 s_rk[BLK_GRAN][G];        // {r (Gaussian owners: r'), pair key, 0}
+    __shared__ float4 s_va[BLK_GRAN][G];        // Gaussian owners: {u, v, -2 w, gam (radians)}
+    __shared__ float2 s_kk[BLK_GRAN][G];        // Gaussian owners: {k1, k0}
     __shared__ double s_red[BLK_GRAN][G];
     __shared__ __align__(8) unsigned long long s_wbar[BLK_GRAN];   // each warp's raw slice
     __shared__ __align__(8) unsigned long long s_gbar;             // the gains table
@@ -954,49 +1071,49 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
                     const int k = lane + 32 * h;
                     float4 o = raw_off[k];
                     const int2 ab = raw_ant[k];
-                    o.w = __int_as_float(ab.x << 16 | ab.y);   // the pair key (pair_gains)
+                    const float key = __int_as_float(ab.x << 16 | ab.y);   // the pair (adjg_next_run)
                     float b = frac_dot3(ch, cl, o, raw_lo[k]);
-                    const float4 va = vis_for_gauss(raw_hi[k]);
                     const double2 rd = raw_r[k];
-                    const float2 rr = make_float2((float)rd.x, (float)rd.y);
+                    float2 rr = make_float2((float)rd.x, (float)rd.y);
                     if (gauss) {
+                        const float4 va = vis_for_gauss(raw_hi[k]);
                         const GaussConst gc = gauss_const(va.x, va.y, -0.5f * va.z, sigma);
                         b = frac_turns(b + gc.cphase);
-                        s_gw[warp][k] = make_float4(gc.gamr, gc.coef, gc.id * fmaf(gc.beta, rr.y, rr.x),
-                                                    gc.id * fmaf(-gc.beta, rr.x, rr.y));
+                        rr = make_float2(gc.id * fmaf(gc.beta, rr.y, rr.x), gc.id * fmaf(-gc.beta, rr.x, rr.y));
+                        s_va[warp][k] = make_float4(va.x, va.y, va.z, gc.gamr);
+                        s_kk[warp][k] = make_float2(gc.k1, gc.k0);
                     }
+                    o.w = b * TWO_PI_F;                       // radians
                     s_off[warp][k] = o;
-                    s_abs[warp][k] = va;
-                    s_r[warp][k] = rr;
-                    s_B[warp][k] = b * TWO_PI_F;              // radians
+                    s_rk[warp][k] = make_float4(rr.x, rr.y, key, 0.f);
                 }
                 const float4 yc_h = raw_cen[0], yc_l = raw_cen[1], yext = raw_cen[2];
                 __syncwarp();                                 // the slice is read: refill it
                 if (lane == 0 && g + BLK_GRAN < g1) adj_raw_load(raw, P, R, g + BLK_GRAN, &s_wbar[warp]);
                 const bool exact = dot3(ext, yext) > D_MAX;
-                float C[2];
+                float cC[2], sC[2];                   // e^{2 pi i C}, C the tile's centre term
 #pragma unroll
-                for (int r = 0; r < 2; ++r) C[r] = frac_dot3(xh[r], P.pix.lo[eidx[r]], yc_h, yc_l);
-                const float Cr[2] = {C[0] * TWO_PI_F, C[1] * TWO_PI_F};
+                for (int r = 0; r < 2; ++r)
+                    __sincosf(frac_dot3(xh[r], P.pix.lo[eidx[r]], yc_h, yc_l) * TWO_PI_F, &sC[r], &cC[r]);
                 const float4* g_lo = P.vis.offlo + (size_t)g * G;   // exact tiles only (rare)
                 float acc[2] = {0.f, 0.f};
                 if (!gauss) {
                     if (exact) {
                         const float4 dxt[2] = {P.pix.off[eidx[0]], P.pix.off[eidx[1]]},
                                  dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
-                        adj_dirac_tile<true, true>(s_off[warp], g_lo, s_r[warp], s_B[warp], sg, C, dxt, dxl, acc);
+                        adjg_dirac_tile<true>(s_off[warp], g_lo, s_rk[warp], sg, cC, sC, dxt, dxl, acc);
                     } else {
-                        adj_dirac_tile<true, false>(s_off[warp], g_lo, s_r[warp], s_B[warp], sg, Cr, dx, dx, acc);
+                        adjg_dirac_tile<false>(s_off[warp], g_lo, s_rk[warp], sg, cC, sC, dx, dx, acc);
                     }
                 } else {
                     if (exact) {
                         const float4 dxt[2] = {P.pix.off[eidx[0]], P.pix.off[eidx[1]]},
                                  dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
-                        if (par) adj_gauss_tile<true, true, true>(s_off[warp], g_lo, s_abs[warp], s_B[warp], s_gw[warp], sg, C, dxt, dxl, pgd, acc);
-                        else adj_gauss_tile<true, true, false>(s_off[warp], g_lo, s_abs[warp], s_B[warp], s_gw[warp], sg, C, dxt, dxl, pgd, acc);
+                        if (par) adjg_gauss_tile<true, true>(s_off[warp], g_lo, s_va[warp], s_kk[warp], s_rk[warp], sg, cC, sC, dxt, dxl, pgd, acc);
+                        else adjg_gauss_tile<true, false>(s_off[warp], g_lo, s_va[warp], s_kk[warp], s_rk[warp], sg, cC, sC, dxt, dxl, pgd, acc);
                     } else {
-                        if (par) adj_gauss_tile<true, false, true>(s_off[warp], g_lo, s_abs[warp], s_B[warp], s_gw[warp], sg, Cr, dx, dx, pgd, acc);
-                        else adj_gauss_tile<true, false, false>(s_off[warp], g_lo, s_abs[warp], s_B[warp], s_gw[warp], sg, Cr, dx, dx, pgd, acc);
+                        if (par) adjg_gauss_tile<false, true>(s_off[warp], g_lo, s_va[warp], s_kk[warp], s_rk[warp], sg, cC, sC, dx, dx, pgd, acc);
+                        else adjg_gauss_tile<false, false>(s_off[warp], g_lo, s_va[warp], s_kk[warp], s_rk[warp], sg, cC, sC, dx, dx, pgd, acc);
                     }
                 }
 #pragma unroll

@@ -74,3 +74,32 @@ def test_gains_multiscale_reduced_50_steps(ctx):
     assert (w.n_pix, w.n_vis) == (4096, 8000) and w.gains is not None
     assert set(np.unique(w.kind)) == {0, 2}
     _solve_both(ctx, w, 50)
+
+
+@pytest.mark.parametrize("kinds", [(0,), (1, 2), (0, 1, 2)])
+def test_gains_operator_parity_with_exact_tiles(ctx, kinds):
+    """Long baselines over a wide field, with gains: a share of the tiles takes
+    the exact phase path in the gains kernels; forward and adjoint still
+    match the oracle to 1e-5 (normwise-max) for every pixel kind."""
+    d = synth.random_problem(61, 3000, 2000, kinds=kinds, gains=True, n_ant=24, uv_max=3000,
+                             w_max=600, extent=0.5)
+    # three Gaussian scales, so that each (kind, sigma) class fills whole granules
+    gauss = d["kind"] != 0
+    d["sigma"] = np.where(gauss, np.random.default_rng(63).choice([1e-4, 2e-4, 4e-4], 2000), 0.0)
+    O = oracle.Problem(d["uvw"], d["lm"], d["sigma"], d["kind"], None, d["ant_pair"], d["gains"],
+                       threads=THREADS)
+    P = ctx.problem()
+    P.set_visibilities(d["uvw"], None, None, d["ant_pair"])
+    P.set_pixels(d["lm"], d["sigma"], d["kind"])
+    P.set_gains(d["gains"])
+    rng = np.random.default_rng(62)
+    x = np.abs(rng.normal(size=2000))
+    f = P.forward(x, 1)
+    share, _ = P.exact_tile_share()
+    assert share > 0.05
+    fo = oracle.forward(O, x)
+    assert np.max(np.abs(f - fo)) / np.max(np.abs(fo)) <= 1e-5
+    r = rng.normal(size=3000) + 1j * rng.normal(size=3000)
+    ao = oracle.adjoint(O, r)
+    assert np.max(np.abs(P.adjoint(r, 1) - ao)) / np.max(np.abs(ao)) <= 1e-5
+    P.close()
