@@ -236,16 +236,29 @@ int sl1m_solve(sl1m_problem* prob, const sl1m_solve_opts* opts, double* img_out,
  * finished solves between rounds.  A request that arrives while others run
  * joins the next round.  While a server runs on a context, the operator and
  * solve calls of that context return SL1M_ERR_BUSY. */
+#define SL1M_ADMIT_TWO_LANES 0   /* default: small and large requests in lanes  */
+#define SL1M_ADMIT_ARRIVAL 1     /* one queue, strictly in arrival order         */
 typedef struct {
     int64_t mem_budget_bytes;   /* 0 = 80% of the device memory free at start   */
     int32_t max_slots;          /* 0 = 64 concurrent solves                      */
     int32_t ticks_per_round;    /* 0 = 4 steps between admission/retirement     */
     int32_t precision;          /* SL1M_MIXED or SL1M_FP64 for every request     */
-    int32_t reserved;
-    double max_pairs_per_tick;  /* work in flight: admit (in arrival order) while
-                                   the summed n_vis*n_pix of running solves stays
-                                   below this; 0 = 4e9 (enough to fill the GPU);
-                                   one request is always admitted              */
+    int32_t admission;          /* SL1M_ADMIT_TWO_LANES or SL1M_ADMIT_ARRIVAL    */
+    double max_pairs_per_tick;  /* work in flight: admit while the summed
+                                   n_vis*n_pix of running solves stays below
+                                   this; 0 = 4e9 (enough to fill the GPU).
+                                   SL1M_ADMIT_ARRIVAL: in arrival order, one
+                                   request always admitted when none runs.
+                                   SL1M_ADMIT_TWO_LANES: requests of at most
+                                   scale/16 pairs ("small") and the rest
+                                   ("large") queue in arrival order in lanes of
+                                   their own; large ones against this budget
+                                   (one always admitted when no large one
+                                   runs), small ones against scale/4 on top,
+                                   where scale is this budget or the pairs of
+                                   the largest running request if that is
+                                   more; a small request never waits behind a
+                                   large one that does not fit               */
 } sl1m_server_opts;
 
 /* Start the request loop (opts may be NULL for defaults). */

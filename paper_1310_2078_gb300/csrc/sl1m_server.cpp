@@ -60,6 +60,7 @@ struct Server {
     uint64_t next_ticket = 1;
     size_t budget = 0, in_use = 0;
     int max_slots = 64, ticks_per_round = 4, precision = SL1M_MIXED;
+    int admission = SL1M_ADMIT_TWO_LANES;
     double max_pairs = 4e9;
     bool stop = false, running = false;
     long long finished = 0, max_active = 0, ticks = 0, rounds = 0;
@@ -98,6 +99,88 @@ static void retire(Server& S, Request* r, int status)
     S.cv_done.notify_all();
 }
 
+// Admission by memory (wait for running solves to free theirs) and by work in
+// flight (N_v N_p summed over running solves: enough to fill the GPU, no
+// more, since every running solve adds its pairs to every tick).
+
+// SL1M_ADMIT_ARRIVAL: strictly in arrival order; the first request that does
+// not fit stops admission (one request is always admitted when none runs).
+static void admit_in_arrival_order(Server& S, std::vector<Request*>& admit)
+{
+    double work = 0.0;
+    for (Request* r : S.active) work += r->prob->pairs();
+    while (!S.pending.empty() && (int)(S.active.size() + admit.size()) < S.max_slots) {
+        Request* r = S.pending.front();
+        const size_t need = r->prob->estimate_bytes();
+        const bool first = S.active.empty() && admit.empty();
+        if (S.in_use + need > S.budget && !first) break;
+        if (work + r->prob->pairs() > S.max_pairs && !first) break;
+        work += r->prob->pairs();
+        S.pending.pop_front();
+        r->bytes = need;
+        S.in_use += need;
+        admit.push_back(r);
+    }
+}
+
+// SL1M_ADMIT_TWO_LANES: requests of at most scale / 16 pairs ("small") and
+// the others ("large") are admitted in arrival order within their lane, each
+// lane against its own work budget: large ones against max_pairs (one large
+// request is always admitted when no large one runs), small ones against
+// scale / 4 more.  scale is max_pairs, or the pairs of the largest running
+// request when one alone exceeds max_pairs: such a request fills the GPU by
+// itself for a long time, and a request of a sixteenth of its size shares
+// its ticks instead of waiting for it to end.  A small request never waits
+// behind a large one that does not fit, and a large one never waits for small
+// ones to drain; small ones add at most a quarter to a tick's work.
+static void admit_two_lanes(Server& S, std::vector<Request*>& admit)
+{
+    double scale = S.max_pairs;
+    for (Request* r : S.active) scale = std::max(scale, r->prob->pairs());
+    const double small_max = scale / 16.0, small_budget = scale / 4.0;
+    double work_large = 0.0, work_small = 0.0;
+    bool any_large = false;
+    for (Request* r : S.active) {
+        const double w = r->prob->pairs();
+        if (w <= small_max) work_small += w;
+        else {
+            work_large += w;
+            any_large = true;
+        }
+    }
+    bool large_blocked = false, small_blocked = false;
+    for (auto it = S.pending.begin(); it != S.pending.end() && !(large_blocked && small_blocked);) {
+        if ((int)(S.active.size() + admit.size()) >= S.max_slots) break;
+        Request* r = *it;
+        const double w = r->prob->pairs();
+        const bool small = w <= small_max;
+        if (small ? small_blocked : large_blocked) {
+            ++it;
+            continue;
+        }
+        const size_t need = r->prob->estimate_bytes();
+        const bool first = S.active.empty() && admit.empty();
+        const bool mem_ok = S.in_use + need <= S.budget || first;
+        const bool work_ok = small ? (work_small + w <= small_budget || first)
+                                   : (work_large + w <= S.max_pairs || !any_large);
+        if (!mem_ok && !small) break;            // memory for the oldest large one first
+        if (!mem_ok || !work_ok) {               // keep arrival order within the lane
+            (small ? small_blocked : large_blocked) = true;
+            ++it;
+            continue;
+        }
+        if (small) work_small += w;
+        else {
+            work_large += w;
+            any_large = true;
+        }
+        it = S.pending.erase(it);
+        r->bytes = need;
+        S.in_use += need;
+        admit.push_back(r);
+    }
+}
+
 static void server_loop(Server* Sp)
 {
     Server& S = *Sp;
@@ -110,22 +193,8 @@ static void server_loop(Server* Sp)
             std::unique_lock<std::mutex> lk(S.mu);
             while (!S.stop && S.pending.empty() && S.active.empty()) S.cv_work.wait(lk);
             if (S.stop && S.pending.empty() && S.active.empty()) break;
-            double work = 0.0;
-            for (Request* r : S.active) work += r->prob->pairs();
-            while (!S.pending.empty() && (int)(S.active.size() + admit.size()) < S.max_slots) {
-                Request* r = S.pending.front();
-                const size_t need = r->prob->estimate_bytes();
-                const bool first = S.active.empty() && admit.empty();
-                // admission by memory: wait for running solves to free theirs
-                if (S.in_use + need > S.budget && !first) break;
-                // admission by work in flight: enough to fill the GPU, no more
-                if (work + r->prob->pairs() > S.max_pairs && !first) break;
-                work += r->prob->pairs();
-                S.pending.pop_front();
-                r->bytes = need;
-                S.in_use += need;
-                admit.push_back(r);
-            }
+            if (S.admission == SL1M_ADMIT_ARRIVAL) admit_in_arrival_order(S, admit);
+            else admit_two_lanes(S, admit);
         }
         // ticks of the running solves (asynchronous) ...
         if (!S.active.empty()) {
@@ -233,6 +302,11 @@ int sl1m_server_start(sl1m_ctx* ctx, const sl1m_server_opts* opts)
     S->max_slots = std::min(S->max_slots, MAX_PROBS);
     S->ticks_per_round = (opts && opts->ticks_per_round > 0) ? opts->ticks_per_round : 4;
     S->max_pairs = (opts && opts->max_pairs_per_tick > 0) ? opts->max_pairs_per_tick : 4e9;
+    S->admission = opts ? opts->admission : SL1M_ADMIT_TWO_LANES;
+    if (S->admission != SL1M_ADMIT_TWO_LANES && S->admission != SL1M_ADMIT_ARRIVAL) {
+        delete S;
+        return sl1m_fail(ctx, SL1M_ERR_ARG, "bad admission policy");
+    }
     S->precision = opts ? opts->precision : SL1M_MIXED;
     if (S->precision != SL1M_MIXED && S->precision != SL1M_FP64) {
         delete S;

@@ -25,6 +25,7 @@ FP64, MIXED = 0, 1
 FISTA, MFISTA = 0, 1
 _ALGOS = {"fista": FISTA, "mfista": MFISTA, FISTA: FISTA, MFISTA: MFISTA}
 DIRAC, GAUSS_PARAXIAL, GAUSS_WIDE = 0, 1, 2
+ADMIT_TWO_LANES, ADMIT_ARRIVAL = 0, 1
 KERNEL_IDS = {"fwd_fp64": 0, "adj_fp64": 1, "fwd_mixed": 2, "adj_mixed": 3,
               "fwd_finish": 4, "adj_finish": 5, "other": 6}
 
@@ -51,7 +52,7 @@ class SolveOpts(C.Structure):
 
 class ServerOpts(C.Structure):
     _fields_ = [("mem_budget_bytes", C.c_int64), ("max_slots", C.c_int32),
-                ("ticks_per_round", C.c_int32), ("precision", C.c_int32), ("reserved", C.c_int32),
+                ("ticks_per_round", C.c_int32), ("precision", C.c_int32), ("admission", C.c_int32),
                 ("max_pairs_per_tick", C.c_double)]
 
 
@@ -307,9 +308,9 @@ class Context:
 
     # ---- continuous-batching server (sl1m_server_*)
     def server_start(self, mem_budget_bytes=0, max_slots=0, ticks_per_round=0, precision=MIXED,
-                     max_pairs_per_tick=0.0):
-        o = ServerOpts(int(mem_budget_bytes), int(max_slots), int(ticks_per_round), int(precision), 0,
-                       float(max_pairs_per_tick))
+                     max_pairs_per_tick=0.0, admission=ADMIT_TWO_LANES):
+        o = ServerOpts(int(mem_budget_bytes), int(max_slots), int(ticks_per_round), int(precision),
+                       int(admission), float(max_pairs_per_tick))
         self.check(self.lib.sl1m_server_start(self.h, C.byref(o)))
 
     def server_submit(self, problem, lam, L=0.0, max_iter=200, rel_tol=0.0, x0=None,

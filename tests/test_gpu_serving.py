@@ -161,3 +161,37 @@ def test_stop_drains_queue(gpu_lib, reqs):
     img, st = probs[0].solve(reqs[0]["lam"], L=reqs[0]["L"], max_iter=5)
     assert st["iters"] == 5
     ctx.close()
+
+
+@pytest.mark.parametrize("admission", ["two_lanes", "arrival"])
+def test_small_request_passes_a_large_one_that_waits(gpu_lib, admission):
+    """Admission lanes.  Under a work budget that one large request fills, a
+    second large request waits for the first; a small request submitted after
+    both is admitted at once under the two-lane policy (it finishes while the
+    first large one still runs), but under arrival-order admission it waits
+    behind the second large one (the first has finished by then).  Either
+    way its image is the one it gets alone."""
+    mode = gpu_lib.ADMIT_TWO_LANES if admission == "two_lanes" else gpu_lib.ADMIT_ARRIVAL
+    ctx = gpu_lib.Context(0)
+    rng = np.random.default_rng(7)
+    probs, lams = [], []
+    for i, (nv, npx) in enumerate([(4000, 3000), (4000, 3000), (300, 200)]):
+        d = synth.random_problem(3000 + i, nv, npx, uv_max=150, w_max=40, extent=0.15)
+        x = np.zeros(npx)
+        x[rng.choice(npx, 5, replace=False)] = 1.0
+        V = oracle.forward(oracle.Problem(d["uvw"], d["lm"]), x)
+        probs.append(build(ctx, d, V))
+        lams.append(0.05 * np.abs(V).max())
+    # L above each problem's ||A||_F^2 (>= its largest eigenvalue): a valid FISTA step
+    alone, _ = probs[2].solve(lams[2], L=1e5, max_iter=20)
+    ctx.server_start(max_slots=8, ticks_per_round=4, max_pairs_per_tick=1.3e7, admission=mode)
+    big = [ctx.server_submit(probs[i], lams[i], L=2e7, max_iter=400) for i in range(2)]
+    small = ctx.server_submit(probs[2], lams[2], L=1e5, max_iter=20)
+    img, st = ctx.server_wait(small, probs[2], timeout_s=120.0)
+    first_large_done = ctx.server_poll(big[0])
+    assert first_large_done == (admission == "arrival")
+    assert np.max(np.abs(img - alone)) <= 1e-4 * max(alone.max(), 1e-30)
+    for i, t in enumerate(big):
+        ctx.server_wait(t, probs[i], timeout_s=120.0)
+    ctx.server_stop()
+    ctx.close()
