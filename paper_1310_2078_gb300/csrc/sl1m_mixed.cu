@@ -179,6 +179,7 @@ __device__ __forceinline__ void fwd_dirac_tile_pt(const float4* __restrict__ s_o
                                                   const float4 (&dx)[2], const float4 (&dxl)[2], int lane,
                                                   float (&sr)[2], float (&si)[2])
 {
+    float sr2[2] = {0.f, 0.f}, si2[2] = {0.f, 0.f};   // second accumulators: one FFMA deep each
 #pragma unroll 1
     for (int c0 = 0; c0 < G; c0 += BT_CH) {
         build_pair_table(T, bl, nb, sBa, gtab, c0, lane);
@@ -197,11 +198,18 @@ __device__ __forceinline__ void fwd_dirac_tile_pt(const float4* __restrict__ s_o
                 float sn, cs;
                 __sincosf(ph, &sn, &cs);
                 const float2 t = T[toff[r] + jj];                      // a g
-                sr[r] = fmaf(t.x, cs, fmaf(t.y, sn, sr[r]));          // a g (cs - i sn)
-                si[r] = fmaf(t.y, cs, fmaf(-t.x, sn, si[r]));
+                sr[r] = fmaf(t.x, cs, sr[r]);
+                sr2[r] = fmaf(t.y, sn, sr2[r]);
+                si[r] = fmaf(t.y, cs, si[r]);
+                si2[r] = fmaf(-t.x, sn, si2[r]);
             }
         }
         __syncwarp();                                                  // table free for the next chunk
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        sr[r] += sr2[r];
+        si[r] += si2[r];
     }
 }
 
@@ -216,6 +224,7 @@ __device__ __forceinline__ void fwd_gauss_tile_pt(const float4* __restrict__ s_o
                                                   const float4 (&dxl)[2], const GaussConst (&gc)[2], int lane,
                                                   float (&sr)[2], float (&si)[2])
 {
+    float sr2[2] = {0.f, 0.f}, si2[2] = {0.f, 0.f};   // second accumulators: one FFMA deep each
 #pragma unroll 1
     for (int c0 = 0; c0 < G; c0 += BT_CH) {
         build_pair_table(T, bl, nb, sBa, gtab, c0, lane);
@@ -247,11 +256,18 @@ __device__ __forceinline__ void fwd_gauss_tile_pt(const float4* __restrict__ s_o
                 const float amp = ex2_approx(fmaf(gc[r].k1, t, gc[r].k0));   // e^{Re(qc)}; a is in T
                 const float2 tv = T[toff[r] + jj];
                 const float ca = amp * cs, sa = amp * sn;
-                sr[r] = fmaf(tv.x, ca, fmaf(tv.y, sa, sr[r]));
-                si[r] = fmaf(tv.y, ca, fmaf(-tv.x, sa, si[r]));
+                sr[r] = fmaf(tv.x, ca, sr[r]);
+                sr2[r] = fmaf(tv.y, sa, sr2[r]);
+                si[r] = fmaf(tv.y, ca, si[r]);
+                si2[r] = fmaf(-tv.x, sa, si2[r]);
             }
         }
         __syncwarp();
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        sr[r] += sr2[r];
+        si[r] += si2[r];
     }
 }
 
