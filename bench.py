@@ -82,6 +82,8 @@ def parse(argv=None):
     ap.add_argument("--fp64-sample", type=int, default=3)
     ap.add_argument("--ticks", type=int, default=4, help="serving: ticks per round")
     ap.add_argument("--max-pairs", type=float, default=4e9, help="serving: work in flight per tick")
+    ap.add_argument("--admission", default="two_lanes", choices=["two_lanes", "arrival"],
+                    help="serving: admission policy of the server")
     args = ap.parse_args(argv)
     if not args.iters:
         args.iters = 200 if args.full_solve else 5
@@ -136,7 +138,7 @@ def job_totals(seconds: float, units: float, ws: int, device="cpu"):
 def workload(cfg: int, rank: int = 0, small: bool = False, args=None):
     from paper_1310_2078_gb300 import synth
     kw = {}
-    if args is not None and cfg in (2, 4):
+    if args is not None and cfg in (2, 3, 4):
         for k in ("n_side", "n_ant", "n_times"):
             if getattr(args, k, 0):
                 kw[k] = getattr(args, k)
@@ -450,7 +452,8 @@ def run_reference(args):
     print(json.dumps(out))
 
 
-def serving_measure(n_requests, rate, ticks=4, max_pairs=4e9, fp64_sample=3, with_cpu=True, dev=0):
+def serving_measure(n_requests, rate, ticks=4, max_pairs=4e9, fp64_sample=3, with_cpu=True, dev=0,
+                    admission="two_lanes"):
     """Continuous batching: `n_requests` independent solves arriving as a
     Poisson stream (`rate` per second), each an independently generated
     array/sky with 4k-256k pixels and 2k-100k visibilities, Dirac or wide
@@ -477,7 +480,8 @@ def serving_measure(n_requests, rate, ticks=4, max_pairs=4e9, fp64_sample=3, wit
         probs.append((P, V))
     torch.cuda.synchronize()
     ctx.counters_reset()
-    ctx.server_start(max_slots=64, ticks_per_round=ticks, max_pairs_per_tick=max_pairs)
+    ctx.server_start(max_slots=64, ticks_per_round=ticks, max_pairs_per_tick=max_pairs,
+                     admission=sl1m.ADMIT_TWO_LANES if admission == "two_lanes" else sl1m.ADMIT_ARRIVAL)
     clocks = ClockSampler(dev)
     clocks.start()
     t0 = time.perf_counter()
@@ -506,7 +510,7 @@ def serving_measure(n_requests, rate, ticks=4, max_pairs=4e9, fp64_sample=3, wit
     # work distribution, each solved alone with the served solve's L and
     # iterations, and the mixed path alone on the same request beside it
     by_work = np.argsort([w.pairs for w in reqs])
-    ranks = np.unique(np.linspace(0, len(reqs) // 2, max(1, fp64_sample)).astype(int))
+    ranks = np.unique(np.linspace(0, len(reqs) // 2, fp64_sample).astype(int)) if fp64_sample > 0 else []
     cmp = []
     for i in by_work[ranks]:
         P, V = probs[i]
@@ -543,7 +547,8 @@ def serving_measure(n_requests, rate, ticks=4, max_pairs=4e9, fp64_sample=3, wit
            "config": {"workload": f"serving: {n_requests} requests, Poisson {rate:g}/s, "
                                   "pixels logU(4k,256k), visibilities logU(2k,100k), "
                                   "Dirac/wide-Gaussian 50/50, gains on 50%",
-                      "max_slots": 64, "ticks_per_round": ticks, "max_pairs_per_tick": max_pairs},
+                      "max_slots": 64, "ticks_per_round": ticks, "max_pairs_per_tick": max_pairs,
+                      "admission": admission},
            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                          "mean": float(lat.mean()), "max": float(lat.max())},
            "pairs_per_s": pairs / T, "wall_s": T, "slowest": slowest,
@@ -559,7 +564,7 @@ def serving_measure(n_requests, rate, ticks=4, max_pairs=4e9, fp64_sample=3, wit
 def run_serve(args):
     """--serve: the serving stream alone, as its own line."""
     out = serving_measure(args.requests or 256, args.rate or 20.0, args.ticks, args.max_pairs,
-                          args.fp64_sample, not args.no_cpu)
+                          args.fp64_sample, not args.no_cpu, admission=args.admission)
     print(json.dumps(out))
 
 
@@ -666,18 +671,21 @@ def main():
         op = 0 if dom.startswith("fwd") else 1
         traffic = ncu_traffic(dom, tuned["nst"][op], tuned["npoly"][op],
                               tuned["ctas_per_sm"][op] * N_SM, w.name)
+    # launches that did work: a solver tick launches every operator kernel, but a
+    # problem whose phase gives it no role in one skips its units
+    worked = {k: max(1, round(prof[k]["pairs"] / (float(w.n_vis) * w.n_pix))) for k in keys}
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
                 "unit": "Gpairs/s", "frac": achieved / peak, "peak_basis": peak_basis,
-                "launches": pd["launches"], "avg_launch_ms": pd["ms"] / max(1, pd["launches"]),
-                "traffic": traffic}
+                "launches": pd["launches"], "launches_with_work": worked[dom],
+                "avg_launch_ms": pd["ms"] / worked[dom], "traffic": traffic}
     if alt:
         roofline["peak_sfu_plus_fma_sincos"] = alt
         roofline["frac_of_sfu_plus_fma_sincos"] = achieved / alt["peak"]
     meas = sfu_peak_measured(w, sfu)
     roofline["peak_measured_sfu"] = meas
     roofline["frac_of_measured_sfu"] = achieved / meas["peak"]
-    per_kernel = {k: {"launches": prof[k]["launches"],
-                      "avg_launch_ms": prof[k]["ms"] / max(1, prof[k]["launches"]),
+    per_kernel = {k: {"launches": prof[k]["launches"], "launches_with_work": worked[k],
+                      "avg_launch_ms": prof[k]["ms"] / worked[k],
                       "Gpairs_per_s": prof[k]["pairs"] / (prof[k]["ms"] / 1e3) / 1e9,
                       "frac_of_peak": prof[k]["pairs"] / (prof[k]["ms"] / 1e3) / 1e9 / peak}
                   for k in keys if prof[k]["ms"] > 0}
@@ -700,7 +708,7 @@ def main():
         del flush
         torch.cuda.empty_cache()
         serving = serving_measure(args.requests or 48, args.rate or 2.0, args.ticks, args.max_pairs,
-                                  args.fp64_sample, not args.no_cpu, dev)
+                                  args.fp64_sample, not args.no_cpu, dev, args.admission)
     if rank == 0:
         out = {"metric": "pixel-visibility pairs/s (fwd+adj)", "value": value, "unit": "pairs/s",
                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
