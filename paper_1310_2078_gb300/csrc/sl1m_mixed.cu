@@ -65,7 +65,7 @@ __device__ __forceinline__ void fwd_dirac_tile(const float4* __restrict__ s_off,
 {
     const float2* ga_row[2] = {s_gain + ant[0].x * GP, s_gain + ant[1].x * GP};   // GAINS only
     const float2* gb_row[2] = {s_gain + ant[0].y * GP, s_gain + ant[1].y * GP};
-#pragma unroll 1
+#pragma unroll 4
     for (int j0 = 0; j0 < G; j0 += 4)
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) {
@@ -583,7 +583,7 @@ __device__ __forceinline__ void adj_dirac_tile(const float4* __restrict__ s_off,
 {
     int cur = -1;                    // GAINS: key of the antenna pair whose products g holds
     float2 g[2];
-#pragma unroll 1
+#pragma unroll 2
     for (int k0 = 0; k0 < G; k0 += 4)
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
