@@ -184,7 +184,7 @@ __device__ __forceinline__ void fwd_dirac_tile_pt(const float4* __restrict__ s_o
     for (int c0 = 0; c0 < G; c0 += BT_CH) {
         build_pair_table(T, bl, nb, sBa, gtab, c0, lane);
         __syncwarp();
-#pragma unroll 4
+#pragma unroll 8
         for (int jj = 0; jj < BT_CH; ++jj) {
             const int j = c0 + jj;
             const float4 o = s_off[j];
@@ -229,7 +229,7 @@ __device__ __forceinline__ void fwd_gauss_tile_pt(const float4* __restrict__ s_o
     for (int c0 = 0; c0 < G; c0 += BT_CH) {
         build_pair_table(T, bl, nb, sBa, gtab, c0, lane);
         __syncwarp();
-#pragma unroll 2
+#pragma unroll 4
         for (int jj = 0; jj < BT_CH; ++jj) {
             const int j = c0 + jj;
             const float4 o = s_off[j];
