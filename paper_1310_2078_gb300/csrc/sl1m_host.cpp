@@ -4,6 +4,8 @@
 #include "sl1m.h"
 
 #include <algorithm>
+#include <future>
+#include <thread>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -63,9 +65,12 @@ static inline float f32lo(double x) { return (float)(x - (double)(float)x); }
 
 // Order `idx[lo, hi)` so that consecutive runs of G elements are compact
 // boxes: recursive split along the wider axis at a multiple of G near the
-// median.  Only the last run can be shorter than G.
+// median.  Only the last run can be shorter than G.  The two halves of a
+// split are independent (disjoint ranges of idx), so down to `par_depth`
+// levels the left half runs on a thread of its own: the same operations on
+// the same ranges, so the same order as one thread gives.
 static void kd_rec(std::vector<int>& idx, size_t lo, size_t hi, const double* x, const double* y,
-                   size_t stride)
+                   size_t stride, int par_depth)
 {
     const size_t n = hi - lo;
     if (n <= (size_t)G) return;
@@ -83,8 +88,29 @@ static void kd_rec(std::vector<int>& idx, size_t lo, size_t hi, const double* x,
                          const double ka = key[(size_t)a * stride], kb = key[(size_t)b * stride];
                          return ka < kb || (ka == kb && a < b);
                      });
-    kd_rec(idx, lo, lo + left, x, y, stride);
-    kd_rec(idx, lo + left, hi, x, y, stride);
+    if (par_depth > 0 && n >= (size_t)1 << 16) {
+        std::future<void> f;
+        try {
+            f = std::async(std::launch::async, [&] { kd_rec(idx, lo, lo + left, x, y, stride, par_depth - 1); });
+        } catch (...) {                    // no thread to be had: the left half runs here
+            kd_rec(idx, lo, lo + left, x, y, stride, 0);
+        }
+        kd_rec(idx, lo + left, hi, x, y, stride, par_depth - 1);
+        if (f.valid()) f.get();
+    } else {
+        kd_rec(idx, lo, lo + left, x, y, stride, 0);
+        kd_rec(idx, lo + left, hi, x, y, stride, 0);
+    }
+}
+
+// Levels of the k-d split that run their halves in parallel: up to the host's
+// hardware threads (at most 16 leaves).
+static int kd_par_depth()
+{
+    const unsigned t = std::max(1u, std::thread::hardware_concurrency());
+    int d = 0;
+    while (d < 4 && (2u << d) <= t) ++d;
+    return d;
 }
 
 // Append `members` (caller indices) in k-d order, padded with -1 to a
@@ -92,7 +118,7 @@ static void kd_rec(std::vector<int>& idx, size_t lo, size_t hi, const double* x,
 static void kd_append(std::vector<int>& order, std::vector<int> members, const double* x,
                       const double* y, size_t stride)
 {
-    kd_rec(members, 0, members.size(), x, y, stride);
+    kd_rec(members, 0, members.size(), x, y, stride, kd_par_depth());
     order.insert(order.end(), members.begin(), members.end());
     while (order.size() % G) order.push_back(-1);
 }

@@ -133,3 +133,18 @@ def test_granules_are_compact_for_uv_tracks(sl1m):
                for g in range(w.n_vis // G)]
     # k-d granules are more than an order of magnitude tighter than random ones
     assert np.median(ext) < 0.1 * np.median(ext_rnd)
+
+
+def test_granule_order_of_a_large_input_is_deterministic_and_compact(sl1m):
+    """Above 2^16 points the top levels of the k-d split run on threads: the
+    order is still a padded permutation, the same on every call, and made of
+    compact boxes (each granule's extent far below a random granule's)."""
+    xy = np.random.default_rng(11).uniform(-1, 1, (300_001, 2))
+    a = sl1m.granule_order(xy)
+    b = sl1m.granule_order(xy)
+    assert np.array_equal(a, b)
+    real = a[a >= 0]
+    assert real.size == 300_001 and np.array_equal(np.sort(real), np.arange(300_001))
+    gr = a[: (len(a) // G - 1) * G].reshape(-1, G)
+    ext = np.ptp(xy[gr], axis=1).max(axis=1)
+    assert np.median(ext) < 0.05
