@@ -214,3 +214,13 @@ def test_measured_sfu_peak_weighs_the_pixel_kinds():
         assert m["per_clk_per_sm_at_max_clock"]["sincos_per_s"] == pytest.approx(16.0)
     m = bench.sfu_peak_measured(W(None), {"sincos_per_s": r / 2, "ex2_per_s": r})
     assert m["peak"] == pytest.approx(bench.sfu_peak(W(None))[0] / 2)
+
+
+def test_profiles_hold_dram_traffic_for_the_default_workload():
+    """The committed launch-list summary of the default workload carries the
+    one-pass DRAM lines the bench reads for `roofline.traffic`."""
+    import re
+    w = bench.workload(bench.parse([]).config)
+    prof = open(os.path.join(ROOT, "profiles", "launch_list_paper_scale_dirac_1024x1024_406400vis.md")).read()
+    lines = re.findall(r"^traffic: kernel=(\S+) .* workload=(\S+) src=\S+ dram_bytes_per_launch=(\d+)$", prof, re.M)
+    assert {k for k, wl, _ in lines if wl == w.name} == {"fwd_mixed", "adj_mixed"}
