@@ -58,6 +58,7 @@ def parse(argv=None):
     ap.add_argument("--n-side", type=int, default=0, help="override: pixel grid side")
     ap.add_argument("--n-ant", type=int, default=0, help="override: antennas")
     ap.add_argument("--n-times", type=int, default=0, help="override: snapshots")
+    ap.add_argument("--no-gains", action="store_true", help="the workload without its gains")
     ap.add_argument("--iters", type=int, default=0,
                     help="FISTA steps per bench step (default 5; 200 with --full-solve)")
     ap.add_argument("--full-solve", action="store_true",
@@ -80,6 +81,9 @@ def parse(argv=None):
                     help="serving arrival rate, 1/s (default 20 with --serve, 2 in the default line)")
     ap.add_argument("--no-serve", action="store_true", help="leave the serving object out of the line")
     ap.add_argument("--fp64-sample", type=int, default=3)
+    ap.add_argument("--table1", action="store_true",
+                    help="the noise-free lambda sweep of Table 1 at its sizes (1024^2 px x 37,800 vis)")
+    ap.add_argument("--table1-cap", type=int, default=1000, help="--table1: FISTA steps at most per lambda")
     ap.add_argument("--ticks", type=int, default=4, help="serving: ticks per round")
     ap.add_argument("--max-pairs", type=float, default=4e9, help="serving: work in flight per tick")
     ap.add_argument("--admission", default="two_lanes", choices=["two_lanes", "arrival"],
@@ -143,6 +147,9 @@ def workload(cfg: int, rank: int = 0, small: bool = False, args=None):
             if getattr(args, k, 0):
                 kw[k] = getattr(args, k)
     w = synth.config2(n_side=128) if small else synth.CONFIGS[cfg](**kw)
+    if args is not None and getattr(args, "no_gains", False) and w.gains is not None:
+        w.gains = None
+        w.name += "-no-gains"
     if rank:
         # weak scaling: every rank solves its own independent problem of the same shape
         rng = synth.rng_for(synth.BASE_SEED + 100 * rank + cfg)
@@ -561,6 +568,51 @@ def serving_measure(n_requests, rate, ticks=4, max_pairs=4e9, fp64_sample=3, wit
     return out
 
 
+def run_table1(args):
+    """--table1: the noise-free lambda sweep of Sect. 4.1 (Table 1) at the
+    paper's sizes -- 1024^2 Dirac pixels of 30 arcsec, 37,800 visibilities, 50
+    point sources, no noise -- with lambda from 1e-6 to 1e-1 of lambda_max
+    (the paper's lambda = 1e-2 ... 1e3 span the same decades below its
+    lambda_max).  Each solve starts from zero and stops when the relative
+    change of E falls below 1e-6, or after --table1-cap steps; L by power
+    iteration once.  Reports per lambda the steps taken, the recovered total
+    flux against the true one, the residual, and the largest error on the
+    sources."""
+    import torch
+    from paper_1310_2078_gb300 import sl1m, synth
+    sl1m.load()
+    torch.cuda.set_device(0)
+    w = synth.table1()
+    ctx = sl1m.Context(0)
+    P = sl1m.problem_from(ctx, w)
+    V = P.forward(w.x_true, sl1m.FP64)                    # noise-free data, FP64 forward
+    P.set_vis_data(V)
+    _, lmax = P.dirty_image(sl1m.MIXED)
+    L, pit = P.max_eig(50, 1e-6, sl1m.MIXED)
+    on = w.x_true > 0
+    true_l1 = float(w.x_true.sum())
+    rows = []
+    t_all = time.perf_counter()
+    for f in (1e-6, 1e-5, 1e-4, 1e-3, 1e-2, 1e-1):
+        t0 = time.perf_counter()
+        img, st = P.solve(f * lmax, L=L, max_iter=args.table1_cap, rel_tol=1e-6, precision=sl1m.MIXED)
+        dt = time.perf_counter() - t0
+        rows.append({"lambda_over_lambda_max": f, "lambda": f * lmax, "iters": st["iters"],
+                     "converged": bool(st["converged"]), "l1": st["l1"], "l1_over_true": st["l1"] / true_l1,
+                     "resid2": st["resid2"], "E": st["E"], "nnz": st["nnz"],
+                     "max_err_on_sources_of_peak": float(np.max(np.abs(img[on] - w.x_true[on])) / w.x_true.max()),
+                     "off_source_flux": float(img[~on].sum()), "seconds": dt})
+    T = time.perf_counter() - t_all
+    iters = sum(r["iters"] for r in rows)
+    out = {"mode": "table1 lambda sweep", "data": "synthetic, noise-free",
+           "config": {"workload": w.name, "n_pix": w.n_pix, "n_vis": w.n_vis, "sources": int(on.sum()),
+                      "precision": "mixed", "rel_tol": 1e-6, "max_iter": args.table1_cap},
+           "true_l1": true_l1, "lambda_max": lmax, "L": L, "power_iters": pit, "rows": rows,
+           "wall_s": T, "pairs_per_s": (2 * iters + len(rows)) * float(w.n_pix) * w.n_vis / T}
+    print(json.dumps(out))
+    ctx.close()
+
+
 def run_serve(args):
     """--serve: the serving stream alone, as its own line."""
     out = serving_measure(args.requests or 256, args.rate or 20.0, args.ticks, args.max_pairs,
@@ -574,6 +626,8 @@ def main():
         return run_reference(args)
     if args.serve:
         return run_serve(args)
+    if args.table1:
+        return run_table1(args)
     import torch
     ws, rank, local = dist_init()
     from paper_1310_2078_gb300 import sl1m

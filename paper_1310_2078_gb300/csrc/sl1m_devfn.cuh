@@ -144,10 +144,11 @@ __device__ __forceinline__ bool mbar_try(unsigned a, unsigned parity)
 
 // Wait until the phase of bar with this parity has completed, bounded by
 // elapsed time: after WAIT_LIMIT_NS on the global timer it gives up and sets
-// `fault`.  A thread whose `fault` is already set does not wait at all, so a
-// kernel whose copies stopped completing gives up once per thread, records
-// the fault (the caller) and runs to its end; no barrier of the CTA is left
-// waiting.
+// `fault`.  A thread whose `fault` is already set does not wait at all, and
+// the kernels issue no further bulk copies from a thread whose `fault` is set,
+// so a kernel whose copies stopped completing gives up once per thread,
+// records the fault (the caller) and runs to its end; no barrier of the CTA is
+// left waiting.
 __device__ __forceinline__ void mbar_wait(unsigned long long* bar, unsigned parity, bool& fault)
 {
     if (fault) return;

@@ -241,6 +241,26 @@ def config4(n_side: int = 1024, n_ant: int = 128, n_times: int = 50) -> Workload
                     meta={"n_side": n_side, "extent": 0.3})
 
 
+def table1(n_side: int = 1024, n_ant: int = 36, n_times: int = 60) -> Workload:
+    """The setting of the noise-free lambda sweep (Sect. 4.1, Table 1): a
+    1024x1024 Dirac grid of 30 arcsec pixels (+/-0.0745 in l,m), 36 antennas,
+    one hour sampled every minute -> 630 baselines x 60 = 37,800 visibilities,
+    declination -22.5 deg with the field at zenith at the start, 50 point
+    sources of flux U(0.2, 2.0) on pixel centres in the inner 80%, no noise.
+    The paper's antenna layout is not available: antennas are uniform in a
+    3 km-radius disk with 5 m height scatter (readings), at 150 MHz."""
+    rng = rng_for(BASE_SEED + 6)
+    uvw, ap = _array(rng, n_ant, 3000.0, 5.0, -22.5, n_times)
+    delta = 30.0 / 206264.806
+    lm = regular_grid(n_side, 0.5 * n_side * delta)
+    x = np.zeros(n_side * n_side)
+    src = rng.choice(inner_pixels(n_side), size=min(50, n_side * n_side // 8), replace=False)
+    x[src] = rng.uniform(0.2, 2.0, src.size)
+    return Workload(f"table1-dirac-{n_side}x{n_side}-{uvw.shape[0]}vis", uvw, ap, lm, x,
+                    np.zeros(uvw.shape[0], np.complex128), precision="mixed",
+                    meta={"n_side": n_side, "extent": 0.5 * n_side * delta, "noise_free": True})
+
+
 def serving_request(i: int, np_range=(4096, 262144), nv_range=(2048, 100_000),
                     seed_base: int = BASE_SEED + 5) -> Workload:
     """Request i of the serving stream: its own seed, pixels ~ logU(np_range),

@@ -164,3 +164,18 @@ def test_equal_seeds_give_equal_inputs():
     for k in c:
         if c[k] is not None:
             np.testing.assert_array_equal(c[k], d[k])
+
+
+def test_table1_setting_has_the_papers_sizes():
+    """The noise-free sweep of Table 1: 1024^2 pixels of 30 arcsec, 36 antennas
+    sampled every minute for an hour (630 x 60 = 37,800 visibilities), 50
+    sources of 0.2-2.0 on pixel centres in the inner 80%, no noise."""
+    w = synth.table1()
+    assert (w.n_pix, w.n_vis) == (1024 * 1024, 37800)
+    delta = 30.0 / 206264.806
+    assert np.allclose(np.diff(np.unique(w.lm[:, 0])), delta)
+    on = np.flatnonzero(w.x_true)
+    assert on.size == 50 and np.all((w.x_true[on] >= 0.2) & (w.x_true[on] <= 2.0))
+    assert set(on) <= set(synth.inner_pixels(1024))
+    assert np.all(w.noise == 0)
+    assert np.array_equal(w.ant_pair[:630], np.stack(np.triu_indices(36, 1), axis=1))
