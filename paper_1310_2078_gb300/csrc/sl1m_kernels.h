@@ -14,9 +14,16 @@ constexpr int NST_DEFAULT = 4;
 // Tile-shape code carried as `nst` below: streamed granules per stage (2, 4
 // or 8) plus 16 x npoly, the pairs of every 8 whose sincos runs on the FMA
 // pipe (0, 1 or 2; Dirac tiles without gains).
+// Bit 8: the batch has no Gaussian pixels, so the no-gains mixed kernels may
+// run an instance compiled without the Gaussian tiles.
+constexpr int SHAPE_DIRAC_ONLY = 1 << 8;
 constexpr int shape_code(int nst, int npoly) { return nst | (npoly << 4); }
 constexpr int shape_nst(int code) { return code & 15; }
-constexpr int shape_npoly(int code) { return code >> 4; }
+constexpr int shape_npoly(int code) { return (code >> 4) & 15; }
+constexpr bool shape_dirac_only(int code) { return (code & SHAPE_DIRAC_ONLY) != 0; }
+// The shape code of a launch over pixels that may (gauss) or may not hold
+// Gaussian pixels.
+constexpr int shape_for(int code, bool gauss) { return gauss ? (code & ~SHAPE_DIRAC_ONLY) : (code | SHAPE_DIRAC_ONLY); }
 cudaError_t launch_forward(int precision, bool gains, int n_ant, const DevProblem* probs,
                            const Plan* plp, int C, double2* partial, cudaStream_t st, int nst = NST_DEFAULT);
 cudaError_t launch_adjoint(int precision, bool gains, int n_ant, const DevProblem* probs, const Plan* plp, int C,

@@ -55,7 +55,10 @@ __device__ unsigned int g_wait_fault;
 template <int NPOLY>
 __device__ __forceinline__ constexpr bool fma_slot(int jj, int r) { return 2 * jj + r >= 8 - NPOLY; }
 
-template <bool GAINS, bool EXACT, int NPOLY = 0>
+// UNR: groups of 4 streamed pixels per iteration of the tile's loop (the
+// unrolling measured fastest: 4 in the kernel instance with Gaussian tiles,
+// 8 in the Dirac-only one).
+template <bool GAINS, bool EXACT, int NPOLY = 0, int UNR = 4>
 __device__ __forceinline__ void fwd_dirac_tile(const float4* __restrict__ s_off,
                                                const float4* __restrict__ s_lo,
                                                const float2* __restrict__ sBa,
@@ -65,7 +68,7 @@ __device__ __forceinline__ void fwd_dirac_tile(const float4* __restrict__ s_off,
 {
     const float2* ga_row[2] = {s_gain + ant[0].x * GP, s_gain + ant[1].x * GP};   // GAINS only
     const float2* gb_row[2] = {s_gain + ant[0].y * GP, s_gain + ant[1].y * GP};
-#pragma unroll 4
+#pragma unroll UNR
     for (int j0 = 0; j0 < G; j0 += 4)
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) {
@@ -109,7 +112,7 @@ __device__ __forceinline__ void fwd_gauss_tile(const float4* __restrict__ s_off,
 {
     const float2* ga_row[2] = {s_gain + ant[0].x * GP, s_gain + ant[1].x * GP};   // GAINS only
     const float2* gb_row[2] = {s_gain + ant[0].y * GP, s_gain + ant[1].y * GP};
-#pragma unroll(GAINS ? 1 : 2)   // the gains variant stays within 80 registers
+#pragma unroll(GAINS ? 1 : 4)   // the gains variant stays within its registers
     for (int j = 0; j < G; ++j) {
         const float4 o = s_off[j];
         const float4 pg = s_pg[j];             // {l, m, r^2/2, nu}
@@ -308,11 +311,13 @@ __device__ __forceinline__ void fwd_stage_load(unsigned char* buf, const DevProb
 }
 
 // Owned: visibilities (warp = one vis granule, lane = 2 visibilities).
+// GAUSS = false: an instance for batches without Gaussian pixels, compiled
+// without the Gaussian tiles (fewer live registers for the Dirac tiles).
 // Streamed: pixel granules through the stage buffers, NST per stage (a tile
 // shape the autotuner picks; the gains kernel stages one, since one granule's
 // gains for all antennas already fill most of shared memory).  One CTA
 // barrier per stage: it frees the buffer the next copies go to.
-template <bool GAINS, int NST, int NPOLY = 0>
+template <bool GAINS, int NST, int NPOLY = 0, bool GAUSS = true>
 __global__ void __launch_bounds__(NTHREADS, GAINS ? 2 : 3)   // gains: pair-table path + gathers fit in 128
 fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ plp, double2* __restrict__ partial)
 {
@@ -369,7 +374,8 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
         const bool gdbl = GAINS && 2u * gbytes <= dyn_smem_bytes() - 2u * S::BYTES;
         // the range's first stage; its buffer's last readers finished before
         // the barrier of the previous range's last stage
-        if (threadIdx.x == 0) fwd_stage_load<NST>(s_dyn + scur * S::BYTES, P, X, g0, min(NST, g1 - g0), &s_sbar[scur]);
+        if (threadIdx.x == 0 && !fault)
+            fwd_stage_load<NST>(s_dyn + scur * S::BYTES, P, X, g0, min(NST, g1 - g0), &s_sbar[scur]);
 
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 xh[2] = {z4, z4}, dx[2] = {z4, z4};
@@ -401,7 +407,7 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
         for (int gs = g0; gs < g1; gs += NST) {
             const int ns = min(NST, g1 - gs);
             __syncthreads();                       // the previous stage is consumed
-            if (threadIdx.x == 0) {
+            if (threadIdx.x == 0 && !fault) {      // (a thread whose wait gave up issues no more copies)
                 if (gs + NST < g1)                 // prefetch the next stage
                     fwd_stage_load<NST>(s_dyn + (scur ^ 1) * S::BYTES, P, X, gs + NST, min(NST, g1 - gs - NST),
                                         &s_sbar[scur ^ 1]);
@@ -456,7 +462,7 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
 #pragma unroll
                 for (int r = 0; r < 2; ++r) C[r] = frac_dot3(xh[r], P.vis.lo[e0 + 32 * r], yc_h, yc_l);
                 float sr[2] = {0.f, 0.f}, si[2] = {0.f, 0.f};
-                if (kind == DIRAC) {
+                if (!GAUSS || kind == DIRAC) {
                     if (GAINS && nb > 0) {
                         if (exact) {
                             const float4 dxt[2] = {P.vis.off[e0], P.vis.off[e0 + 32]},
@@ -472,7 +478,7 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                                      dxl[2] = {P.vis.offlo[e0], P.vis.offlo[e0 + 32]};
                         fwd_dirac_tile<GAINS, true>(q_off, q_lo, q_Ba, gtab, dxt, dxl, ant, sr, si);
                     } else {
-                        fwd_dirac_tile<GAINS, false, NPOLY>(q_off, q_lo, q_Ba, gtab, dx, dx, ant, sr, si);
+                        fwd_dirac_tile<GAINS, false, NPOLY, GAUSS ? 4 : 8>(q_off, q_lo, q_Ba, gtab, dx, dx, ant, sr, si);
                     }
 #pragma unroll
                     for (int r = 0; r < 2; ++r) {
@@ -698,7 +704,7 @@ __device__ __forceinline__ void adj_stage_load(unsigned char* buf, const DevProb
 // Owned: pixels (warp = one pixel granule, lane = 2 pixels).
 // Streamed: visibility granules through the two stage buffers, NSA per stage,
 // one CTA barrier per stage (it frees the buffer the next copies go to).
-template <int NSA, int NPOLY = 0>
+template <int NSA, int NPOLY = 0, bool GAUSS = true>
 __global__ void __launch_bounds__(NTHREADS, 3)
 adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ plp, double* __restrict__ partial)
 {
@@ -737,7 +743,8 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
         const int g1 = (int)min((long long)upb, (long long)g0 + (u_end - u));
         // the range's first stage; its buffer's last readers finished before
         // the barrier of the previous range's last stage
-        if (threadIdx.x == 0) adj_stage_load<NSA>(s_dyn + scur * S::BYTES, P, g0, min(NSA, g1 - g0), &s_sbar[scur]);
+        if (threadIdx.x == 0 && !fault)
+            adj_stage_load<NSA>(s_dyn + scur * S::BYTES, P, g0, min(NSA, g1 - g0), &s_sbar[scur]);
         const int pgi = blk * BLK_GRAN + warp;
         const bool pg_ok = pgi < P.pix.n_gran;
         const int e0 = (pg_ok ? pgi : 0) * G + lane;     // this lane's pixels: e0, e0 + 32
@@ -758,17 +765,17 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
             for (int r = 0; r < 2; ++r) {
                 xh[r] = P.pix.hi[eidx[r]];
                 dx[r] = to_rad(P.pix.off[eidx[r]]);
-                if (kind != DIRAC) pgd[r] = pix_for_gauss(P.pgauss[eidx[r]]);
+                if (GAUSS && kind != DIRAC) pgd[r] = pix_for_gauss(P.pgauss[eidx[r]]);
             }
         }
-        const bool gauss = (kind != DIRAC);
+        const bool gauss = GAUSS && (kind != DIRAC);   // GAUSS = false: no Gaussian pixels in the batch
         const bool par = (kind == PARAXIAL);
         double tot[2] = {0.0, 0.0};
 
         for (int gs = g0; gs < g1; gs += NSA) {
             const int ns = min(NSA, g1 - gs);
             __syncthreads();                       // the previous stage is consumed
-            if (threadIdx.x == 0 && gs + NSA < g1)  // prefetch the next stage
+            if (threadIdx.x == 0 && !fault && gs + NSA < g1)  // prefetch the next stage
                 adj_stage_load<NSA>(s_dyn + (scur ^ 1) * S::BYTES, P, gs + NSA, min(NSA, g1 - gs - NSA),
                                     &s_sbar[scur ^ 1]);
             mbar_wait(&s_sbar[scur], (spar >> scur) & 1u, fault);
@@ -1054,12 +1061,12 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
             const int pgi = blk * BLK_GRAN + og;
             if (pgi >= P.pix.n_gran) break;                  // uniform over the CTA
             __syncthreads();                                 // s_gain / s_red free again
-            if (threadIdx.x == 0) {
+            if (threadIdx.x == 0 && !fault) {
                 fence_proxy_async_smem();                    // the table's last readers are done
                 bulk_load(s_gain, P.gains32 + (size_t)pgi * gtab_n, (unsigned)gtab_n * (unsigned)sizeof(float2),
                           &s_gbar);
             }
-            if (lane == 0 && g0 + warp < g1) adj_raw_load(raw, P, R, g0 + warp, &s_wbar[warp]);
+            if (lane == 0 && !fault && g0 + warp < g1) adj_raw_load(raw, P, R, g0 + warp, &s_wbar[warp]);
             const float4 ch = P.pix.cen_hi[pgi], cl = P.pix.cen_lo[pgi], ext = P.pix.ext[pgi];
             const int kind = P.gkind[pgi];
             const float sigma = P.gsig[pgi];
@@ -1105,7 +1112,7 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
                 }
                 const float4 yc_h = raw_cen[0], yc_l = raw_cen[1], yext = raw_cen[2];
                 __syncwarp();                                 // the slice is read: refill it
-                if (lane == 0 && g + BLK_GRAN < g1) adj_raw_load(raw, P, R, g + BLK_GRAN, &s_wbar[warp]);
+                if (lane == 0 && !fault && g + BLK_GRAN < g1) adj_raw_load(raw, P, R, g + BLK_GRAN, &s_wbar[warp]);
                 const bool exact = dot3(ext, yext) > D_MAX;
                 float cC[2], sC[2];                   // e^{2 pi i C}, C the tile's centre term
 #pragma unroll
@@ -1248,29 +1255,36 @@ static int occ_of(K kernel, int dyn)
 using FwdKernel = void (*)(const DevProblem*, const Plan*, double2*);
 using AdjKernel = void (*)(const DevProblem*, const Plan*, double*);
 
-// The no-gains kernel of a tile-shape code (nst 2 / 4 / 8, npoly 0 / 1 / 2).
-template <int N>
+// The no-gains kernel of a tile-shape code (nst 2 / 4 / 8, npoly 0 / 1 / 2,
+// with or without the Gaussian tiles).
+template <int N, bool GS>
 static FwdKernel fwd_by_poly(int np)
 {
-    return np <= 0 ? fwd_mixed_kernel<false, N, 0> : np == 1 ? fwd_mixed_kernel<false, N, 1>
-                                                             : fwd_mixed_kernel<false, N, 2>;
+    return np <= 0 ? fwd_mixed_kernel<false, N, 0, GS> : np == 1 ? fwd_mixed_kernel<false, N, 1, GS>
+                                                                 : fwd_mixed_kernel<false, N, 2, GS>;
 }
-template <int N>
+template <int N, bool GS>
 static AdjKernel adj_by_poly(int np)
 {
-    return np <= 0 ? adj_mixed_kernel<N, 0> : np == 1 ? adj_mixed_kernel<N, 1> : adj_mixed_kernel<N, 2>;
+    return np <= 0 ? adj_mixed_kernel<N, 0, GS> : np == 1 ? adj_mixed_kernel<N, 1, GS> : adj_mixed_kernel<N, 2, GS>;
+}
+template <bool GS>
+static FwdKernel fwd_kernel_gs(int nst, int np)
+{
+    return nst <= 2 ? fwd_by_poly<2, GS>(np) : nst <= 4 ? fwd_by_poly<4, GS>(np) : fwd_by_poly<8, GS>(np);
 }
 static FwdKernel fwd_kernel_of(int code)
 {
     const int nst = shape_nst(code), np = shape_npoly(code);
-    return nst <= 2 ? fwd_by_poly<2>(np) : nst <= 4 ? fwd_by_poly<4>(np) : fwd_by_poly<8>(np);
+    return shape_dirac_only(code) ? fwd_kernel_gs<false>(nst, np) : fwd_kernel_gs<true>(nst, np);
 }
 // The no-gains adjoint stages 2 or 4 granules (with 8, its stage buffers and
 // per-warp records would leave room for 1 CTA per SM).
 static AdjKernel adj_kernel_of(int code)
 {
     const int nst = shape_nst(code), np = shape_npoly(code);
-    return nst <= 2 ? adj_by_poly<2>(np) : adj_by_poly<4>(np);
+    if (shape_dirac_only(code)) return nst <= 2 ? adj_by_poly<2, false>(np) : adj_by_poly<4, false>(np);
+    return nst <= 2 ? adj_by_poly<2, true>(np) : adj_by_poly<4, true>(np);
 }
 
 cudaError_t launch_forward_mixed(bool gains, int n_ant, int nst, const DevProblem* probs, const Plan* plp, int C,
