@@ -297,9 +297,10 @@ int sl1m_server_info(sl1m_ctx* ctx, sl1m_server_info_t* info);
  * adjoint of this problem it times, with CUDA events, every (streamed
  * granules per shared-memory stage: 2, 4 or 8; the adjoint 2 or 4) x
  * (persistent grid: 1 .. occupancy CTAs per SM) of the mixed no-gains
- * kernels, then at the fastest of those the share npoly (1 or 2 of
- * every 8 pairs) whose sincos runs on the FMA pipe instead of the SFU; with
- * gains or in FP64 only the grid is tuned.  The choice is kept in the context,
+ * kernels, then for every stage count at its fastest grid the share npoly
+ * (1 or 2 of every 8 pairs) whose sincos runs on the FMA pipe instead of the
+ * SFU (each timed launch follows a launch of the other operator, as in a
+ * solve); with gains or in FP64 only the grid is tuned.  The choice is kept in the context,
  * keyed by (precision, operator, gains, Gaussian pixels, log2 of the work
  * units); later launches of problems with the same key -- single solves and
  * server batches -- use it.  nst_out, ctas_per_sm_out and npoly_out ([2]:

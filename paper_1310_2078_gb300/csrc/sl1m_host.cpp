@@ -966,6 +966,10 @@ int batch_set(sl1m_ctx* ctx, Batch& B, const std::vector<sl1m_problem*>& probs,
             const auto ta = ctx->tune.find(tune_key(precision, 1, c == 1, gauss, ua));
             if (tf != ctx->tune.end()) { B.nst[0][c] = tf->second.first; kf = tf->second.second; }
             if (ta != ctx->tune.end()) { B.nst[1][c] = ta->second.first; ka = ta->second.second; }
+            if (precision != 0 && c == 0) {         // no Gaussian pixels: the Dirac-only instances
+                B.nst[0][c] = shape_for(B.nst[0][c], gauss);
+                B.nst[1][c] = shape_for(B.nst[1][c], gauss);
+            }
             const int occf = occupancy(precision == 0 ? 0 : 2, c == 1, std::max(1, B.n_ant_max), B.nst[0][c]);
             const int occa = occupancy(precision == 0 ? 1 : 3, c == 1, std::max(1, B.n_ant_max), B.nst[1][c]);
             kf = kf > 0 ? std::min(kf, occf) : occf;
@@ -1628,6 +1632,7 @@ int sl1m_autotune(sl1m_problem* prob, int precision, int32_t* nst_out, int32_t* 
         float best = 1e30f;
         int bcode = NST_DEFAULT, bk = 0;
         const auto time_shape = [&](int code, int k) -> float {
+            if (mixed_plain) code = shape_for(code, prob->has_gauss);
             DevPlan P;
             if (build_plan(nb, ns, ctx->num_sms * k, P, st, &uc) != cudaSuccess) { rc = SL1M_ERR_CUDA; return 0.f; }
             const size_t need = (size_t)std::max(1, P.pl.n_slots) * BLK;
@@ -1635,33 +1640,46 @@ int sl1m_autotune(sl1m_problem* prob, int precision, int32_t* nst_out, int32_t* 
                 rc = SL1M_ERR_OOM;
                 return 0.f;
             }
+            // each timed launch follows a launch of the other operator, as in a
+            // solver tick: a forward does not find the pixel stream the previous
+            // forward left in L2, and shapes are ranked as a solve runs them
             float ms = 0.f;
             for (int rep = 0; rep < 4; ++rep) {
-                if (rep == 1) cudaEventRecord(e0, st);
+                const int rb = batch_op(ctx, *Bop, 1 - op);
+                if (rb != SL1M_OK) { rc = rb; return 0.f; }
+                cudaEventRecord(e0, st);
                 cudaError_t e = op == 0 ? launch_forward(precision, gains, prob->n_ant, Bop->desc.p, P.dpl.p, P.pl.C,
                                                          ctx->partial_f.p, st, code)
                                         : launch_adjoint(precision, gains, prob->n_ant, Bop->desc.p, P.dpl.p, P.pl.C,
                                                          ctx->partial_a.p, st, code);
                 if (e != cudaSuccess) { rc = SL1M_ERR_CUDA; return 0.f; }
                 ctx->n_launch += 1;
+                cudaEventRecord(e1, st);
+                if (cudaEventSynchronize(e1) != cudaSuccess) { rc = SL1M_ERR_CUDA; return 0.f; }
+                float m = 0.f;
+                cudaEventElapsedTime(&m, e0, e1);
+                if (rep > 0) ms += m;                // the first is a warm-up
             }
-            cudaEventRecord(e1, st);
-            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = SL1M_ERR_CUDA; return 0.f; }
-            cudaEventElapsedTime(&ms, e0, e1);
             return ms;
         };
-        for (int nst : cands) {
-            const int occ = occupancy((precision == SL1M_FP64 ? 0 : 2) + op, gains, std::max(1, prob->n_ant), nst);
+        std::vector<int> kbest(cands.size(), 1);   // per stage count: its fastest grid at npoly 0
+        for (size_t ci = 0; ci < cands.size(); ++ci) {
+            const int nst = cands[ci];
+            const int occ = occupancy((precision == SL1M_FP64 ? 0 : 2) + op, gains, std::max(1, prob->n_ant),
+                                      mixed_plain ? shape_for(nst, prob->has_gauss) : nst);
+            float bn = 1e30f;
             for (int k = 1; k <= occ && rc == SL1M_OK; ++k) {
                 const float ms = time_shape(nst, k);
+                if (rc == SL1M_OK && ms < bn) { bn = ms; kbest[ci] = k; }
                 if (rc == SL1M_OK && ms < best) { best = ms; bcode = nst; bk = k; }
             }
         }
-        if (mixed_plain) {
-            const int nst = bcode, k0 = bk;       // stage-1 choice (npoly 0)
+        // then npoly 1 and 2 at every stage count (with its grid): the stage
+        // count that is fastest at npoly 0 need not be the fastest at npoly 1
+        for (size_t ci = 0; mixed_plain && ci < cands.size() && rc == SL1M_OK; ++ci) {
             for (int npoly = 1; npoly <= 2 && rc == SL1M_OK; ++npoly) {
-                const int code = shape_code(nst, npoly);
-                const int k = std::min(k0, occupancy(2 + op, false, 1, code));
+                const int code = shape_code(cands[ci], npoly);
+                const int k = std::min(kbest[ci], occupancy(2 + op, false, 1, shape_for(code, prob->has_gauss)));
                 const float ms = time_shape(code, k);
                 if (rc == SL1M_OK && ms < best) { best = ms; bcode = code; bk = k; }
             }
