@@ -175,6 +175,34 @@ __device__ __forceinline__ int adj_finish_mode(const DevProblem& P)
     }
 }
 
+// Sum of the ncon partial slots of element i, from slot poff on, in slot
+// order.  The loads of 8 slots are issued before their additions, so they are
+// in flight together (one L2 round trip per 8 slots, not per slot); the sum
+// is added in the same order as one load at a time would add it.
+template <class T>
+__device__ __forceinline__ void add_in(T& s, const T& q);
+template <>
+__device__ __forceinline__ void add_in<double>(double& s, const double& q) { s += q; }
+template <>
+__device__ __forceinline__ void add_in<double2>(double2& s, const double2& q)
+{
+    s.x += q.x;
+    s.y += q.y;
+}
+template <class T>
+__device__ __forceinline__ void sum_slots(T& s, const T* __restrict__ partial, int poff, int ncon, int i)
+{
+    int c = 0;
+    for (; c + 8 <= ncon; c += 8) {
+        T q[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) q[t] = partial[(size_t)(poff + c + t) * BLK + i];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) add_in(s, q[t]);
+    }
+    for (; c < ncon; ++c) add_in(s, partial[(size_t)(poff + c) * BLK + i]);
+}
+
 // ---------------------------------------------------------- forward finish
 // Grid-stride over the plan's owned blocks (BLK visibilities each): sums the
 // block's partial slots in CTA order, then per problem
@@ -215,11 +243,7 @@ fwd_finish_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__
             const int e = blk * BLK + i;
             if (e >= P.vis.n_pad) continue;
             double2 s = make_double2(0.0, 0.0);
-            for (int c = 0; c < ncon; ++c) {
-                const double2 q = partial[(size_t)(poff + c) * BLK + i];
-                s.x += q.x;
-                s.y += q.y;
-            }
+            sum_slots(s, partial, poff, ncon, i);
             if (!isfinite(s.x) || !isfinite(s.y)) bad = 1;
             if (mode == FIN_OP) {
                 P.fwd_out[e] = s;
@@ -298,7 +322,7 @@ adj_finish_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__
             const int e = blk * BLK + i;
             if (e >= P.pix.n_pad) continue;
             double s = 0.0;
-            for (int c = 0; c < ncon; ++c) s += partial[(size_t)(poff + c) * BLK + i];
+            sum_slots(s, partial, poff, ncon, i);
             if (!isfinite(s)) bad = 1;
             if (mode == FIN_OP) {
                 P.adj_out[e] = s;
