@@ -40,7 +40,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 MUFU_PER_SM_CLK = 16          # sin/cos/ex2 per clock per SM (CUDA guide throughput table)
-SFU_OPS_PER_PAIR = {"dirac": 2, "gauss": 3}
+# MUFU results per pair, per operator: the forward takes a sine and a cosine
+# (its output is complex), the adjoint a cosine alone (its output is real:
+# Re(conj(A) r) = |r| cos(theta + arg r)); a Gaussian pixel adds an exp2.
+SFU_OPS_PER_PAIR = {"fwd": {"dirac": 2, "gauss": 3}, "adj": {"dirac": 1, "gauss": 2}}
+# The fewest instructions a Dirac pair takes with its trigonometry on the
+# SFU and on the FMA pipe.  Forward: 3 FFMA phase, 1 FMUL argument scale,
+# 2 MUFU, 2 FFMA accumulate; 21 with the 16-instruction sincos.  Adjoint: 1
+# FADD + 3 FFMA phase, 1 FMUL, 1 MUFU, 1 FFMA; 16 with the 11-instruction
+# cosine.
+INSTR_PER_PAIR = {"fwd": (8, 21), "adj": (7, 16)}
 N_SM = 152
 SM_MAX_MHZ = 2070.0
 L2_BYTES = 129 * 2 ** 20
@@ -266,52 +275,55 @@ def ncu_traffic(kernel, nst, npoly, ctas, workload):
     return None
 
 
-def sfu_peak(w):
-    """SFU issue bound of the operator kernels on workload w (Gpairs/s).
+def sfu_peak(w, op="fwd"):
+    """SFU issue bound of operator op ("fwd" or "adj") on workload w (Gpairs/s).
 
-    Per pair the SFU runs sin and cos (Dirac) plus exp2 (Gaussian); the
-    bound is N_SM x 16 MUFU/clk x max clock over the MUFU ops per pair,
-    weighted by the share of pairs of each kind (time per pair adds up).
-    For all-Dirac work a second figure is returned: the bound when a share
-    of the pairs takes its sincos on the FMA pipe, a linear program over two
-    limits per SM sub-partition -- one warp instruction issued per clock and
-    one MUFU warp instruction per 8 clocks -- with the fewest instructions a
-    pair can take: 8 on the SFU path (3 FFMA phase, 1 FMUL argument scale,
-    2 MUFU, 2 FFMA accumulate) and 21 on the FMA path (3 phase, 16 sincos,
-    2 accumulate)."""
+    Per pair the SFU runs the trigonometry (forward: sin and cos, adjoint:
+    cos) plus exp2 for a Gaussian pixel; the bound is N_SM x 16 MUFU/clk x
+    max clock over the MUFU ops per pair, weighted by the share of pairs of
+    each kind (time per pair adds up).  For all-Dirac work a second figure is
+    returned: the bound when a share of the pairs takes its trigonometry on
+    the FMA pipe, a linear program over two limits per SM sub-partition --
+    one warp instruction issued per clock and one MUFU warp instruction per 8
+    clocks -- with the fewest instructions a pair can take on either path
+    (INSTR_PER_PAIR)."""
     per_sm_clk = N_SM * SM_MAX_MHZ * 1e6 / 1e9
     kinds = np.zeros(w.n_pix, np.int32) if w.kind is None else np.asarray(w.kind)
     f_gauss = float(np.mean(kinds != 0))
-    mufu = (1 - f_gauss) * SFU_OPS_PER_PAIR["dirac"] + f_gauss * SFU_OPS_PER_PAIR["gauss"]
+    ops = SFU_OPS_PER_PAIR[op]
+    mufu = (1 - f_gauss) * ops["dirac"] + f_gauss * ops["gauss"]
     peak = per_sm_clk * MUFU_PER_SM_CLK / mufu
     basis = (f"SFU issue: {N_SM} SM x {MUFU_PER_SM_CLK} MUFU/clk x {SM_MAX_MHZ:.0f} MHz / "
-             f"{mufu:.3g} MUFU per pair ({100 * (1 - f_gauss):.0f}% Dirac pairs at 2, "
-             f"{100 * f_gauss:.0f}% Gaussian at 3)")
+             f"{mufu:.3g} MUFU per pair ({100 * (1 - f_gauss):.0f}% Dirac pairs at {ops['dirac']}, "
+             f"{100 * f_gauss:.0f}% Gaussian at {ops['gauss']})")
     alt = None
     if f_gauss == 0.0:
         # per sub-partition and clock: x SFU-path and y FMA-path warp-pairs,
-        # 2 x <= 1/8 (MUFU), 8 x + 21 y <= 1 (issue); maximise x + y
-        x = 1.0 / 16.0
-        y = (1.0 - 8.0 * x) / 21.0
+        # m x <= 1/8 (MUFU), a x + b y <= 1 (issue); maximise x + y
+        a, b = INSTR_PER_PAIR[op]
+        x = min(1.0 / (8.0 * ops["dirac"]), 1.0 / a)
+        y = max(0.0, (1.0 - a * x) / b)
         pairs_per_sm_clk = 4 * 32 * (x + y)
         alt = {"peak": per_sm_clk * pairs_per_sm_clk,
                "basis": "LP over issue (1 warp instr/clk/SMSP) and MUFU (1/8 per clk/SMSP): "
-                        "8 instr/pair on the SFU path, 21 with sincos on the FMA pipe; "
+                        f"{a} instr/pair on the SFU path, {b} with the trigonometry on the FMA pipe; "
                         f"{pairs_per_sm_clk:.2f} pairs/clk/SM at {100 * y / (x + y):.0f}% FMA-path pairs"}
     return peak, basis, alt
 
 
-def sfu_peak_measured(w, sfu):
-    """The SFU bound of workload w from the measured MUFU rates (Gpairs/s):
-    a pair takes a sin and a cos, and an exp2 when its pixel is Gaussian, so
-    its time on the unit is 2 / (sin-or-cos rate) + f_gauss / (exp2 rate)."""
+def sfu_peak_measured(w, sfu, op="fwd"):
+    """The SFU bound of operator op on workload w from the measured MUFU rates
+    (Gpairs/s): a pair takes a sin and a cos (forward) or a cos (adjoint), and
+    an exp2 when its pixel is Gaussian, so its time on the unit is m / (sin-
+    or-cos rate) + f_gauss / (exp2 rate)."""
     kinds = np.zeros(w.n_pix, np.int32) if w.kind is None else np.asarray(w.kind)
     f_gauss = float(np.mean(kinds != 0))
-    t_pair = 2.0 / sfu["sincos_per_s"] + f_gauss / sfu["ex2_per_s"]
+    m = SFU_OPS_PER_PAIR[op]["dirac"]
+    t_pair = m / sfu["sincos_per_s"] + f_gauss / sfu["ex2_per_s"]
     per_clk_sm = {k: v / (N_SM * SM_MAX_MHZ * 1e6) for k, v in sfu.items()}
     return {"peak": 1.0 / t_pair / 1e9,
             "basis": "sl1m_measure_sfu: sin/cos and exp2 results per second on this GPU; "
-                     f"2 sin/cos + {f_gauss:.3g} exp2 per pair",
+                     f"{m} sin/cos + {f_gauss:.3g} exp2 per pair",
             "measured_per_s": sfu,
             "per_clk_per_sm_at_max_clock": per_clk_sm}
 
@@ -719,7 +731,8 @@ def main():
     dom = max(keys, key=lambda k: prof[k]["ms"])
     pd = prof[dom]
     achieved = pd["pairs"] / (pd["ms"] / 1e3) / 1e9 if pd["ms"] > 0 else 0.0
-    peak, peak_basis, alt = sfu_peak(w)
+    op_of = lambda k: "fwd" if k.startswith("fwd") else "adj"   # noqa: E731
+    peak, peak_basis, alt = sfu_peak(w, op_of(dom))
     traffic = None
     if tuned is not None:
         op = 0 if dom.startswith("fwd") else 1
@@ -735,14 +748,21 @@ def main():
     if alt:
         roofline["peak_sfu_plus_fma_sincos"] = alt
         roofline["frac_of_sfu_plus_fma_sincos"] = achieved / alt["peak"]
-    meas = sfu_peak_measured(w, sfu)
+    meas = sfu_peak_measured(w, sfu, op_of(dom))
     roofline["peak_measured_sfu"] = meas
     roofline["frac_of_measured_sfu"] = achieved / meas["peak"]
-    per_kernel = {k: {"launches": prof[k]["launches"], "launches_with_work": worked[k],
-                      "avg_launch_ms": prof[k]["ms"] / worked[k],
-                      "Gpairs_per_s": prof[k]["pairs"] / (prof[k]["ms"] / 1e3) / 1e9,
-                      "frac_of_peak": prof[k]["pairs"] / (prof[k]["ms"] / 1e3) / 1e9 / peak}
-                  for k in keys if prof[k]["ms"] > 0}
+    per_kernel = {}
+    for k in keys:
+        if prof[k]["ms"] <= 0:
+            continue
+        rate = prof[k]["pairs"] / (prof[k]["ms"] / 1e3) / 1e9
+        pk, _, pk_alt = sfu_peak(w, op_of(k))
+        per_kernel[k] = {"launches": prof[k]["launches"], "launches_with_work": worked[k],
+                         "avg_launch_ms": prof[k]["ms"] / worked[k], "Gpairs_per_s": rate,
+                         "sfu_peak": pk, "frac_of_peak": rate / pk,
+                         "frac_of_measured_sfu": rate / sfu_peak_measured(w, sfu, op_of(k))["peak"]}
+        if pk_alt:
+            per_kernel[k]["frac_of_sfu_plus_fma"] = rate / pk_alt["peak"]
     fin_ms = prof["fwd_finish"]["ms"] + prof["adj_finish"]["ms"]
     fin_bytes = prof["fwd_finish"]["bytes"] + prof["adj_finish"]["bytes"]
     vec = {"kernels": "fwd_finish+adj_finish (residual, threshold, momentum)",

@@ -22,9 +22,11 @@
  *     a host thread of its own; the caller's sl1m_server_* calls and
  *     sl1m_last_error may run meanwhile.
  *   - Precision: SL1M_FP64 evaluates every step in FP64 ("plain" path);
- *     SL1M_MIXED evaluates sincos/exp and the complex multiply-accumulates in
- *     FP32 after an exact FP32 reduction of the phase to fractional turns;
- *     sums over tiles, norms, step sizes and the projection stay in FP64.
+ *     SL1M_MIXED evaluates sincos/exp and the multiply-accumulates in FP32
+ *     after an exact FP32 reduction of the phase to fractional turns (the
+ *     adjoint, whose output is real, takes r and the gains in polar form and
+ *     one cosine per pair); sums over tiles, norms, step sizes and the
+ *     projection stay in FP64.
  */
 #ifndef SL1M_H
 #define SL1M_H
@@ -298,8 +300,8 @@ int sl1m_server_info(sl1m_ctx* ctx, sl1m_server_info_t* info);
  * granules per shared-memory stage: 2, 4 or 8; the adjoint 2 or 4) x
  * (persistent grid: 1 .. occupancy CTAs per SM) of the mixed no-gains
  * kernels, then for every stage count at its fastest grid the share npoly
- * (1 or 2 of every 8 pairs) whose sincos runs on the FMA pipe instead of the
- * SFU (each timed launch follows a launch of the other operator, as in a
+ * (1 or 2 of every 8 pairs) whose sincos (adjoint: cosine) runs on the FMA
+ * pipe instead of the SFU (each timed launch follows a launch of the other operator, as in a
  * solve); with gains or in FP64 only the grid is tuned.  The choice is kept in the context,
  * keyed by (precision, operator, gains, Gaussian pixels, log2 of the work
  * units); later launches of problems with the same key -- single solves and

@@ -148,8 +148,9 @@ struct DevProblem {
     const int* gkind;         // [pix.n_gran] kind per pixel granule
     const float4* pghdr;      // [pix.n_gran][4] centre hi, centre lo, extent, {sigma, kind, 0, 0}
     const float4* vgabs;      // [vis.n_pad] {u, v, -2 w, u^2 + v^2} in FP32 (the adjoint's Gaussian terms)
-    float2* r32;              // [vis.n_pad] the adjoint's input residual in FP32 (r32_kernel)
-    const float2* gains32;    // [pix.n_gran][gain_rows(n_ant)][GP] or null
+    float2* r32;              // [vis.n_pad] the mixed adjoint's input residual in polar form,
+                              // {|r|, arg r in turns} in FP32 (r32_kernel)
+    const float2* gpol32;     // [pix.n_gran][gain_rows(n_ant)][GP] {|G|, arg G in turns} or null
     const double2* gains64;   // [pix.n_pad][n_ant] or null
     int n_ant;
     // operator mode (st == null): one forward x -> fwd_out or adjoint r -> adj_out

@@ -74,6 +74,15 @@ __device__ __forceinline__ void sincos_fma(float ph, float& s, float& c)
     c = fmaf(-h, h, 1.0f);
 }
 
+// The cosine alone by the same interpolant (the adjoint needs no sine):
+// cos(2 pi f) = 1 - h^2.  11 FMA-pipe instructions.
+__device__ __forceinline__ float cos_fma(float ph)
+{
+    const float f = frac_turns(ph * INV_TWO_PI_F);
+    const float h = f * fmaf(fmaf(fmaf(fmaf(SCP4, f * f, SCP3), f * f, SCP2), f * f, SCP1), f * f, SCP0);
+    return fmaf(-h, h, 1.0f);
+}
+
 // ---- bulk (TMA) copies global -> shared, completed on an mbarrier
 __device__ __forceinline__ unsigned smem_u32(const void* p)
 {

@@ -471,7 +471,7 @@ struct ProblemDev {
     DBuf<double> gsig64;
     DBuf<int> gkind;
     DBuf<float4> pghdr;
-    DBuf<float2> gains32;
+    DBuf<float2> gpol32;
     DBuf<double2> gains64;
     // operator scratch
     DBuf<double> x_user, x_sorted, adj_sorted, img_user;
@@ -586,11 +586,12 @@ int sl1m_problem::rebuild(cudaStream_t st)
         gkind_pix = gk;
         pix_orig = H.orig;
         if (n_ant > 0) {
-            // FP32: per pixel granule one row of GP per antenna (gain_rows(n_ant)
-            // rows), the shared-memory layout, so a granule's table is one bulk
-            // copy; FP64: [pixel][antenna]
+            // FP32 in polar form {|G|, arg G in turns} (modulus and argument
+            // taken in FP64): per pixel granule one row of GP per antenna
+            // (gain_rows(n_ant) rows), the shared-memory layout, so a granule's
+            // table is one bulk copy; FP64: [pixel][antenna]
             const size_t tab = (size_t)gain_rows(n_ant) * GP;
-            std::vector<float2> g32((size_t)H.n_gran * tab, make_float2(0.f, 0.f));
+            std::vector<float2> gp32((size_t)H.n_gran * tab, make_float2(0.f, 0.f));
             std::vector<double2> g64((size_t)H.n_pad * n_ant, make_double2(0.0, 0.0));
             for (int t = 0; t < H.n_pad; ++t) {
                 const int o = H.orig[t];
@@ -598,14 +599,15 @@ int sl1m_problem::rebuild(cudaStream_t st)
                 const size_t row0 = (size_t)(t / G) * tab + (size_t)(t % G);
                 for (int a = 0; a < n_ant; ++a) {
                     const double re = gains[((size_t)o * n_ant + a) * 2], im = gains[((size_t)o * n_ant + a) * 2 + 1];
-                    g32[row0 + (size_t)a * GP] = make_float2((float)re, (float)im);
+                    gp32[row0 + (size_t)a * GP] =
+                        make_float2((float)std::hypot(re, im), (float)(std::atan2(im, re) / 6.283185307179586));
                     g64[(size_t)t * n_ant + a] = make_double2(re, im);
                 }
             }
-            CK(D.gains32.upload(g32.data(), g32.size(), st));
+            CK(D.gpol32.upload(gp32.data(), gp32.size(), st));
             CK(D.gains64.upload(g64.data(), g64.size(), st));
         } else {
-            D.gains32.free();
+            D.gpol32.free();
             D.gains64.free();
         }
     }
@@ -684,7 +686,7 @@ int sl1m_problem::rebuild(cudaStream_t st)
     hp.gsig64 = D.gsig64.p;
     hp.gkind = D.gkind.p;
     hp.pghdr = D.pghdr.p;
-    hp.gains32 = n_ant > 0 ? D.gains32.p : nullptr;
+    hp.gpol32 = n_ant > 0 ? D.gpol32.p : nullptr;
     hp.gains64 = n_ant > 0 ? D.gains64.p : nullptr;
     hp.n_ant = n_ant;
     hp.x = nullptr;
@@ -886,7 +888,7 @@ size_t sl1m_problem::dev_bytes() const
     side(D.vis);
     side(D.pix);
     b += D.ant.bytes() + D.vgabs.bytes() + D.r32.bytes() + D.vslot.bytes() + D.gbl.bytes() + D.gnb.bytes() + D.V.bytes() + D.pgauss.bytes() + D.pgauss64.bytes() + D.gsig.bytes() +
-         D.gsig64.bytes() + D.gkind.bytes() + D.pghdr.bytes() + D.gains32.bytes() + D.gains64.bytes();
+         D.gsig64.bytes() + D.gkind.bytes() + D.pghdr.bytes() + D.gpol32.bytes() + D.gains64.bytes();
     b += D.x_user.bytes() + D.x_sorted.bytes() + D.adj_sorted.bytes() + D.img_user.bytes() +
          D.r_user.bytes() + D.r_sorted.bytes() + D.fwd_sorted.bytes() + D.vis_user.bytes();
     b += D.I0.bytes() + D.I1.bytes() + D.y.bytes() + D.xv.bytes() + D.blk_r2.bytes() + D.blk_l1.bytes() +
@@ -1017,7 +1019,9 @@ static int launch_op_class(sl1m_ctx* ctx, Batch& B, int op, int c)
                               ctx->partial_f.p, st));
         prof_end(ctx, tk, 0.0, B.fin_bytes[0]);
     } else {
-        if (B.precision != 0 && c == 0) {         // the mixed no-gains adjoint reads r in FP32
+        // the mixed adjoints read r in polar form, written once for the whole
+        // batch before its first class
+        if (B.precision != 0 && (c == 0 || !B.has_class[0])) {
             int vmax = 1;
             for (const DevProblem& d : B.hdesc) vmax = std::max(vmax, d.vis.n_pad);
             CKL(launch_r32(B.desc.p, (int)B.hdesc.size(), vmax, st));

@@ -23,7 +23,9 @@
 // so B + D, at most 2 pi (1 + D_MAX) in size, goes to the SFU's sincos with
 // no reduction step of its own; on the exact path the fractional turns are
 // reduced exactly and then scaled.  sincos / exp2 run on the SFU in FP32;
-// each granule's FP32 sum is added into FP64 accumulators.
+// each granule's FP32 sum is added into FP64 accumulators.  The adjoint's
+// output is real, so it takes one cosine per pair: Re(conj(A) r) =
+// |A| |r| cos(arg r - arg A), with r and the gains held in polar form.
 //
 // Work split: a CTA owns BLK_GRAN granules of one side (one per warp, 2
 // elements per lane) and streams granules of the other side through shared
@@ -79,23 +81,28 @@ __device__ __forceinline__ void fwd_dirac_tile(const float4* __restrict__ s_off,
         const float4 ol = EXACT ? s_lo[j] : o;
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
+            // with gains {|G|, arg G in turns}: a G_a conj(G_b) e^{-i ph} =
+            // a |G_a| |G_b| e^{-i (ph + 2 pi (psi_b - psi_a))}
+            float2 ga = make_float2(1.f, 0.f), gb = ga;
+            if (GAINS) {
+                ga = ga_row[r][j];
+                gb = gb_row[r][j];
+            }
             float ph;                          // radians
-            if (EXACT) ph = frac_turns(fmaf(b, INV_TWO_PI_F, frac_dot3(dx[r], dxl[r], o, ol))) * TWO_PI_F;
-            else ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, b)));   // dx in radians
+            if (EXACT) {
+                ph = frac_dot3(dx[r], dxl[r], o, ol);
+                if (GAINS) ph += gb.y - ga.y;
+                ph = frac_turns(fmaf(b, INV_TWO_PI_F, ph)) * TWO_PI_F;
+            } else {
+                const float b0 = GAINS ? fmaf(gb.y - ga.y, TWO_PI_F, b) : b;
+                ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, b0)));   // dx in radians
+            }
             float sn, cs;
             if (!EXACT && fma_slot<NPOLY>(jj, r)) sincos_fma(ph, sn, cs);
             else __sincosf(ph, &sn, &cs);
-            if (GAINS) {
-                const float2 ga = ga_row[r][j];
-                const float2 gb = gb_row[r][j];
-                const float gr = fmaf(ga.x, gb.x, ga.y * gb.y);    // G_a conj(G_b)
-                const float gi = fmaf(ga.y, gb.x, -ga.x * gb.y);
-                sr[r] = fmaf(ba.y, fmaf(gr, cs, gi * sn), sr[r]);    // a g (cs - i sn)
-                si[r] = fmaf(ba.y, fmaf(gi, cs, -gr * sn), si[r]);
-            } else {
-                sr[r] = fmaf(ba.y, cs, sr[r]);
-                si[r] = fmaf(-ba.y, sn, si[r]);
-            }
+            const float m = GAINS ? ba.y * (ga.x * gb.x) : ba.y;
+            sr[r] = fmaf(m, cs, sr[r]);
+            si[r] = fmaf(-m, sn, si[r]);
         }
     }
 }
@@ -123,40 +130,45 @@ __device__ __forceinline__ void fwd_gauss_tile(const float4* __restrict__ s_off,
         for (int r = 0; r < 2; ++r) {
             const float uf = xh[r].x, vf = xh[r].y, wf = xh[r].z;
             const float t = fmaf(uf, pg.x, fmaf(vf, pg.y, -wf * pg.z));
+            float2 ga = make_float2(1.f, 0.f), gb = ga;      // gains {|G|, arg G in turns}
+            if (GAINS) {
+                ga = ga_row[r][j];
+                gb = gb_row[r][j];
+            }
             float ph;                          // radians
             if (EXACT) {
                 ph = fmaf(b, INV_TWO_PI_F, frac_dot3(dx[r], dxl[r], o, ol));
+                if (GAINS) ph += gb.y - ga.y;
                 ph = fmaf(-gc[r].gamr * INV_TWO_PI_F, t, ph);
                 if (PAR) ph = fmaf(-wf, pg.w, ph);
                 ph = frac_turns(ph) * TWO_PI_F;
             } else {
-                ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, b)));
+                const float b0 = GAINS ? fmaf(gb.y - ga.y, TWO_PI_F, b) : b;
+                ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, b0)));
                 ph = fmaf(-gc[r].gamr, t, ph);
                 if (PAR) ph = fmaf(-wf * TWO_PI_F, pg.w, ph);
             }
             float sn, cs;
             __sincosf(ph, &sn, &cs);
-            const float amp = ba.y * ex2_approx(fmaf(gc[r].k1, t, gc[r].k0));   // (x/n) e^{Re(qc)}
-            if (GAINS) {
-                const float2 ga = ga_row[r][j];
-                const float2 gb = gb_row[r][j];
-                const float gr = fmaf(ga.x, gb.x, ga.y * gb.y);
-                const float gi = fmaf(ga.y, gb.x, -ga.x * gb.y);
-                sr[r] = fmaf(amp, fmaf(gr, cs, gi * sn), sr[r]);
-                si[r] = fmaf(amp, fmaf(gi, cs, -gr * sn), si[r]);
-            } else {
-                sr[r] = fmaf(amp, cs, sr[r]);
-                si[r] = fmaf(-amp, sn, si[r]);
-            }
+            float amp = ba.y * ex2_approx(fmaf(gc[r].k1, t, gc[r].k0));   // (x/n) e^{Re(qc)}
+            if (GAINS) amp *= ga.x * gb.x;
+            sr[r] = fmaf(amp, cs, sr[r]);
+            si[r] = fmaf(-amp, sn, si[r]);
         }
     }
 }
 
 // ---- forward with gains through the granule's pair table
-// T[s][jj] = a_j G_{j a_s} conj(G_{j b_s}) (a_j = x_j / n_j, j = c0 + jj) for
-// the nb distinct antenna pairs (a_s, b_s) of the warp's visibility granule
-// and BT_CH pixels of the streamed granule; rows of BT_P, so the lanes of a
-// half-warp (one pair, consecutive pixels) write distinct banks.
+// For the nb distinct antenna pairs (a_s, b_s) of the warp's visibility
+// granule and BT_CH pixels j = c0 + jj of the streamed granule, the table
+// holds a_j G_{j a_s} conj(G_{j b_s}) e^{-i B_j} (a_j = x_j / n_j) in polar
+// form: T[s][jj] = {B_j - arg (radians, within one turn), |a_j G G|} (Dirac
+// pixels) or {.., log2 |a_j G G|} (Gaussian pixels, for the amplitude's
+// exponent).  A pair then starts its phase from the table entry, needs no B_j
+// of its own, and accumulates with two FFMA.  Rows of BT_P, so the lanes of a
+// half-warp (one pair, consecutive pixels) write distinct banks.  gtab: the
+// gains in polar form {|G|, arg G in turns}.
+template <bool LOG>
 __device__ __forceinline__ void build_pair_table(float2* __restrict__ T, const int2* __restrict__ bl, int nb,
                                                  const float2* __restrict__ sBa,
                                                  const float2* __restrict__ gtab, int c0, int lane)
@@ -165,14 +177,15 @@ __device__ __forceinline__ void build_pair_table(float2* __restrict__ T, const i
         const int s = e / BT_CH, jj = e % BT_CH, j = c0 + jj;
         const int2 ab = bl[s];
         const float2 ga = gtab[ab.x * GP + j], gb = gtab[ab.y * GP + j];
-        const float a = sBa[j].y;
-        T[s * BT_P + jj] = make_float2(a * fmaf(ga.x, gb.x, ga.y * gb.y), a * fmaf(ga.y, gb.x, -ga.x * gb.y));
+        const float2 ba = sBa[j];                                    // {B_j (radians), a_j}
+        // arg of a G_a conj(G_b) in turns: psi_a - psi_b (+ 1/2 when a_j < 0)
+        const float arg = (ga.y - gb.y) + (ba.y < 0.f ? 0.5f : 0.f);
+        const float ph = frac_turns(fmaf(ba.x, INV_TWO_PI_F, -arg)) * TWO_PI_F;
+        const float m = fabsf(ba.y) * (ga.x * gb.x);
+        T[s * BT_P + jj] = make_float2(ph, LOG ? __log2f(m) : m);   // log2(0) = -inf: amplitude 0
     }
 }
 
-// Dirac tile with gains from the pair table: per pair one table load (the
-// visibility's row toff = slot * BT_P) replaces two gathers and the complex
-// product of the gains.
 template <bool EXACT>
 __device__ __forceinline__ void fwd_dirac_tile_pt(const float4* __restrict__ s_off,
                                                   const float4* __restrict__ s_lo,
@@ -182,37 +195,28 @@ __device__ __forceinline__ void fwd_dirac_tile_pt(const float4* __restrict__ s_o
                                                   const float4 (&dx)[2], const float4 (&dxl)[2], int lane,
                                                   float (&sr)[2], float (&si)[2])
 {
-    float sr2[2] = {0.f, 0.f}, si2[2] = {0.f, 0.f};   // second accumulators: one FFMA deep each
 #pragma unroll 1
     for (int c0 = 0; c0 < G; c0 += BT_CH) {
-        build_pair_table(T, bl, nb, sBa, gtab, c0, lane);
+        build_pair_table<false>(T, bl, nb, sBa, gtab, c0, lane);
         __syncwarp();
 #pragma unroll 8
         for (int jj = 0; jj < BT_CH; ++jj) {
             const int j = c0 + jj;
             const float4 o = s_off[j];
-            const float b = sBa[j].x;
             const float4 ol = EXACT ? s_lo[j] : o;
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
+                const float2 t = T[toff[r] + jj];                      // {B - arg, |a g|}
                 float ph;
-                if (EXACT) ph = frac_turns(fmaf(b, INV_TWO_PI_F, frac_dot3(dx[r], dxl[r], o, ol))) * TWO_PI_F;
-                else ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, b)));
+                if (EXACT) ph = frac_turns(fmaf(t.x, INV_TWO_PI_F, frac_dot3(dx[r], dxl[r], o, ol))) * TWO_PI_F;
+                else ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, t.x)));
                 float sn, cs;
                 __sincosf(ph, &sn, &cs);
-                const float2 t = T[toff[r] + jj];                      // a g
-                sr[r] = fmaf(t.x, cs, sr[r]);
-                sr2[r] = fmaf(t.y, sn, sr2[r]);
-                si[r] = fmaf(t.y, cs, si[r]);
-                si2[r] = fmaf(-t.x, sn, si2[r]);
+                sr[r] = fmaf(t.y, cs, sr[r]);
+                si[r] = fmaf(-t.y, sn, si[r]);
             }
         }
         __syncwarp();                                                  // table free for the next chunk
-    }
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        sr[r] += sr2[r];
-        si[r] += si2[r];
     }
 }
 
@@ -227,50 +231,40 @@ __device__ __forceinline__ void fwd_gauss_tile_pt(const float4* __restrict__ s_o
                                                   const float4 (&dxl)[2], const GaussConst (&gc)[2], int lane,
                                                   float (&sr)[2], float (&si)[2])
 {
-    float sr2[2] = {0.f, 0.f}, si2[2] = {0.f, 0.f};   // second accumulators: one FFMA deep each
 #pragma unroll 1
     for (int c0 = 0; c0 < G; c0 += BT_CH) {
-        build_pair_table(T, bl, nb, sBa, gtab, c0, lane);
+        build_pair_table<true>(T, bl, nb, sBa, gtab, c0, lane);
         __syncwarp();
 #pragma unroll 4
         for (int jj = 0; jj < BT_CH; ++jj) {
             const int j = c0 + jj;
             const float4 o = s_off[j];
             const float4 pg = s_pg[j];
-            const float b = sBa[j].x;
             const float4 ol = EXACT ? s_lo[j] : o;
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
+                const float2 tv = T[toff[r] + jj];                     // {B - arg, log2 |a g|}
                 const float wf = xh[r].z;
                 const float t = fmaf(xh[r].x, pg.x, fmaf(xh[r].y, pg.y, -wf * pg.z));
                 float ph;
                 if (EXACT) {
-                    ph = fmaf(b, INV_TWO_PI_F, frac_dot3(dx[r], dxl[r], o, ol));
+                    ph = fmaf(tv.x, INV_TWO_PI_F, frac_dot3(dx[r], dxl[r], o, ol));
                     ph = fmaf(-gc[r].gamr * INV_TWO_PI_F, t, ph);
                     if (PAR) ph = fmaf(-wf, pg.w, ph);
                     ph = frac_turns(ph) * TWO_PI_F;
                 } else {
-                    ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, b)));
+                    ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, tv.x)));
                     ph = fmaf(-gc[r].gamr, t, ph);
                     if (PAR) ph = fmaf(-wf * TWO_PI_F, pg.w, ph);
                 }
                 float sn, cs;
                 __sincosf(ph, &sn, &cs);
-                const float amp = ex2_approx(fmaf(gc[r].k1, t, gc[r].k0));   // e^{Re(qc)}; a is in T
-                const float2 tv = T[toff[r] + jj];
-                const float ca = amp * cs, sa = amp * sn;
-                sr[r] = fmaf(tv.x, ca, sr[r]);
-                sr2[r] = fmaf(tv.y, sa, sr2[r]);
-                si[r] = fmaf(tv.y, ca, si[r]);
-                si2[r] = fmaf(-tv.x, sa, si2[r]);
+                const float amp = ex2_approx(fmaf(gc[r].k1, t, gc[r].k0 + tv.y));   // |a g| e^{Re(qc)}
+                sr[r] = fmaf(amp, cs, sr[r]);
+                si[r] = fmaf(-amp, sn, si[r]);
             }
         }
         __syncwarp();
-    }
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        sr[r] += sr2[r];
-        si[r] += si2[r];
     }
 }
 
@@ -415,9 +409,9 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                     const int b = gdbl ? gcur : 0;
                     fence_proxy_async_smem();
                     if (gs == g0 || !gdbl)
-                        bulk_load(s_gain + b * gtab_n, P.gains32 + (size_t)gs * gtab_n, gbytes, &s_gbar[b]);
+                        bulk_load(s_gain + b * gtab_n, P.gpol32 + (size_t)gs * gtab_n, gbytes, &s_gbar[b]);
                     if (gdbl && gs + 1 < g1)      // prefetch the next granule's table
-                        bulk_load(s_gain + (b ^ 1) * gtab_n, P.gains32 + (size_t)(gs + 1) * gtab_n, gbytes,
+                        bulk_load(s_gain + (b ^ 1) * gtab_n, P.gpol32 + (size_t)(gs + 1) * gtab_n, gbytes,
                                   &s_gbar[b ^ 1]);
                 }
             }
@@ -549,136 +543,125 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
 }
 
 // ----------------------------------------------------------- adjoint tiles
+// The adjoint's output is real (the image is real: its gradient is Re A^H r),
+// and for one pair Re(conj(A_kj) r_k) = |r_k| cos(theta_kj + arg r_k): a cosine alone, not
+// a sine and a cosine.  r32_kernel writes r in polar form {|r|, arg r in
+// turns}; when a stage is derived, arg r_k is added to the visibility's B term
+// (so theta + arg r costs nothing per pair) and |r_k| rides in the same record
+// (Gaussian owners: log2 |r'_k| inside the amplitude's exponent).
+// With weights that are all positive, a bias of the SFU's cosine would add
+// up over the N_v terms of a sum (where a sine and a cosine weighted by Re r
+// and Im r of either sign cancel it), so every odd visibility k takes
+// -cos(theta + pi) instead: its record carries B + arg r + 1/2 turn and the
+// tile subtracts its term (odd_turn, the sign free in the FFMA).
 
-// Gain of owned pixel r (0/1 of this lane) at antenna a.
-struct NoGain {
-    __device__ float2 operator()(int, int) const { return make_float2(1.f, 0.f); }
-};
-// gains in shared memory, [antenna][pixel of the owned granule], rows of GP
+// Half a turn for an odd streamed visibility k (see above).
+__device__ __forceinline__ float odd_turn(int k) { return (k & 1) ? 0.5f : 0.f; }
+
+// Gain of owned pixel r (0/1 of this lane) at antenna a: gains in shared
+// memory, [antenna][pixel of the owned granule], rows of GP.
 struct SmemGain {
     const float2* tab;
     int lane;
     __device__ float2 operator()(int a, int r) const { return tab[a * GP + lane + 32 * r]; }
 };
 
-// With gains the streamed visibilities of a granule are sorted by antenna
-// pair and carry the pair as key = a << 16 | b (in the w slot of their
-// offsets, which the adjoint does not otherwise use): g[r] = G_ja conj(G_jb)
-// for the lane's two pixels is formed once per run of equal pairs.
-template <class GF>
-__device__ __forceinline__ void pair_gains(int key, int& cur, const GF& gain, float2 (&g)[2])
-{
-    if (key == cur) return;                       // warp-uniform: every lane has the same k
-    cur = key;
-    const int a = key >> 16, b = key & 0xffff;
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const float2 ga = gain(a, r), gb = gain(b, r);
-        g[r] = make_float2(fmaf(ga.x, gb.x, ga.y * gb.y), fmaf(ga.y, gb.x, -ga.x * gb.y));
-    }
-}
-
-template <bool GAINS, bool EXACT, class GF, int NPOLY = 0>
+// Dirac owners.  rec[k] = {B_k + arg r_k (radians), |r_k|, -, -}.
+template <bool EXACT, int NPOLY = 0>
 __device__ __forceinline__ void adj_dirac_tile(const float4* __restrict__ s_off,
                                                const float4* __restrict__ s_lo,
-                                               const float2* __restrict__ s_r,
-                                               const float* __restrict__ sB, const GF& gain,
+                                               const float4* __restrict__ s_rec,
                                                const float (&C)[2],
                                                const float4 (&dx)[2], const float4 (&dxl)[2],
                                                float (&acc)[2])
 {
-    int cur = -1;                    // GAINS: key of the antenna pair whose products g holds
-    float2 g[2];
 #pragma unroll 2
     for (int k0 = 0; k0 < G; k0 += 4)
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
         const int k = k0 + kk;
         const float4 o = s_off[k];             // {du, dv, dw, W}
-        const float b = sB[k];
-        const float2 rr = s_r[k];
+        const float2 br = *reinterpret_cast<const float2*>(s_rec + k);
         const float4 ol = EXACT ? s_lo[k] : o;
-        if (GAINS) pair_gains(__float_as_int(o.w), cur, gain, g);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             float ph;                                  // radians; C and dx in radians unless EXACT
-            if (EXACT) ph = frac_turns((C[r] + b * INV_TWO_PI_F) + frac_dot3(dx[r], dxl[r], o, ol)) * TWO_PI_F;
-            else ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, C[r] + b)));
-            float sn, cs;
-            if (!EXACT && fma_slot<NPOLY>(kk, r)) sincos_fma(ph, sn, cs);
-            else __sincosf(ph, &sn, &cs);                 // exp(+i ph) = cs + i sn
-            if (GAINS) {
-                const float zr = fmaf(cs, rr.x, -sn * rr.y);
-                const float zi = fmaf(cs, rr.y, sn * rr.x);
-                acc[r] = fmaf(g[r].x, zr, fmaf(g[r].y, zi, acc[r]));  // Re(conj(g) z)
-            } else {
-                acc[r] = fmaf(cs, rr.x, fmaf(-sn, rr.y, acc[r]));
-            }
+            if (EXACT) ph = frac_turns((C[r] + br.x * INV_TWO_PI_F) + frac_dot3(dx[r], dxl[r], o, ol)) * TWO_PI_F;
+            else ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, C[r] + br.x)));
+            const float cs = (!EXACT && fma_slot<NPOLY>(kk, r)) ? cos_fma(ph) : __cosf(ph);
+            acc[r] = fmaf((kk & 1) ? -br.y : br.y, cs, acc[r]);   // odd k: -cos(theta + pi)
         }
     }
 }
 
-template <bool GAINS, bool EXACT, bool PAR, class GF>
+// Gaussian owners.  va[k] = {u, v, -2 w, u^2 + v^2}; rec[k] = {B_k + arg r'_k
+// (radians), gamr, k1, k0 + log2 |r'_k|}: the amplitude times |r'| is
+// 2^(k1 t + k0'), t = u l + v m - w r^2/2.
+template <bool EXACT, bool PAR>
 __device__ __forceinline__ void adj_gauss_tile(const float4* __restrict__ s_off,
                                                const float4* __restrict__ s_lo,
                                                const float4* __restrict__ s_abs,
-                                               const float* __restrict__ sB,
-                                               const float4* __restrict__ s_gw, const GF& gain,
+                                               const float4* __restrict__ s_rec,
                                                const float (&C)[2],
                                                const float4 (&dx)[2], const float4 (&dxl)[2],
                                                const float4 (&pgd)[2], float (&acc)[2])
 {
-    int cur = -1;                    // GAINS: key of the antenna pair whose products g holds
-    float2 g[2];
-#pragma unroll 2
-    for (int k = 0; k < G; ++k) {
+#pragma unroll 1
+    for (int k0 = 0; k0 < G; k0 += 2)
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+        const int k = k0 + kk;
         const float4 o = s_off[k];
-        const float4 va = s_abs[k];            // {u, v, -2 w, u^2 + v^2}
-        const float4 gw = s_gw[k];             // {gamr, coef, r're, r'im}
-        const float b = sB[k];
+        const float4 va = s_abs[k];
+        const float4 rc = s_rec[k];
         const float4 ol = EXACT ? s_lo[k] : o;
-        if (GAINS) pair_gains(__float_as_int(o.w), cur, gain, g);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             // pgd = {l, m, r^2/4, pi nu}: t = u l + v m - w r^2/2
             const float t = fmaf(va.x, pgd[r].x, fmaf(va.y, pgd[r].y, va.z * pgd[r].z));
             float ph;                                  // radians; C and dx in radians unless EXACT
             if (EXACT) {
-                ph = (C[r] + b * INV_TWO_PI_F) + frac_dot3(dx[r], dxl[r], o, ol);
-                ph = fmaf(-gw.x * INV_TWO_PI_F, t, ph);
+                ph = (C[r] + rc.x * INV_TWO_PI_F) + frac_dot3(dx[r], dxl[r], o, ol);
+                ph = fmaf(-rc.y * INV_TWO_PI_F, t, ph);
                 if (PAR) ph = fmaf(va.z, pgd[r].w * INV_TWO_PI_F, ph);   // -w nu, turns
                 ph = frac_turns(ph) * TWO_PI_F;
             } else {
-                ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, C[r] + b)));
-                ph = fmaf(-gw.x, t, ph);
+                ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, C[r] + rc.x)));
+                ph = fmaf(-rc.y, t, ph);
                 if (PAR) ph = fmaf(va.z, pgd[r].w, ph);                  // -2 pi w nu
             }
-            float sn, cs;
-            __sincosf(ph, &sn, &cs);
-            const float amp = ex2_approx(gw.y * fmaf(va.z, t, va.w));   // coef |(u,v) - w (l,m)|^2
-            const float zr = fmaf(cs, gw.z, -sn * gw.w);
-            if (GAINS) {
-                const float zi = fmaf(cs, gw.w, sn * gw.z);
-                acc[r] = fmaf(amp, fmaf(g[r].x, zr, g[r].y * zi), acc[r]);
-            } else {
-                acc[r] = fmaf(amp, zr, acc[r]);
-            }
+            const float amp = ex2_approx(fmaf(rc.z, t, rc.w));          // |r'| e^{Re(qc)}
+            acc[r] = fmaf(kk ? -amp : amp, __cosf(ph), acc[r]);           // odd k: -cos(theta + pi)
         }
     }
+}
+
+// The record of a streamed visibility for a Gaussian owner of scale sigma:
+// r' = id (1 - i beta) r has |r'| = |r| / sqrt(1 + beta^2) and arg r' =
+// arg r - atan(beta) (id > 0).  b: the visibility's B term in turns, with
+// odd_turn's half turn for odd k; rp = {|r|, arg r in turns}; va = {u, v, -2 w,
+// -}.  Returns {B + arg r' (radians), gamr, k1, k0 + log2 |r'|}.
+__device__ __forceinline__ float4 adj_gauss_record(float b, float2 rp, const float4 va, float sigma)
+{
+    const GaussConst gc = gauss_const(va.x, va.y, -0.5f * va.z, sigma);
+    b = frac_turns(b + gc.cphase);
+    b = frac_turns(b + fmaf(-atanf(gc.beta), INV_TWO_PI_F, rp.y));
+    const float lgr = __log2f(rp.x) - 0.5f * __log2f(fmaf(gc.beta, gc.beta, 1.0f));   // -inf when r = 0
+    return make_float4(b * TWO_PI_F, gc.gamr, gc.k1, gc.k0 + lgr);
 }
 
 // Adjoint stage buffers in dynamic shared memory: two of them, each holding
 // NSA streamed visibility granules as they sit in HBM -- offsets, offset
 // residuals, the Gaussian form {u, v, -2 w, u^2 + v^2}, the residual r in
-// FP32 (written by r32_kernel just before the launch) and the granule centres
-// and extents -- filled by bulk (TMA) copies on one mbarrier per buffer; the
-// copies of stage s + 1 are issued when stage s starts.
+// polar form (written by r32_kernel just before the launch) and the granule
+// centres and extents -- filled by bulk (TMA) copies on one mbarrier per
+// buffer; the copies of stage s + 1 are issued when stage s starts.
 template <int NSA>
 struct AdjStage {
     static constexpr int OFF = 0;                      // float4 [NSA][G]
     static constexpr int LO = OFF + NSA * G * 16;      // float4 [NSA][G]
     static constexpr int GA = LO + NSA * G * 16;       // float4 [NSA][G]
-    static constexpr int R = GA + NSA * G * 16;        // float2 [NSA][G]
+    static constexpr int R = GA + NSA * G * 16;        // float2 [NSA][G] {|r|, arg r in turns}
     static constexpr int CEN = R + NSA * G * 8;        // float4 [3][NSA]: centre hi, centre lo, extent
     static constexpr int BYTES = CEN + 48 * NSA;       // a multiple of 16
 };
@@ -710,8 +693,9 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
 {
     using S = AdjStage<NSA>;
     extern __shared__ __align__(128) unsigned char s_dyn[];    // two stage buffers
-    __shared__ float s_B[BLK_GRAN][NSA][G];
-    __shared__ float4 s_gw[BLK_GRAN][NSA][G];   // Gaussian owners: {gamr, coef, r're, r'im}
+    // per warp, the streamed visibilities' records for its owned granule:
+    // Dirac {B + arg r (radians), |r|, -, -}, Gaussian adj_gauss_record's
+    __shared__ float4 s_rec[BLK_GRAN][NSA][G];
     __shared__ __align__(8) unsigned long long s_sbar[2];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -791,17 +775,10 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int k = lane + 32 * h;
-                    float b = frac_dot3(ch, cl, b_off[q * G + k], b_lo[q * G + k]);
-                    if (gauss) {
-                        const float4 va = b_ga[q * G + k];
-                        const GaussConst gc = gauss_const(va.x, va.y, -0.5f * va.z, sigma);
-                        b = frac_turns(b + gc.cphase);
-                        const float2 rr = b_r[q * G + k];
-                        // r' = id (1 - i beta) r
-                        s_gw[warp][q][k] = make_float4(gc.gamr, gc.coef, gc.id * fmaf(gc.beta, rr.y, rr.x),
-                                                       gc.id * fmaf(-gc.beta, rr.x, rr.y));
-                    }
-                    s_B[warp][q][k] = b * TWO_PI_F;           // radians
+                    const float b = frac_dot3(ch, cl, b_off[q * G + k], b_lo[q * G + k]) + odd_turn(k);
+                    const float2 rp = b_r[q * G + k];
+                    s_rec[warp][q][k] = gauss ? adj_gauss_record(b, rp, b_ga[q * G + k], sigma)
+                                              : make_float4(frac_turns(b + rp.y) * TWO_PI_F, rp.x, 0.f, 0.f);
                 }
             }
             __syncwarp();
@@ -813,28 +790,27 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
                 for (int r = 0; r < 2; ++r) C[r] = frac_dot3(xh[r], P.pix.lo[eidx[r]], yc_h, yc_l);
                 const float Cr[2] = {C[0] * TWO_PI_F, C[1] * TWO_PI_F};
                 float acc[2] = {0.f, 0.f};
-                const NoGain ng;
+                const float4* q_off = b_off + q * G;
+                const float4* q_lo = b_lo + q * G;
+                const float4* q_ga = b_ga + q * G;
+                const float4* q_rec = s_rec[warp][q];
                 if (!gauss) {
                     if (exact) {
                         const float4 dxt[2] = {P.pix.off[eidx[0]], P.pix.off[eidx[1]]},
-                                 dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
-                        adj_dirac_tile<false, true>(b_off + q * G, b_lo + q * G, b_r + q * G, s_B[warp][q], ng, C, dxt,
-                                                    dxl, acc);
+                                     dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
+                        adj_dirac_tile<true>(q_off, q_lo, q_rec, C, dxt, dxl, acc);
                     } else {
-                        adj_dirac_tile<false, false, NoGain, NPOLY>(b_off + q * G, b_lo + q * G, b_r + q * G, s_B[warp][q],
-                                                                    ng, Cr, dx,
-                                                     dx, acc);
+                        adj_dirac_tile<false, NPOLY>(q_off, q_lo, q_rec, Cr, dx, dx, acc);
                     }
+                } else if (exact) {
+                    const float4 dxt[2] = {P.pix.off[eidx[0]], P.pix.off[eidx[1]]},
+                                 dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
+                    if (par) adj_gauss_tile<true, true>(q_off, q_lo, q_ga, q_rec, C, dxt, dxl, pgd, acc);
+                    else adj_gauss_tile<true, false>(q_off, q_lo, q_ga, q_rec, C, dxt, dxl, pgd, acc);
+                } else if (par) {
+                    adj_gauss_tile<false, true>(q_off, q_lo, q_ga, q_rec, Cr, dx, dx, pgd, acc);
                 } else {
-                    if (exact) {
-                        const float4 dxt[2] = {P.pix.off[eidx[0]], P.pix.off[eidx[1]]},
-                                 dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
-                        if (par) adj_gauss_tile<false, true, true>(b_off + q * G, b_lo + q * G, b_ga + q * G, s_B[warp][q], s_gw[warp][q], ng, C, dxt, dxl, pgd, acc);
-                        else adj_gauss_tile<false, true, false>(b_off + q * G, b_lo + q * G, b_ga + q * G, s_B[warp][q], s_gw[warp][q], ng, C, dxt, dxl, pgd, acc);
-                    } else {
-                        if (par) adj_gauss_tile<false, false, true>(b_off + q * G, b_lo + q * G, b_ga + q * G, s_B[warp][q], s_gw[warp][q], ng, Cr, dx, dx, pgd, acc);
-                        else adj_gauss_tile<false, false, false>(b_off + q * G, b_lo + q * G, b_ga + q * G, s_B[warp][q], s_gw[warp][q], ng, Cr, dx, dx, pgd, acc);
-                    }
+                    adj_gauss_tile<false, false>(q_off, q_lo, q_ga, q_rec, Cr, dx, dx, pgd, acc);
                 }
 #pragma unroll
                 for (int r = 0; r < 2; ++r) tot[r] += (double)acc[r];
@@ -853,120 +829,116 @@ adj_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
 
 // ---- adjoint tiles with gains
 // A streamed visibility granule's members are sorted by antenna pair, so for
-// an owned pixel j each pair s = (a, b) is one run of visibilities k.  Their
-// contribution is  Re( conj(g_js) e^{2 pi i C} sum_{k in s} e^{i theta_jk} r_k )
-// with g_js = G_ja conj(G_jb), C the tile's centre term and theta = 2 pi (B + D)
-// (+ the Gaussian terms): the run is summed as a complex number z, and at the
-// run's end acc += Re(w z) with w = conj(g) e^{2 pi i C} formed once per run.
-// Per record k: off = {du, dv, dw, B in radians}, rk = {r (or the Gaussian
-// r' = id (1 - i beta) r), pair key a << 16 | b, 0}; Gaussian owners also read
-// va = {u, v, -2 w, gam in radians} and kk = {k1, k0}, the amplitude being
-// 2^(k1 t + k0) with t = u l + v m - w r^2/2.
+// an owned pixel j each pair s = (a, b) is one run of visibilities k.  With
+// g_js = G_ja conj(G_jb) = M e^{2 pi i (psi_a - psi_b)} (psi = arg G in
+// turns), r_k = |r_k| e^{2 pi i rho_k} and C the tile's centre term, the run
+// adds
+//   Re( conj(g_js) e^{2 pi i C} sum_{k in s} e^{i theta_jk} r_k )
+//     = M sum_{k in s} |r_k| cos(theta_jk + 2 pi (rho_k + Phi)),
+// Phi = C + psi_b - psi_a, theta = 2 pi (B + D) (+ the Gaussian terms): rho_k
+// sits in the record's B term, Phi is formed once per run from the gains in
+// polar form, and M multiplies the run's sum z at the run's end.
+// Per record k: off = {du, dv, dw, B + rho (radians)}, kr = {pair key a << 16
+// | b, |r| (Dirac owners) or k0 + log2 |r'| (Gaussian owners), k1, 0};
+// Gaussian owners also read va = {u, v, -2 w, gam in radians}, the amplitude
+// times |r'| being 2^(k1 t + k0') with t = u l + v m - w r^2/2.
 
-// Add the run held in (zr, zi) with weight w into acc: acc += Re(w z).
-__device__ __forceinline__ void adjg_flush(const float2 (&w)[2], float (&zr)[2], float (&zi)[2], float (&acc)[2])
+// The run held in z, of magnitude M, into acc: acc += M z.
+__device__ __forceinline__ void adjg_flush(const float (&M)[2], float (&z)[2], float (&acc)[2])
 {
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-        acc[r] = fmaf(w[r].x, zr[r], fmaf(-w[r].y, zi[r], acc[r]));
-        zr[r] = 0.f;
-        zi[r] = 0.f;
+        acc[r] = fmaf(M[r], z[r], acc[r]);
+        z[r] = 0.f;
     }
 }
 
 // At a new pair `key` (antenna indices a = key >> 16, b = key & 0xffff, both
-// valid): flush the run so far, then w = conj(G_ja conj(G_jb)) (cC + i sC) for
-// the lane's two pixels.
-template <class GF>
-__device__ __forceinline__ void adjg_next_run(int key, int& cur, const GF& gain, const float (&cC)[2],
-                                              const float (&sC)[2], float2 (&w)[2], float (&zr)[2],
-                                              float (&zi)[2], float (&acc)[2])
+// valid): flush the run so far, then M = |G_ja| |G_jb| and Phi = C + psi_jb -
+// psi_ja (radians; turns when EXACT) for the lane's two pixels, Ct = C in
+// turns.
+template <bool EXACT, class GF>
+__device__ __forceinline__ void adjg_next_run(int key, int& cur, const GF& gain, const float (&Ct)[2],
+                                              float (&M)[2], float (&Phi)[2], float (&z)[2], float (&acc)[2])
 {
     if (key == cur) return;                       // warp-uniform: every lane has the same k
-    adjg_flush(w, zr, zi, acc);
+    adjg_flush(M, z, acc);
     cur = key;
     const int a = key >> 16, b = key & 0xffff;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-        const float2 ga = gain(a, r), gb = gain(b, r);
-        const float gr = fmaf(ga.x, gb.x, ga.y * gb.y), gi = fmaf(ga.y, gb.x, -ga.x * gb.y);   // G_a conj(G_b)
-        w[r] = make_float2(fmaf(gr, cC[r], gi * sC[r]), fmaf(gr, sC[r], -gi * cC[r]));         // conj(g) e^{iC}
+        const float2 ga = gain(a, r), gb = gain(b, r);   // {|G|, arg G in turns}
+        M[r] = ga.x * gb.x;
+        const float f = frac_turns(Ct[r] + (gb.y - ga.y));
+        Phi[r] = EXACT ? f : f * TWO_PI_F;
     }
 }
 
 template <bool EXACT, class GF>
 __device__ __forceinline__ void adjg_dirac_tile(const float4* __restrict__ s_off, const float4* __restrict__ g_lo,
-                                                const float4* __restrict__ s_rk, const GF& gain,
-                                                const float (&cC)[2], const float (&sC)[2],
-                                                const float4 (&dx)[2], const float4 (&dxl)[2], float (&acc)[2])
+                                                const float4* __restrict__ s_kr, const GF& gain,
+                                                const float (&Ct)[2], const float4 (&dx)[2],
+                                                const float4 (&dxl)[2], float (&acc)[2])
 {
     int cur = -1;
-    float2 w[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-    float zr[2] = {0.f, 0.f}, zi[2] = {0.f, 0.f};
+    float M[2] = {0.f, 0.f}, Phi[2] = {0.f, 0.f}, z[2] = {0.f, 0.f};
 #pragma unroll 1
     for (int k0 = 0; k0 < G; k0 += 4)
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
         const int k = k0 + kk;
         const float4 o = s_off[k];
-        const float4 rk = s_rk[k];
-        adjg_next_run(__float_as_int(rk.z), cur, gain, cC, sC, w, zr, zi, acc);
+        const float2 kr = *reinterpret_cast<const float2*>(s_kr + k);   // {key, |r|}
+        adjg_next_run<EXACT>(__float_as_int(kr.x), cur, gain, Ct, M, Phi, z, acc);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             float ph;                              // radians
-            if (EXACT) ph = frac_turns(o.w * INV_TWO_PI_F + frac_dot3(dx[r], dxl[r], o, g_lo[k])) * TWO_PI_F;
-            else ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, o.w)));
-            float sn, cs;
-            __sincosf(ph, &sn, &cs);               // e^{i ph} = cs + i sn
-            zr[r] = fmaf(cs, rk.x, fmaf(-sn, rk.y, zr[r]));
-            zi[r] = fmaf(cs, rk.y, fmaf(sn, rk.x, zi[r]));
+            if (EXACT) ph = frac_turns((o.w * INV_TWO_PI_F + Phi[r]) + frac_dot3(dx[r], dxl[r], o, g_lo[k])) * TWO_PI_F;
+            else ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, o.w + Phi[r])));
+            z[r] = fmaf((kk & 1) ? -kr.y : kr.y, __cosf(ph), z[r]);   // odd k: -cos(theta + pi)
         }
     }
-    adjg_flush(w, zr, zi, acc);                 // the last run
+    adjg_flush(M, z, acc);                      // the last run
 }
 
 template <bool EXACT, bool PAR, class GF>
 __device__ __forceinline__ void adjg_gauss_tile(const float4* __restrict__ s_off, const float4* __restrict__ g_lo,
-                                                const float4* __restrict__ s_va, const float2* __restrict__ s_kk,
-                                                const float4* __restrict__ s_rk, const GF& gain,
-                                                const float (&cC)[2], const float (&sC)[2],
+                                                const float4* __restrict__ s_va, const float4* __restrict__ s_kr,
+                                                const GF& gain, const float (&Ct)[2],
                                                 const float4 (&dx)[2], const float4 (&dxl)[2],
                                                 const float4 (&pgd)[2], float (&acc)[2])
 {
     int cur = -1;
-    float2 w[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-    float zr[2] = {0.f, 0.f}, zi[2] = {0.f, 0.f};
-#pragma unroll 2
-    for (int k = 0; k < G; ++k) {
+    float M[2] = {0.f, 0.f}, Phi[2] = {0.f, 0.f}, z[2] = {0.f, 0.f};
+#pragma unroll 1
+    for (int k0 = 0; k0 < G; k0 += 2)
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+        const int k = k0 + kk;
         const float4 o = s_off[k];
         const float4 va = s_va[k];                 // {u, v, -2 w, gam (radians)}
-        const float2 ka = s_kk[k];                 // {k1, k0}
-        const float4 rk = s_rk[k];                 // {r', key, 0}
-        adjg_next_run(__float_as_int(rk.z), cur, gain, cC, sC, w, zr, zi, acc);
+        const float4 kr = s_kr[k];                 // {key, k0', k1, 0}
+        adjg_next_run<EXACT>(__float_as_int(kr.x), cur, gain, Ct, M, Phi, z, acc);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             // pgd = {l, m, r^2/4, pi nu}: t = u l + v m - w r^2/2
             const float t = fmaf(va.x, pgd[r].x, fmaf(va.y, pgd[r].y, va.z * pgd[r].z));
             float ph;                              // radians
             if (EXACT) {
-                ph = o.w * INV_TWO_PI_F + frac_dot3(dx[r], dxl[r], o, g_lo[k]);
+                ph = (o.w * INV_TWO_PI_F + Phi[r]) + frac_dot3(dx[r], dxl[r], o, g_lo[k]);
                 ph = fmaf(-va.w * INV_TWO_PI_F, t, ph);
                 if (PAR) ph = fmaf(va.z, pgd[r].w * INV_TWO_PI_F, ph);   // -w nu, turns
                 ph = frac_turns(ph) * TWO_PI_F;
             } else {
-                ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, o.w)));
+                ph = fmaf(dx[r].z, o.z, fmaf(dx[r].y, o.y, fmaf(dx[r].x, o.x, o.w + Phi[r])));
                 ph = fmaf(-va.w, t, ph);
                 if (PAR) ph = fmaf(va.z, pgd[r].w, ph);                  // -2 pi w nu
             }
-            float sn, cs;
-            __sincosf(ph, &sn, &cs);
-            const float amp = ex2_approx(fmaf(ka.x, t, ka.y));        // e^{Re(qc)}
-            const float ca = amp * cs, sa = amp * sn;
-            zr[r] = fmaf(ca, rk.x, fmaf(-sa, rk.y, zr[r]));
-            zi[r] = fmaf(ca, rk.y, fmaf(sa, rk.x, zi[r]));
+            const float amp = ex2_approx(fmaf(kr.z, t, kr.y));        // |r'| e^{Re(qc)}
+            z[r] = fmaf(kk ? -amp : amp, __cosf(ph), z[r]);             // odd k: -cos(theta + pi)
         }
     }
-    adjg_flush(w, zr, zi, acc);                 // the last run
+    adjg_flush(M, z, acc);                      // the last run
 }
 
 // Adjoint with gains.  The CTA's 8 warps share one owned pixel granule at a
@@ -981,13 +953,13 @@ __device__ __forceinline__ void adjg_gauss_tile(const float4* __restrict__ s_off
 // inside the run.  For each owned granule the 8 warp sums are added in warp
 // order (deterministic).
 struct AdjRaw {                                   // one warp's slice, bytes
-    static constexpr int OFF = 0, LO = 1024, HI = 2048, R = 3072, ANT = 4096, CEN = 4608;
+    static constexpr int OFF = 0, LO = 1024, HI = 2048, R = 3072, ANT = 3584, CEN = 4096;
     static constexpr int BYTES = CEN + 48;        // a multiple of 16
 };
 
-// Lane 0: copy visibility granule g of P (residual R) into a warp's raw slice.
-__device__ __forceinline__ void adj_raw_load(unsigned char* raw, const DevProblem& P, const double2* R, int g,
-                                             unsigned long long* bar)
+// Lane 0: copy visibility granule g of P into a warp's raw slice (r: the
+// polar residual r32_kernel wrote).
+__device__ __forceinline__ void adj_raw_load(unsigned char* raw, const DevProblem& P, int g, unsigned long long* bar)
 {
     const size_t e = (size_t)g * G;
     fence_proxy_async_smem();                     // the slice's last readers (generic proxy) are done
@@ -995,7 +967,7 @@ __device__ __forceinline__ void adj_raw_load(unsigned char* raw, const DevProble
     bulk_copy(raw + AdjRaw::OFF, P.vis.off + e, 1024, bar);
     bulk_copy(raw + AdjRaw::LO, P.vis.offlo + e, 1024, bar);
     bulk_copy(raw + AdjRaw::HI, P.vis.hi + e, 1024, bar);
-    bulk_copy(raw + AdjRaw::R, R + e, 1024, bar);
+    bulk_copy(raw + AdjRaw::R, P.r32 + e, 512, bar);
     bulk_copy(raw + AdjRaw::ANT, P.ant + e, 512, bar);
     bulk_copy(raw + AdjRaw::CEN, P.vis.cen_hi + g, 16, bar);
     bulk_copy(raw + AdjRaw::CEN + 16, P.vis.cen_lo + g, 16, bar);
@@ -1007,15 +979,14 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
                        double* __restrict__ partial)
 {
     // per warp, what its tiles read for its current granule
-    __shared__ float4 s_off[BLK_GRAN][G];       // {du, dv, dw, B (radians)}
-    __shared__ float4 s_rk[BLK_GRAN][G];        // {r (Gaussian owners: r'), pair key, 0}
+    __shared__ float4 s_off[BLK_GRAN][G];       // {du, dv, dw, B + arg r (radians)}
+    __shared__ float4 s_kr[BLK_GRAN][G];        // {pair key, |r| or k0 + log2 |r'|, k1, 0}
     __shared__ float4 s_va[BLK_GRAN][G];        // Gaussian owners: {u, v, -2 w, gam (radians)}
-    __shared__ float2 s_kk[BLK_GRAN][G];        // Gaussian owners: {k1, k0}
     __shared__ double s_red[BLK_GRAN][G];
     __shared__ __align__(8) unsigned long long s_wbar[BLK_GRAN];   // each warp's raw slice
     __shared__ __align__(8) unsigned long long s_gbar;             // the gains table
     // dynamic: [raw slices, BLK_GRAN x AdjRaw::BYTES][the owned granule's gains
-    // [gain_rows(n_ant)][GP]], each filled by bulk (TMA) copies
+    // in polar form [gain_rows(n_ant)][GP]], each filled by bulk (TMA) copies
     extern __shared__ __align__(128) unsigned char s_dyn[];
     float2* const s_gain = reinterpret_cast<float2*>(s_dyn + BLK_GRAN * AdjRaw::BYTES);
 
@@ -1024,7 +995,7 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
     const float4* const raw_off = reinterpret_cast<const float4*>(raw + AdjRaw::OFF);
     const float4* const raw_lo = reinterpret_cast<const float4*>(raw + AdjRaw::LO);
     const float4* const raw_hi = reinterpret_cast<const float4*>(raw + AdjRaw::HI);
-    const double2* const raw_r = reinterpret_cast<const double2*>(raw + AdjRaw::R);
+    const float2* const raw_r = reinterpret_cast<const float2*>(raw + AdjRaw::R);
     const int2* const raw_ant = reinterpret_cast<const int2*>(raw + AdjRaw::ANT);
     const float4* const raw_cen = reinterpret_cast<const float4*>(raw + AdjRaw::CEN);
     const Plan pl = *plp;
@@ -1063,10 +1034,10 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
             __syncthreads();                                 // s_gain / s_red free again
             if (threadIdx.x == 0 && !fault) {
                 fence_proxy_async_smem();                    // the table's last readers are done
-                bulk_load(s_gain, P.gains32 + (size_t)pgi * gtab_n, (unsigned)gtab_n * (unsigned)sizeof(float2),
+                bulk_load(s_gain, P.gpol32 + (size_t)pgi * gtab_n, (unsigned)gtab_n * (unsigned)sizeof(float2),
                           &s_gbar);
             }
-            if (lane == 0 && !fault && g0 + warp < g1) adj_raw_load(raw, P, R, g0 + warp, &s_wbar[warp]);
+            if (lane == 0 && !fault && g0 + warp < g1) adj_raw_load(raw, P, g0 + warp, &s_wbar[warp]);
             const float4 ch = P.pix.cen_hi[pgi], cl = P.pix.cen_lo[pgi], ext = P.pix.ext[pgi];
             const int kind = P.gkind[pgi];
             const float sigma = P.gsig[pgi];
@@ -1095,49 +1066,48 @@ adj_mixed_gains_kernel(const DevProblem* __restrict__ probs, const Plan* __restr
                     float4 o = raw_off[k];
                     const int2 ab = raw_ant[k];
                     const float key = __int_as_float(ab.x << 16 | ab.y);   // the pair (adjg_next_run)
-                    float b = frac_dot3(ch, cl, o, raw_lo[k]);
-                    const double2 rd = raw_r[k];
-                    float2 rr = make_float2((float)rd.x, (float)rd.y);
+                    const float b = frac_dot3(ch, cl, o, raw_lo[k]) + odd_turn(k);   // turns
+                    const float2 rp = raw_r[k];                             // {|r|, arg r in turns}
+                    float4 kr;
                     if (gauss) {
                         const float4 va = vis_for_gauss(raw_hi[k]);
-                        const GaussConst gc = gauss_const(va.x, va.y, -0.5f * va.z, sigma);
-                        b = frac_turns(b + gc.cphase);
-                        rr = make_float2(gc.id * fmaf(gc.beta, rr.y, rr.x), gc.id * fmaf(-gc.beta, rr.x, rr.y));
-                        s_va[warp][k] = make_float4(va.x, va.y, va.z, gc.gamr);
-                        s_kk[warp][k] = make_float2(gc.k1, gc.k0);
+                        const float4 rec = adj_gauss_record(b, rp, va, sigma);   // {B', gamr, k1, k0'}
+                        o.w = rec.x;
+                        s_va[warp][k] = make_float4(va.x, va.y, va.z, rec.y);
+                        kr = make_float4(key, rec.w, rec.z, 0.f);
+                    } else {
+                        o.w = frac_turns(b + rp.y) * TWO_PI_F;
+                        kr = make_float4(key, rp.x, 0.f, 0.f);
                     }
-                    o.w = b * TWO_PI_F;                       // radians
                     s_off[warp][k] = o;
-                    s_rk[warp][k] = make_float4(rr.x, rr.y, key, 0.f);
+                    s_kr[warp][k] = kr;
                 }
                 const float4 yc_h = raw_cen[0], yc_l = raw_cen[1], yext = raw_cen[2];
                 __syncwarp();                                 // the slice is read: refill it
-                if (lane == 0 && !fault && g + BLK_GRAN < g1) adj_raw_load(raw, P, R, g + BLK_GRAN, &s_wbar[warp]);
+                if (lane == 0 && !fault && g + BLK_GRAN < g1) adj_raw_load(raw, P, g + BLK_GRAN, &s_wbar[warp]);
                 const bool exact = dot3(ext, yext) > D_MAX;
-                float cC[2], sC[2];                   // e^{2 pi i C}, C the tile's centre term
+                float Ct[2];                          // the tile's centre term C, turns
 #pragma unroll
-                for (int r = 0; r < 2; ++r)
-                    __sincosf(frac_dot3(xh[r], P.pix.lo[eidx[r]], yc_h, yc_l) * TWO_PI_F, &sC[r], &cC[r]);
+                for (int r = 0; r < 2; ++r) Ct[r] = frac_dot3(xh[r], P.pix.lo[eidx[r]], yc_h, yc_l);
                 const float4* g_lo = P.vis.offlo + (size_t)g * G;   // exact tiles only (rare)
                 float acc[2] = {0.f, 0.f};
                 if (!gauss) {
                     if (exact) {
                         const float4 dxt[2] = {P.pix.off[eidx[0]], P.pix.off[eidx[1]]},
-                                 dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
-                        adjg_dirac_tile<true>(s_off[warp], g_lo, s_rk[warp], sg, cC, sC, dxt, dxl, acc);
+                                     dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
+                        adjg_dirac_tile<true>(s_off[warp], g_lo, s_kr[warp], sg, Ct, dxt, dxl, acc);
                     } else {
-                        adjg_dirac_tile<false>(s_off[warp], g_lo, s_rk[warp], sg, cC, sC, dx, dx, acc);
+                        adjg_dirac_tile<false>(s_off[warp], g_lo, s_kr[warp], sg, Ct, dx, dx, acc);
                     }
+                } else if (exact) {
+                    const float4 dxt[2] = {P.pix.off[eidx[0]], P.pix.off[eidx[1]]},
+                                 dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
+                    if (par) adjg_gauss_tile<true, true>(s_off[warp], g_lo, s_va[warp], s_kr[warp], sg, Ct, dxt, dxl, pgd, acc);
+                    else adjg_gauss_tile<true, false>(s_off[warp], g_lo, s_va[warp], s_kr[warp], sg, Ct, dxt, dxl, pgd, acc);
+                } else if (par) {
+                    adjg_gauss_tile<false, true>(s_off[warp], g_lo, s_va[warp], s_kr[warp], sg, Ct, dx, dx, pgd, acc);
                 } else {
-                    if (exact) {
-                        const float4 dxt[2] = {P.pix.off[eidx[0]], P.pix.off[eidx[1]]},
-                                 dxl[2] = {P.pix.offlo[eidx[0]], P.pix.offlo[eidx[1]]};
-                        if (par) adjg_gauss_tile<true, true>(s_off[warp], g_lo, s_va[warp], s_kk[warp], s_rk[warp], sg, cC, sC, dxt, dxl, pgd, acc);
-                        else adjg_gauss_tile<true, false>(s_off[warp], g_lo, s_va[warp], s_kk[warp], s_rk[warp], sg, cC, sC, dxt, dxl, pgd, acc);
-                    } else {
-                        if (par) adjg_gauss_tile<false, true>(s_off[warp], g_lo, s_va[warp], s_kk[warp], s_rk[warp], sg, cC, sC, dx, dx, pgd, acc);
-                        else adjg_gauss_tile<false, false>(s_off[warp], g_lo, s_va[warp], s_kk[warp], s_rk[warp], sg, cC, sC, dx, dx, pgd, acc);
-                    }
+                    adjg_gauss_tile<false, false>(s_off[warp], g_lo, s_va[warp], s_kr[warp], sg, Ct, dx, dx, pgd, acc);
                 }
 #pragma unroll
                 for (int r = 0; r < 2; ++r) tot[r] += (double)acc[r];
@@ -1188,8 +1158,10 @@ static int adj_stage_bytes_of(int nst)
     return 2 * (nst <= 2 ? AdjStage<2>::BYTES : AdjStage<4>::BYTES);
 }
 
-// r32 = the adjoint's input residual in FP32, for every problem of the batch
-// that takes part in the coming adjoint (blockIdx.y = problem).
+// r32 = the mixed adjoint's input residual in polar form, {|r|, arg r in
+// turns}, for every problem of the batch that takes part in the coming adjoint
+// (blockIdx.y = problem).  Modulus and argument are taken in FP64 and rounded
+// once to FP32 (arg r to 3e-8 turn).
 __global__ void r32_kernel(const DevProblem* __restrict__ probs)
 {
     const DevProblem& P = probs[blockIdx.y];
@@ -1197,7 +1169,7 @@ __global__ void r32_kernel(const DevProblem* __restrict__ probs)
     if (!adj_role(P, R) || !P.r32) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.vis.n_pad; i += gridDim.x * blockDim.x) {
         const double2 v = R[i];
-        P.r32[i] = make_float2((float)v.x, (float)v.y);
+        P.r32[i] = make_float2((float)hypot(v.x, v.y), (float)(atan2(v.y, v.x) * 0.15915494309189535));
     }
 }
 cudaError_t launch_r32(const DevProblem* probs, int n_probs, int max_vis_pad, cudaStream_t st)

@@ -36,6 +36,22 @@ def test_sfu_peak_of_a_kind_mix_adds_time_per_pair():
     assert alt is None
 
 
+def test_sfu_peak_of_the_adjoint_counts_one_cosine():
+    """The adjoint's output is real, so a pair takes a cosine alone: the
+    Dirac bound is twice the forward's, and its LP stays MUFU-bound with a
+    small FMA-path share (7 instructions per SFU-path pair leave 1/8 of the
+    issue slots)."""
+    peak, basis, alt = bench.sfu_peak(W(None), "adj")
+    assert peak == pytest.approx(152 * 16 * 2.07, rel=1e-12)
+    per_sm_clk = 4 * 32 * (1 / 8 + (1 - 7 / 8) / 16)
+    assert alt["peak"] == pytest.approx(152 * 2.07 * per_sm_clk, rel=1e-12)
+    kinds = [0] * 25 + [2] * 75          # 1 MUFU for Dirac, 2 for Gaussian (cos + exp2)
+    assert bench.sfu_peak(W(kinds), "adj")[0] == pytest.approx(152 * 16 * 2.07 / 1.75, rel=1e-12)
+    r = 16 * bench.N_SM * bench.SM_MAX_MHZ * 1e6
+    m = bench.sfu_peak_measured(W(kinds), {"sincos_per_s": r, "ex2_per_s": 2 * r}, "adj")
+    assert m["peak"] == pytest.approx(1e-9 / (1 / r + 0.75 / (2 * r)))
+
+
 def test_kernel_source_hash_ignores_comments_only(tmp_path):
     src = os.path.join(ROOT, "paper_1310_2078_gb300", "csrc")
     for f in bench.KERNEL_SOURCES:

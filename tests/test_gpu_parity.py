@@ -130,7 +130,14 @@ def test_paper_scale_config_sampled(ctx):
     a = P.adjoint(r, 1)
     cols = rng.choice(w.n_pix, 60, replace=False)
     ao = oracle.adjoint(O, r, cols=cols)
-    assert np.max(np.abs(a[cols] - ao)) / np.max(np.abs(ao)) <= 1e-5
+    err = np.max(np.abs(a[cols] - ao)) / np.max(np.abs(ao))
+    assert err <= 1e-5
+    # A residual of random phases makes each column a sum of 406,400 terms
+    # of random sign, of size ~sqrt(N_v): per-term rounding then stays near
+    # 1e-7 relative, while a bias common to all terms (e.g. of the cosine when
+    # every weight |r_k| is positive) grows with N_v and shows here as
+    # several 1e-6.
+    assert err <= 2e-6
 
 
 def test_adjoint_identity_on_gpu(ctx):
