@@ -113,6 +113,33 @@ static int kd_par_depth()
     return d;
 }
 
+// Run fn(lo, hi) over [0, n) cut into contiguous chunks, one per host thread
+// (at most 16), when n is large enough to pay for the threads.  For loops whose
+// iterations write only their own outputs: the result is the one a single
+// thread gives.
+template <class F>
+static void parallel_chunks(size_t n, size_t min_per_chunk, const F& fn)
+{
+    const size_t t = std::min<size_t>(16, std::max(1u, std::thread::hardware_concurrency()));
+    const size_t nc = std::max<size_t>(1, std::min(t, n / std::max<size_t>(1, min_per_chunk)));
+    if (nc <= 1) {
+        fn((size_t)0, n);
+        return;
+    }
+    std::vector<std::future<void>> fs;
+    size_t done = 0;                       // chunks [0, done) run on threads
+    try {
+        for (size_t c = 1; c < nc; ++c) {
+            fs.push_back(std::async(std::launch::async, [&fn, n, nc, c] { fn(n * c / nc, n * (c + 1) / nc); }));
+            done = c;
+        }
+    } catch (...) {                        // no thread to be had: the rest runs here
+    }
+    fn(0, n / nc);
+    for (size_t c = done + 1; c < nc; ++c) fn(n * c / nc, n * (c + 1) / nc);
+    for (auto& f : fs) f.get();
+}
+
 // Append `members` (caller indices) in k-d order, padded with -1 to a
 // multiple of G.
 static void kd_append(std::vector<int>& order, std::vector<int> members, const double* x,
@@ -139,25 +166,27 @@ static void group_by_exact_share(std::vector<int>& order, const double* uvw, con
     if (ng < 2 || pext.empty()) return;
     const size_t step = (pext.size() + 1023) / 1024;
     std::vector<std::pair<float, int>> key(ng);
-    bool any = false;
-    for (size_t g = 0; g < ng; ++g) {
-        double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
-        for (size_t i = g * G; i < (g + 1) * G; ++i) {
-            const int o = order[i];
-            if (o < 0) continue;
-            for (int a = 0; a < 3; ++a) {
-                mn[a] = std::min(mn[a], uvw[3 * (size_t)o + a]);
-                mx[a] = std::max(mx[a], uvw[3 * (size_t)o + a]);
+    parallel_chunks(ng, 256, [&](size_t g0, size_t g1) {
+        for (size_t g = g0; g < g1; ++g) {
+            double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+            for (size_t i = g * G; i < (g + 1) * G; ++i) {
+                const int o = order[i];
+                if (o < 0) continue;
+                for (int a = 0; a < 3; ++a) {
+                    mn[a] = std::min(mn[a], uvw[3 * (size_t)o + a]);
+                    mx[a] = std::max(mx[a], uvw[3 * (size_t)o + a]);
+                }
             }
+            const float e[3] = {(float)(0.5 * (mx[0] - mn[0])), (float)(0.5 * (mx[1] - mn[1])),
+                                (float)(0.5 * (mx[2] - mn[2]))};
+            int n_ex = 0, n = 0;
+            for (size_t p = 0; p < pext.size(); p += step, ++n)
+                n_ex += e[0] * pext[p].x + e[1] * pext[p].y + e[2] * pext[p].z > D_MAX;
+            key[g] = {(float)n_ex / (float)std::max(1, n), (int)g};
         }
-        const float e[3] = {(float)(0.5 * (mx[0] - mn[0])), (float)(0.5 * (mx[1] - mn[1])),
-                            (float)(0.5 * (mx[2] - mn[2]))};
-        int n_ex = 0, n = 0;
-        for (size_t p = 0; p < pext.size(); p += step, ++n)
-            n_ex += e[0] * pext[p].x + e[1] * pext[p].y + e[2] * pext[p].z > D_MAX;
-        key[g] = {(float)n_ex / (float)std::max(1, n), (int)g};
-        any |= n_ex > 0;
-    }
+    });
+    bool any = false;
+    for (const auto& k : key) any |= k.first > 0.f;
     if (!any) return;
     std::stable_sort(key.begin(), key.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
     std::vector<int> out(order.size());
@@ -182,10 +211,38 @@ static void sort_baselines(std::vector<int>& order, const std::vector<int>& ant)
         });
 }
 
+// An allocator whose resize() leaves new elements of a trivial type
+// uninitialised (every slot is written afterwards): the large host arrays of
+// a layout are then first touched by the threads that fill them, not zeroed
+// by one thread before.
+template <class T>
+struct NoInitAlloc : std::allocator<T> {
+    template <class U>
+    struct rebind {
+        using other = NoInitAlloc<U>;
+    };
+    NoInitAlloc() = default;
+    template <class U>
+    NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+    template <class U>
+    void construct(U* p) noexcept
+    {
+        ::new ((void*)p) U;
+    }
+    template <class U, class... A>
+    void construct(U* p, A&&... a)
+    {
+        ::new ((void*)p) U(std::forward<A>(a)...);
+    }
+};
+template <class T>
+using HostVec = std::vector<T, NoInitAlloc<T>>;
+
 struct HostSide {
     int n = 0, n_pad = 0, n_gran = 0, n_blk = 0;
-    std::vector<float4> hi, lo, off, offlo, cen_hi, cen_lo, ext;
-    std::vector<d4> d;
+    HostVec<float4> hi, lo, off, offlo;
+    std::vector<float4> cen_hi, cen_lo, ext;
+    HostVec<d4> d;
     std::vector<int> orig;
 };
 
@@ -203,7 +260,9 @@ static void layout_side(const std::vector<int>& order, const std::vector<d4>& xy
     S.hi.resize(S.n_pad); S.lo.resize(S.n_pad); S.off.resize(S.n_pad); S.offlo.resize(S.n_pad);
     S.d.resize(S.n_pad);
     S.cen_hi.resize(S.n_gran); S.cen_lo.resize(S.n_gran); S.ext.resize(S.n_gran);
-    for (int g = 0; g < S.n_gran; ++g) {
+    // granules are independent: each fills only its own slots
+    parallel_chunks((size_t)S.n_gran, 512, [&](size_t g0, size_t g1) {
+    for (int g = (int)g0; g < (int)g1; ++g) {
         int ref = -1;
         double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
         for (int t = 0; t < G; ++t) {
@@ -238,6 +297,7 @@ static void layout_side(const std::vector<int>& order, const std::vector<d4>& xy
             S.offlo[i] = make_float4(f32lo(dd[0]), f32lo(dd[1]), f32lo(dd[2]), 0.f);
         }
     }
+    });
 }
 
 // ============================================================ device buffers
@@ -527,7 +587,11 @@ int sl1m_problem::rebuild(cudaStream_t st)
         std::vector<std::pair<std::pair<int, double>, int>> cls(n_pix);
         for (int64_t j = 0; j < n_pix; ++j)
             cls[j] = {{kind.empty() ? 0 : kind[j], sigma.empty() ? 0.0 : sigma[j]}, (int)j};
-        std::stable_sort(cls.begin(), cls.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+        // (one class, the common case: already in the order the sort gives)
+        bool one_class = true;
+        for (int64_t j = 1; j < n_pix && one_class; ++j) one_class = cls[j].first == cls[0].first;
+        if (!one_class)
+            std::stable_sort(cls.begin(), cls.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
         std::vector<int> order;
         std::vector<std::pair<int, double>> gran_cls;
         size_t i = 0;
