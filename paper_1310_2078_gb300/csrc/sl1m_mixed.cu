@@ -544,11 +544,12 @@ fwd_mixed_kernel(const DevProblem* __restrict__ probs, const Plan* __restrict__ 
 
 // ----------------------------------------------------------- adjoint tiles
 // The adjoint's output is real (the image is real: its gradient is Re A^H r),
-// and for one pair Re(conj(A_kj) r_k) = |r_k| cos(theta_kj + arg r_k): a cosine alone, not
-// a sine and a cosine.  r32_kernel writes r in polar form {|r|, arg r in
-// turns}; when a stage is derived, arg r_k is added to the visibility's B term
-// (so theta + arg r costs nothing per pair) and |r_k| rides in the same record
-// (Gaussian owners: log2 |r'_k| inside the amplitude's exponent).
+// and for one pair Re(conj(A_kj) r_k) = |A_kj| |r_k| cos(theta_kj + arg r_k)
+// with theta_kj = -arg A_kj: a cosine alone, not a sine and a cosine.
+// r32_kernel writes r in polar form {|r|, arg r in turns}; when a stage is
+// derived, arg r_k is added to the visibility's B term (so theta + arg r
+// costs nothing per pair) and |r_k| rides in the same record (Gaussian
+// owners: log2 |r'_k| inside the amplitude's exponent).
 // With weights that are all positive, a bias of the SFU's cosine would add
 // up over the N_v terms of a sum (where a sine and a cosine weighted by Re r
 // and Im r of either sign cancel it), so every odd visibility k takes
