@@ -31,7 +31,8 @@ cudaError_t launch_adjoint(int precision, bool gains, int n_ant, const DevProble
 // which: 0 fwd fp64, 1 adj fp64, 2 fwd mixed, 3 adj mixed
 int occupancy(int which, bool gains, int n_ant, int nst = NST_DEFAULT);
 int fwd_smem_bytes(int n_ant, bool gains, int nst);
-// Before a mixed no-gains adjoint: each problem's input residual in FP32 (r32).
+// Before a mixed adjoint: each problem's input residual in polar form, {|r|,
+// arg r in turns} in FP32 (r32).
 cudaError_t launch_r32(const DevProblem* probs, int n_probs, int max_vis_pad, cudaStream_t st);
 // The mixed gains kernels' bounded waits for their bulk copies set a device
 // flag when they give up; read it into *host_flag (asynchronously on st: valid
