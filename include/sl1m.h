@@ -389,6 +389,26 @@ int sl1m_plan_preview(int32_t n_probs, const int32_t* owned_blocks, const int32_
  * 64).  n_pad = ceil(n / 64) * 64.  order may be NULL to query n_pad. */
 int sl1m_granule_order(int64_t n, const double* xy, int32_t* order, int64_t* n_pad);
 
+/* Host-only: the FP32 layout of one side that the mixed kernels read for the
+ * exact phase split of Sect. 3.1's phase (X.Y = X.Yc + Xc.(Y - Yc) +
+ * (X - Xc).(Y - Yc), each product from FP32 halves).  xyzw [n][4]: element
+ * coordinates (x, y, z) and an auxiliary value (pixels: l, m, n - 1, 1/n;
+ * visibilities: u, v, w, weight); order [n_pad]: a padded permutation of
+ * 0..n-1 (-1 = padding, n_pad a multiple of 64), e.g. sl1m_granule_order's.
+ * Outputs, each [n_pad][4] or [n_pad / 64][4] floats and each may be NULL:
+ *   hi, lo     the element's (x, y, z) as hi = fl32(x), lo = fl32(x - hi); w 0
+ *   off, offlo the same split of the offset from the granule centre; off.w =
+ *              the auxiliary value (0 for padding)
+ *   cen_hi, cen_lo, ext  per granule: the centre (the middle of the members'
+ *              bounding box) split the same way, and the extent, an upper
+ *              bound of |offset| per axis (half the box, rounded up).
+ * A padding slot copies the coordinates of a member of its granule.
+ * SL1M_ERR_ARG: null inputs, n_pad not a multiple of 64 or below n, an index
+ * out of range or repeated.  The paper has no counterpart; it exposes, for
+ * tests, what the library lays out in HBM. */
+int sl1m_granule_layout(int64_t n, const double* xyzw, const int32_t* order, int64_t n_pad, float* hi,
+                        float* lo, float* off, float* offlo, float* cen_hi, float* cen_lo, float* ext);
+
 /* Device bytes the problem holds (inputs, layout and solver workspace). */
 int sl1m_problem_bytes(const sl1m_problem* prob, int64_t* bytes);
 

@@ -1884,6 +1884,41 @@ int sl1m_granule_order(int64_t n, const double* xy, int32_t* order, int64_t* n_p
     return SL1M_OK;
 }
 
+int sl1m_granule_layout(int64_t n, const double* xyzw, const int32_t* order, int64_t n_pad, float* hi,
+                        float* lo, float* off, float* offlo, float* cen_hi, float* cen_lo, float* ext)
+{
+    if (n <= 0 || !xyzw || !order || n > ((int64_t)1 << 30) || n_pad < n || n_pad % G != 0 ||
+        n_pad > ((int64_t)1 << 31) - G)
+        return SL1M_ERR_ARG;
+    std::vector<char> seen((size_t)n, 0);
+    std::vector<int> ord((size_t)n_pad);
+    for (int64_t i = 0; i < n_pad; ++i) {
+        const int32_t o = order[i];
+        if (o < -1 || o >= n) return SL1M_ERR_ARG;
+        if (o >= 0) {
+            if (seen[(size_t)o]) return SL1M_ERR_ARG;
+            seen[(size_t)o] = 1;
+        }
+        ord[(size_t)i] = o;
+    }
+    std::vector<d4> xyz((size_t)n);
+    for (int64_t i = 0; i < n; ++i)
+        xyz[(size_t)i] = make_d4(xyzw[4 * i], xyzw[4 * i + 1], xyzw[4 * i + 2], xyzw[4 * i + 3]);
+    HostSide H;
+    layout_side(ord, xyz, (int)n, H);
+    auto put = [](float* dst, const float4* src, size_t cnt) {
+        if (dst) std::memcpy(dst, src, cnt * sizeof(float4));
+    };
+    put(hi, H.hi.data(), H.hi.size());
+    put(lo, H.lo.data(), H.lo.size());
+    put(off, H.off.data(), H.off.size());
+    put(offlo, H.offlo.data(), H.offlo.size());
+    put(cen_hi, H.cen_hi.data(), H.cen_hi.size());
+    put(cen_lo, H.cen_lo.data(), H.cen_lo.size());
+    put(ext, H.ext.data(), H.ext.size());
+    return SL1M_OK;
+}
+
 int sl1m_counters(sl1m_ctx* ctx, int64_t* launches, int64_t* h2d_bytes, int64_t* d2h_bytes)
 {
     if (!ctx) return SL1M_ERR_ARG;

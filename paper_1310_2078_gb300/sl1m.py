@@ -36,6 +36,7 @@ EXPORTS = [
     "sl1m_forward_dev", "sl1m_adjoint_dev", "sl1m_max_eig", "sl1m_solve",
     "sl1m_profile_enable", "sl1m_profile_reset", "sl1m_profile_read", "sl1m_problem_bytes",
     "sl1m_counters", "sl1m_counters_reset", "sl1m_plan_preview", "sl1m_granule_order",
+    "sl1m_granule_layout",
     "sl1m_server_start", "sl1m_server_submit", "sl1m_server_poll", "sl1m_server_wait",
     "sl1m_server_stop", "sl1m_server_info", "sl1m_forward_noalloc", "sl1m_autotune",
     "sl1m_dirty_image", "sl1m_solve_refine", "sl1m_get_solution", "sl1m_set_tile_shape",
@@ -150,6 +151,7 @@ def load():
             "sl1m_plan_preview": ([i32, vp, vp, i32, vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32),
                                    vp, vp, vp, vp], C.c_int),
             "sl1m_granule_order": ([i64, vp, vp, C.POINTER(i64)], C.c_int),
+            "sl1m_granule_layout": ([i64, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp], C.c_int),
             "sl1m_server_start": ([vp, C.POINTER(ServerOpts)], C.c_int),
             "sl1m_server_submit": ([vp, vp, C.POINTER(SolveOpts), C.POINTER(C.c_uint64)], C.c_int),
             "sl1m_server_poll": ([vp, C.c_uint64, C.POINTER(C.c_int)], C.c_int),
@@ -243,6 +245,22 @@ def granule_order(xy):
         raise SL1MError(st, "sl1m_granule_order failed")
     out = np.zeros(npad.value, np.int32)
     lib.sl1m_granule_order(xy.shape[0], _ptr(xy), _ptr(out), C.byref(npad))
+    return out
+
+
+def granule_layout(xyzw, order):
+    """Host-only FP32 layout of one side (sl1m_granule_layout): a dict of
+    hi, lo, off, offlo [n_pad, 4] and cen_hi, cen_lo, ext [n_pad / 64, 4]."""
+    lib = load()
+    xyzw = _f64(xyzw, (-1, 4))
+    order = np.ascontiguousarray(order, np.int32)
+    npad = order.shape[0]
+    out = {k: np.zeros((npad, 4), np.float32) for k in ("hi", "lo", "off", "offlo")}
+    out.update({k: np.zeros((npad // 64, 4), np.float32) for k in ("cen_hi", "cen_lo", "ext")})
+    st = lib.sl1m_granule_layout(xyzw.shape[0], _ptr(xyzw), _ptr(order), npad,
+                                 *(_ptr(out[k]) for k in ("hi", "lo", "off", "offlo", "cen_hi", "cen_lo", "ext")))
+    if st != OK:
+        raise SL1MError(st, "sl1m_granule_layout failed")
     return out
 
 

@@ -148,3 +148,123 @@ def test_granule_order_of_a_large_input_is_deterministic_and_compact(sl1m):
     gr = a[: (len(a) // G - 1) * G].reshape(-1, G)
     ext = np.ptp(xy[gr], axis=1).max(axis=1)
     assert np.median(ext) < 0.05
+
+
+# ---- the FP32 layout the mixed kernels read (exact phase split, Sect. 3.1)
+
+def _layout_restated(xyzw, order):
+    """The layout from its definition, in numpy: per granule the centre is the
+    middle of its members' bounding box and the extent half the box (rounded
+    up by a relative 1e-7); every stored FP32 value is one rounding of an FP64
+    quantity (hi = fl32(x), lo = fl32(x - hi)); a padding slot copies the last
+    member of its granule with auxiliary value 0."""
+    f32 = np.float32
+    npad = len(order)
+    ng = npad // G
+    hi = np.zeros((npad, 4), f32)
+    lo = np.zeros((npad, 4), f32)
+    off = np.zeros((npad, 4), f32)
+    offlo = np.zeros((npad, 4), f32)
+    cen_hi = np.zeros((ng, 4), f32)
+    cen_lo = np.zeros((ng, 4), f32)
+    ext = np.zeros((ng, 4), f32)
+    for g in range(ng):
+        idx = order[g * G:(g + 1) * G]
+        real = idx[idx >= 0]
+        if real.size:
+            c = xyzw[real, :3]
+            mn, mx = c.min(axis=0), c.max(axis=0)
+            cen = 0.5 * (mn + mx)
+            ext[g, :3] = ((mx - mn) * 0.5000001).astype(f32)
+            ref = real[-1]
+        else:
+            cen = np.zeros(3)
+        cen_hi[g, :3] = cen.astype(f32)
+        cen_lo[g, :3] = (cen - cen.astype(f32).astype(np.float64)).astype(f32)
+        for t, o in enumerate(idx):
+            i = g * G + t
+            if o >= 0:
+                v, aux = xyzw[o, :3], xyzw[o, 3]
+            elif real.size:
+                v, aux = xyzw[ref, :3], 0.0
+            else:
+                v, aux = cen, 0.0
+            hi[i, :3] = v.astype(f32)
+            lo[i, :3] = (v - v.astype(f32).astype(np.float64)).astype(f32)
+            d = v - cen
+            off[i, :3] = d.astype(f32)
+            off[i, 3] = f32(aux)
+            offlo[i, :3] = (d - d.astype(f32).astype(np.float64)).astype(f32)
+    return dict(hi=hi, lo=lo, off=off, offlo=offlo, cen_hi=cen_hi, cen_lo=cen_lo, ext=ext)
+
+
+def _pixels_xyzw(lm):
+    r2 = (lm ** 2).sum(axis=1)
+    n = np.sqrt(1.0 - r2)
+    return np.column_stack([lm[:, 0], lm[:, 1], -r2 / (1.0 + n), 1.0 / n])
+
+
+@pytest.mark.parametrize("side", ["pixels", "visibilities"])
+def test_granule_layout_is_its_definition(sl1m, side):
+    """The library's FP32 layout of the wide-field geometry (l, m to +-0.5,
+    w-term significant) equals the definition restated in numpy, bit for bit,
+    and satisfies what the exact phase split needs: hi + lo and off + offlo
+    give the FP64 coordinate and offset to 2^-47 relative, and the extent
+    bounds every member's |offset| per axis."""
+    w = synth.config2(n_side=47)                 # 2,209 pixels: a padded last granule
+    if side == "pixels":
+        xyzw = _pixels_xyzw(w.lm)
+        order = sl1m.granule_order(w.lm)
+    else:
+        xyzw = np.column_stack([w.uvw, np.ones(w.n_vis)])
+        order = sl1m.granule_order(w.uvw[:, :2])
+    got = sl1m.granule_layout(xyzw, order)
+    want = _layout_restated(xyzw, order)
+    for k in want:
+        assert np.array_equal(got[k].view(np.uint32), want[k].view(np.uint32)), k
+    real = order >= 0
+    c = xyzw[order[real], :3]
+    assert np.all(np.abs(got["hi"][real, :3].astype(np.float64) + got["lo"][real, :3] - c)
+                  <= 2.0 ** -47 * np.abs(c) + 1e-300)
+    g = np.flatnonzero(real) // G
+    cen = got["cen_hi"][g, :3].astype(np.float64) + got["cen_lo"][g, :3]
+    d = c - cen
+    assert np.all(np.abs(got["off"][real, :3].astype(np.float64) + got["offlo"][real, :3] - d)
+                  <= 2.0 ** -46 * np.abs(c).max())
+    assert np.all(np.abs(d) <= got["ext"][g, :3])
+    assert np.array_equal(got["off"][real, 3], xyzw[order[real], 3].astype(np.float32))
+    assert np.all(got["off"][~real, 3] == 0.0)
+
+
+def test_granule_layout_of_a_large_input_on_threads(sl1m):
+    """Above 1,024 granules the layout runs on host threads: still the
+    definition, bit for bit (checked on a sample of granules), and the same on
+    every call."""
+    rng = np.random.default_rng(5)
+    lm = rng.uniform(-0.4, 0.4, (200_003, 2))
+    xyzw = _pixels_xyzw(lm)
+    order = sl1m.granule_order(lm)
+    a = sl1m.granule_layout(xyzw, order)
+    b = sl1m.granule_layout(xyzw, order)
+    for k in a:
+        assert np.array_equal(a[k].view(np.uint32), b[k].view(np.uint32)), k
+    ng = len(order) // G
+    for g in np.concatenate([rng.choice(ng - 1, 40, replace=False), [ng - 1]]):
+        sub = order[g * G:(g + 1) * G]
+        want = _layout_restated(xyzw, sub)
+        sl = slice(g * G, (g + 1) * G)
+        for k in ("hi", "lo", "off", "offlo"):
+            assert np.array_equal(a[k][sl].view(np.uint32), want[k].view(np.uint32)), (g, k)
+        for k in ("cen_hi", "cen_lo", "ext"):
+            assert np.array_equal(a[k][g].view(np.uint32), want[k][0].view(np.uint32)), (g, k)
+
+
+def test_granule_layout_rejects_a_bad_order(sl1m):
+    xyzw = _pixels_xyzw(np.random.default_rng(0).uniform(-0.3, 0.3, (70, 2)))
+    good = np.concatenate([np.arange(70), -np.ones(58, int)]).astype(np.int32)
+    sl1m.granule_layout(xyzw, good)
+    for bad in (np.concatenate([np.arange(69), [3], -np.ones(58, int)]),   # repeated index
+                np.concatenate([np.arange(69), [70], -np.ones(58, int)]),  # out of range
+                good[:100]):                                                 # not a multiple of 64
+        with pytest.raises(sl1m.SL1MError):
+            sl1m.granule_layout(xyzw, np.asarray(bad, np.int32))
