@@ -137,3 +137,67 @@ def test_exact_path_keeps_the_bound_where_the_fp32_chain_does_not():
     exact = phase_error(*data, exact=True)
     assert np.max(np.abs(plain)) > 2e-6
     assert np.max(np.abs(exact)) < 1e-6
+
+
+# ---- the adjoint's polar form: one cosine per pair
+
+def adjoint_terms(xc, x, yc, y, r, alternate=True, bias=0.0):
+    """The mixed adjoint's FP32 term of every pair, carried out as the kernel
+    does with roles swapped (owned X = pixels, streamed Y = visibilities):
+    r in polar form {|r|, arg r in turns} (FP64, rounded once), arg r added to
+    the streamed element's B term in turns (plus half a turn for odd k when
+    `alternate`), the phase C + B' + D in radians, one cosine (here exact in
+    FP64 of the FP32 argument, plus `bias`), and the term |r| cos (negated
+    for odd k)."""
+    xh, xl = split(x)
+    ych, ycl = split(yc)
+    dxh, _ = split(x - xc)
+    xch, xcl = split(xc)
+    dyh, dyl = split(y - yc)
+    C = frac_dot3(xh, xl, ych, ycl)
+    B = frac_dot3(xch, xcl, dyh, dyl)
+    rabs = np.hypot(r.real, r.imag).astype(f32)
+    rho = (np.arctan2(r.imag, r.real) / (2 * math.pi)).astype(f32)
+    odd = (np.arange(len(r)) % 2 == 1) & alternate
+    b = B + np.where(odd, f32(0.5), f32(0.0))
+    bp = frac_turns(b + rho) * TWO_PI_F                       # B + arg r (+ pi), radians
+    dx = dxh * TWO_PI_F
+    ph = fma32(dx[:, 2], dyh[:, 2], fma32(dx[:, 1], dyh[:, 1], fma32(dx[:, 0], dyh[:, 0], C * TWO_PI_F + bp)))
+    cs = (np.cos(ph.astype(np.float64)) + bias).astype(f32)
+    return np.where(odd, -rabs, rabs) * cs
+
+
+def test_adjoint_polar_term_is_re_conj_a_r():
+    """|r| cos(theta + arg r), with arg r folded into B and every other term
+    taken as -cos(theta + pi), equals Re(conj(A) r) = Re(e^{2 pi i X.Y} r) to
+    the phase split's micro-turn, at the wide-field and the largest accepted
+    products."""
+    rng = np.random.default_rng(6)
+    for uv, w in ((2000.0, 500.0), (0.99 * 2.0 ** 21 / 0.5, 0.99 * 2.0 ** 19)):
+        xc, x, yc, y = draw(rng, 200000, uv, w, 0.45, np.array([40.0, 40.0, 15.0]),
+                            np.array([0.0156, 0.0156, 0.005]))
+        # pixels own: X = (l, m, n - 1), Y = (u, v, w)
+        r = rng.normal(size=len(x)) + 1j * rng.normal(size=len(x))
+        got = adjoint_terms(yc, y, xc, x, r).astype(np.float64)
+        want = (np.exp(2j * math.pi * (x * y).sum(axis=1)) * r).real
+        err = np.abs(got - want) / np.abs(r)
+        assert np.max(err) < 4e-6                  # 2 pi x the micro-turn phase bound, and rounding
+        assert np.sqrt(np.mean(err ** 2)) < 4e-7
+
+
+def test_alternating_signs_cancel_a_bias_of_the_cosine():
+    """With the weights |r| all positive, a bias of the cosine adds up over a
+    column's N terms; taking every other term as -cos(theta + pi) makes it
+    cancel in pairs.  Over 400,000 terms a bias of 2e-8 moves the plain sum
+    by ~1e-2 (N E|r| bias) and the alternated one by far less."""
+    rng = np.random.default_rng(7)
+    xc, x, yc, y = draw(rng, 400000, 1000.0, 250.0, 0.28, np.array([30.0, 30.0, 10.0]),
+                        np.array([0.0024, 0.0024, 0.0008]))
+    r = rng.normal(size=len(x)) + 1j * rng.normal(size=len(x))
+    bias = 2e-8
+    plain = adjoint_terms(yc, y, xc, x, r, alternate=False, bias=bias).astype(np.float64).sum()
+    plain0 = adjoint_terms(yc, y, xc, x, r, alternate=False).astype(np.float64).sum()
+    alt = adjoint_terms(yc, y, xc, x, r, alternate=True, bias=bias).astype(np.float64).sum()
+    alt0 = adjoint_terms(yc, y, xc, x, r, alternate=True).astype(np.float64).sum()
+    assert abs((plain - plain0) - bias * np.abs(r).sum()) < 0.05 * bias * np.abs(r).sum()
+    assert abs(alt - alt0) < 0.02 * abs(plain - plain0)
