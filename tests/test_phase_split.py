@@ -19,6 +19,11 @@ paper-scale workloads and at the largest products the library accepts, and
 checks the phase against the FP64 phase: within 1e-6 turn, with an rms far
 below it.  It also checks the two facts the split rests on: whole-turn
 rounding is exact below 2^22, and an FP32 D past D_MAX would break the bound.
+
+The adjoint's output is real, so the kernel takes one cosine per pair,
+Re(conj(A) r) = |r| cos(theta + arg r), with arg r folded into B and every
+other term taken as -cos(theta + pi); the last two tests carry that form out
+in FP32 against the FP64 Re(conj(A) r), and show why the signs alternate.
 """
 import math
 
